@@ -1,0 +1,45 @@
+/*
+ * fdf_oracle.h -- interface of the plain scalar FP64 CPU oracle of the fastdf
+ * hot path (Elbers 2022, "Geodesic motion and phase-space evolution of massive
+ * neutrinos", arXiv:2207.14256).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This header and oracle/fdf_oracle.c are loaded by
+ * the test-suite, by the smoke check and by the benchmark's CPU-baseline leg,
+ * and by nothing else.  The product library (libfdf.so) neither includes this
+ * header nor links the oracle; the two share no code, no header and no table.
+ *
+ * Units: Mpc for lengths and conformal time (c = 1), eV for momenta, masses
+ * and temperature.  Arrays of 3-vectors are SoA: v[c*n + i], c = 0,1,2.
+ * Field grids are [8][N^3] with the cell index (iz*N + iy)*N + ix and the slot
+ * order (d_x psi, d_y psi, d_z psi, d_x phi, d_y phi, d_z phi, phi_dot, psi).
+ */
+#ifndef FDF_ORACLE_H
+#define FDF_ORACLE_H
+#include <stdint.h>
+
+typedef struct {
+    double   box;          /* L, Mpc */
+    int64_t  n_part;       /* particles per species */
+    int32_t  n_grid;       /* N, a power of two */
+    int32_t  n_species;
+    double   m_ev[4];      /* neutrino mass per species, eV */
+    double   T_K;          /* present-day neutrino temperature, K (paper: 1.95) */
+    double   z_start, z_end;
+    int32_t  n_steps;
+    int32_t  flags;        /* bit 0: fixed amplitudes (|R| = sqrt(P/V)) */
+    uint64_t seed;
+    double   h, omega_m, omega_r;   /* Omega_Lambda = 1 - omega_m - omega_r */
+    double   A_s, n_s, k_pivot;
+} or_params;
+
+typedef struct {
+    int32_t nk, na;
+    const double *lnk, *lna;                    /* ascending node positions */
+    const double *T_psi, *T_phi, *dTphi_dlna;   /* [na][nk] */
+    int32_t ncdf;
+    const double *cdf_t, *cdf_F;                /* q/T nodes, normalised CDF */
+} or_tables;
+
+#define OR_FLAG_FIXED_AMPLITUDE 1
+
+#endif
