@@ -1,0 +1,350 @@
+"""Throughput benchmark of the neutrino geodesic hot path on GB300.
+
+One benchmark step is one whole pass of the hot path over one workload:
+pre-initial sampling and momentum transform, n_steps leapfrog steps (each a
+field build at the new scale factor plus one fused particle pass), and the
+delta-f weighted CIC deposit.  The metric is particle-steps per second
+(species x particles x leapfrog steps / time).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (its own seed) with no data-path collective; rank 0 prints one JSON
+line with the whole-job aggregate.  --impl reference times the CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2207_14256_gb300 import inputs as I  # noqa: E402
+
+METRIC = "neutrino particle-steps/s at 256^3 vs plain FP64 GPU form; served p99 latency"
+UNIT = "particle-steps/s"
+WORKLOAD = "c3_3x256"
+PUSH_BYTES_PER_PARTICLE = {1: 60, 2: 60, 0: 120}   # algorithmic bytes per particle-step (see DESIGN)
+GRID_BYTES_PER_CELL = {1: 28, 2: 14, 0: 56}        # the 7 gradient fields read once per step
+
+
+def describe(p):
+    return ("%d species x %d^3 particles on a %d^3 grid, box %g Mpc, m = %s eV, %d steps in log a from z = %g "
+            "to %g, %s grids" % (p["n_species"], round(p["n_part"] ** (1 / 3)), p["n_grid"], p["box"],
+                                 "/".join("%g" % m for m in p["m_ev"]), p["n_steps"], p["z_start"], p["z_end"],
+                                 {0: "FP64", 1: "FP32", 2: "BF16"}[p["precision"]]))
+
+
+# ----------------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------------------------
+def run_once(fdf, ctx, p, out_dev):
+    fdf.fdf_sample(ctx)
+    fdf.fdf_step(ctx, p["n_steps"])
+    fdf.fdf_deposit(ctx, -1, fdf.FDF_Q_W_EPS, out_dev)
+
+
+def bench_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2207_14256_gb300 import fdf
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    p = I.config(args.workload, seed=I.config(args.workload)["seed"] + 1000 * rank)
+    tables = I.transfer_tables(p)
+    stream = torch.cuda.Stream(device=dev)
+    P = fdf.make_params(p)
+    T, keep = fdf.make_tables(tables)
+    N = p["n_grid"]
+    dep = torch.zeros((N, N, N), dtype=torch.float64, device=dev)
+    units = p["n_species"] * p["n_part"] * p["n_steps"]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    ctx = fdf.fdf_create(P, T, stream)
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                run_once(fdf, ctx, p, dep)
+            barrier()
+            clocks = Clocks(dev.index)
+            clocks.start()
+            fdf.fdf_timing(ctx, True)
+            l0 = fdf.fdf_launch_count(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record(stream)
+            for _ in range(args.steps):
+                run_once(fdf, ctx, p, dep)
+            e1.record(stream)
+            barrier()
+            ms = e0.elapsed_time(e1)
+            launches = fdf.fdf_launch_count(ctx) - l0
+            ktimes = {k: fdf.fdf_kernel_time(ctx, v) for k, v in fdf.KERNEL_CLASSES.items()}
+            fdf.fdf_timing(ctx, False)
+            clk = clocks.stop()
+    finally:
+        fdf.fdf_destroy(ctx)
+
+    # end to end through the C-ABI with host buffers: tables uploaded by fdf_create,
+    # every species' x, q, w read back into pinned host memory, every step
+    np_ = p["n_part"]
+    hx = torch.empty((3, np_), dtype=torch.float64, pin_memory=True)
+    hq = torch.empty((3, np_), dtype=torch.float64, pin_memory=True)
+    hw = torch.empty((np_,), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        c2 = fdf.fdf_create(P, T, stream)
+        try:
+            fdf.fdf_sample(c2)
+            fdf.fdf_step(c2, p["n_steps"])
+            for s in range(p["n_species"]):
+                fdf.fdf_get(c2, s, hx, hq, hw)
+        finally:
+            fdf.fdf_destroy(c2)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    tab_bytes = sum(np.asarray(tables[k]).nbytes for k in ("lnk", "lna", "T_psi", "T_phi", "dTphi_dlna", "cdf_t",
+                                                         "cdf_F"))
+
+    # the plain FP64 form on the same workload (one warm-up, one timed run)
+    plain = None
+    if not args.no_plain:
+        p64 = dict(p, precision=I.PREC_F64)
+        P64 = fdf.make_params(p64)
+        c3 = fdf.fdf_create(P64, T, stream)
+        try:
+            with torch.cuda.stream(stream):
+                run_once(fdf, c3, p64, dep)
+                barrier()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                fdf.fdf_timing(c3, True)
+                f0.record(stream)
+                run_once(fdf, c3, p64, dep)
+                f1.record(stream)
+                barrier()
+                pms = f0.elapsed_time(f1)
+                push64 = fdf.fdf_kernel_time(c3, fdf.FDF_K_PUSH)
+        finally:
+            fdf.fdf_destroy(c3)
+        plain = {"value": units / (pms / 1e3), "ms_per_step": pms, "push_ms_per_launch": push64[0] / push64[1]}
+
+    return dict(p=p, ms=ms, units=units, launches=launches, ktimes=ktimes, clocks=clk, e2e_s=e2e_s,
+                e2e_steps=e2e_steps, tab_bytes=tab_bytes, d2h=p["n_species"] * np_ * 7 * 8, plain=plain)
+
+
+# ----------------------------------------------------------------------------------------------
+def cpu_baseline(workload, budget_s=25.0):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload:
+    one field build at full grid size plus one leapfrog step of a particle subset,
+    extrapolated to the whole workload (grids per step + particles per step)."""
+    import oracle
+
+    p = I.config(workload)
+    tables = I.transfer_tables(p)
+    o = oracle.Oracle(p, tables)
+    threads = oracle.num_threads()
+    t0 = time.perf_counter()
+    R = o.noise()
+    t_noise = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.fields(o.lna(p["n_steps"] // 2), 0x7F, R)
+    t_grid = time.perf_counter() - t0
+    m = 1 << 16
+    gidx = np.arange(m)
+    frozen = np.zeros((8, p["n_grid"], p["n_grid"], p["n_grid"]))
+    ic = o.initial(gidx, frozen=frozen)
+    k = p["n_steps"] // 2
+    t0 = time.perf_counter()
+    o.integrate(gidx, ic["x"], ic["q"], ic["q0"], k, k + 2, frozen=frozen)
+    t_part = (time.perf_counter() - t0) / (2 * m)
+    n_total = p["n_species"] * p["n_part"]
+    t_step = t_grid + n_total * t_part
+    value = n_total / t_step
+    sample = ("oracle: one %d^3 field build (%.2f s) + two leapfrog steps of %d particles (%.2f us/particle-step, "
+              "frozen fields), extrapolated to %d particles x %d steps; noise field once (%.2f s, excluded)"
+              % (p["n_grid"], t_grid, m, t_part * 1e6, n_total, p["n_steps"], t_noise))
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+            "seconds_per_leapfrog_step": t_step}
+
+
+def line_base(args, world):
+    return {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    p = I.config(args.workload)
+
+    if args.impl == "reference":
+        # the CPU oracle: rank 0 alone works, other ranks exit without work
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(args.warmup + args.steps):
+            steps.append(cpu_baseline(args.workload))
+        timed = steps[args.warmup:]
+        v = float(np.median([s["value"] for s in timed]))
+        cb = dict(timed[0], value=v)
+        out = line_base(args, world)
+        out.update({"impl": "reference", "value": v,
+                    "ms_per_step": float(np.median([s["seconds_per_leapfrog_step"] for s in timed])) * 1e3 *
+                    p["n_steps"], "dtype": "f64",
+                    "config": {"workload": args.workload, "description": describe(p),
+                               "l2": "inputs larger than L2 (host run)"},
+                    "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                                "d2h_bytes_per_step": 0}})
+        print(json.dumps(out))
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl")
+        dist = td
+    r = bench_ours(args, rank, world, dist)
+    ms = r["ms"]
+    e2e_s = r["e2e_s"] / r["e2e_steps"]
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    ms_per_step = ms / args.steps
+    value = world * r["units"] / (ms_per_step / 1e3)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    prec = r["p"]["precision"]
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    push_ms, push_n = r["ktimes"]["push"]
+    push_avg = push_ms / max(push_n, 1)
+    n_total = r["p"]["n_species"] * r["p"]["n_part"]
+    N3 = r["p"]["n_grid"] ** 3
+    alg = n_total * PUSH_BYTES_PER_PARTICLE[prec] + N3 * GRID_BYTES_PER_CELL[prec]
+    achieved = alg / (push_avg / 1e3) / 1e9
+    roof = {"kernel": "k_push_split (fused drift + wrap + gather + kick)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if hbm else None, "traffic": None,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800",
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": push_avg}
+    per_run = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+               for k, v in r["ktimes"].items()}
+    out = line_base(args, world)
+    out.update({
+        "value": value, "ms_per_step": ms_per_step, "dtype": "f32",
+        "config": {"workload": args.workload, "description": describe(r["p"]),
+                   "l2": "inputs larger than L2 (%.1f GB particle state)" % (n_total * 48 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "e2e": {"value": world * r["units"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["tab_bytes"],
+                "d2h_bytes_per_step": r["d2h"],
+                "note": "fdf_create (table upload) + sample + steps + fdf_get of every species into pinned host "
+                        "memory + fdf_destroy, per step"},
+        "gpu_launches": r["launches"],
+        "kernels": per_run,
+        "clocks": r["clocks"],
+    })
+    if r["plain"]:
+        out["plain_f64"] = dict(r["plain"], value=world * r["plain"]["value"],
+                                note="the plain FP64 form (FP64 grids, FFT, state and arithmetic), same workload")
+        out["speedup_vs_plain_f64"] = value / out["plain_f64"]["value"]
+    if not args.no_cpu and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

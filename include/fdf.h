@@ -1,0 +1,214 @@
+/*
+ * fdf.h -- C-ABI of libfdf.so: GB300 (sm_103a) integration of massive-neutrino
+ * particles along geodesics of a linearly perturbed spacetime, the fastdf
+ * method of Elbers 2022, "Geodesic motion and phase-space evolution of massive
+ * neutrinos" (arXiv:2207.14256).
+ *
+ * The calls follow the paper's statement of the problem.  Inputs are the
+ * transfer functions of the potentials phi and psi, the box, the mesh, the
+ * step in log a, the redshift range, the neutrino masses and the particle
+ * count (Sec. 2.1 and Sec. 4).  Outputs are particle positions, momenta and
+ * delta-f weights (Sec. 2.2) and the weighted density estimate
+ * (eq:empirical_rho).
+ *
+ * Conventions.
+ *  - Units: Mpc for lengths and conformal time (c = 1); eV for momenta, masses
+ *    and temperatures; k in 1/Mpc.
+ *  - Every call returns FDF_OK (0) or a negative FDF_E* code; no exception or
+ *    C++ type crosses this boundary.  fdf_error_string() names a code and
+ *    fdf_last_error() returns the last detailed message of this thread.
+ *  - The context owns the device memory it allocated.  A caller-provided
+ *    arena stays owned by the caller and must outlive the context.
+ *  - All device work is enqueued on the CUDA stream given to fdf_create (NULL
+ *    = the legacy default stream).  Calls that return data to the host
+ *    (fdf_get, fdf_get_initial, fdf_deposit, fdf_build_fields with host
+ *    output) synchronise that stream before returning.
+ *  - Arrays of 3-vectors are structure-of-arrays: v[c * n + i], c = 0, 1, 2.
+ *    Grids are N^3 with cell index (iz * N + iy) * N + ix, node positions
+ *    x = (ix, iy, iz) * L / N.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef FDF_H
+#define FDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FDF_API __attribute__((visibility("default")))
+#else
+#define FDF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define FDF_OK        0
+#define FDF_EINVAL   (-1)  /* invalid argument or parameter set */
+#define FDF_ENOMEM   (-2)  /* device allocation failed, or the arena is too small */
+#define FDF_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed */
+#define FDF_ESTATE   (-4)  /* call out of order (e.g. fdf_step before fdf_sample) */
+#define FDF_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define FDF_ENAN     (-6)  /* a non-finite value was produced */
+#define FDF_ENOSYS   (-7)  /* configuration not supported by this build */
+
+/* ---- precision forms (fdf_params.precision) ------------------------------ */
+/* FDF_PREC_F64: the plain form.  Grids, FFTs, positions, momenta and all
+ *   arithmetic in FP64 (positions as FP64 Mpc, wrapped with floor).
+ * FDF_PREC_F32: the split form.  Grid build, FFT and gradient storage in FP32;
+ *   positions as 32-bit fixed-point fractions of the box (resolution
+ *   L / 2^32, periodic wrap exact by integer overflow); momenta as
+ *   q = q_0 + dq with q_0 and dq in FP32 (|dq| << |q|); the per-step drift
+ *   integral evaluated in float-float (about 44-bit mantissa) on the FP32
+ *   pipe; kick integrals in FP32.
+ * FDF_PREC_BF16: the split form with BF16 gradient-grid storage. */
+#define FDF_PREC_F64  0
+#define FDF_PREC_F32  1
+#define FDF_PREC_BF16 2
+
+/* ---- flags (fdf_params.flags) -------------------------------------------- */
+#define FDF_FLAG_FIXED_AMPLITUDE 1  /* |R_k| = sqrt(P(k)/V), random phase ("fixed" ICs, Sec. 4) */
+
+/* ---- deposit quantities (fdf_deposit) ------------------------------------ */
+#define FDF_Q_W_EPS 0  /* w_k eps_k: the delta-f energy density of eq:empirical_rho */
+#define FDF_Q_W     1  /* w_k */
+#define FDF_Q_EPS   2  /* eps_k (no delta-f weight) */
+#define FDF_Q_COUNT 3  /* 1 */
+
+/* ---- timed kernel classes (fdf_kernel_time) ------------------------------ */
+#define FDF_K_PUSH     0  /* fused drift + wrap + gather + kick */
+#define FDF_K_FIELDS_Z 1  /* spectrum generation + inverse DFT along z */
+#define FDF_K_FIELDS_Y 2  /* inverse DFT along y */
+#define FDF_K_FIELDS_X 3  /* inverse DFT along x + interleave into the gather grid */
+#define FDF_K_OTHER    4  /* sampling, initial transform, weights, deposit, export */
+#define FDF_K_COUNT    5
+
+typedef struct fdf_ctx fdf_ctx;
+
+/* Run parameters (Sec. 4 lists the paper's: 800^3 particles, L = 3.2 Gpc,
+ * M = 800, d log a = 0.01, z = 1e9 to 0).  Species share the potential grids
+ * and the time grid; they differ in mass.  The background is a flat
+ * radiation + matter + Lambda model, H = H0 sqrt(omega_r a^-4 + omega_m a^-3 +
+ * 1 - omega_m - omega_r), H0 = h / 2997.92458 Mpc^-1. */
+typedef struct fdf_params {
+    double   box_mpc;          /* L > 0 */
+    int64_t  n_part;           /* particles per species, >= 0 */
+    int32_t  n_grid;           /* N, power of two in [8, 512] */
+    int32_t  n_species;        /* 1..4 */
+    double   m_ev[4];          /* neutrino mass per species, >= 0 */
+    double   T_nu_K;           /* present-day neutrino temperature (1.95 K in Sec. 2) */
+    double   z_start, z_end;   /* z_start > z_end > -1 (paper: 1e9 and the N-body start) */
+    int32_t  n_steps;          /* >= 1, constant step in log a (Sec. 3.3) */
+    int32_t  precision;        /* FDF_PREC_* */
+    uint64_t seed;             /* Philox key of the sampler and of the Gaussian field */
+    double   h, omega_m, omega_r;
+    double   A_s, n_s, k_pivot; /* primordial curvature spectrum, k_pivot in 1/Mpc */
+    int32_t  flags;            /* FDF_FLAG_* */
+    int32_t  n_gl;             /* Gauss-Legendre nodes per step integral, 2..8; 0 = the
+                                  smallest count whose error bound is below 1e-13 for
+                                  this step size (4 at d ln a = 0.17) */
+    int32_t  sort_every;       /* re-bucket particles by cell every this many steps (0 = never) */
+    int32_t  reserved;
+} fdf_params;
+
+/* Input tables, host memory, copied by fdf_create.
+ *  T_psi, T_phi, dTphi_dlna: [na][nk] row-major, the transfer functions of
+ *  psi and phi relative to the primordial curvature R, and d T_phi / d ln a,
+ *  on uniform ascending grids lnk[nk] (ln(k Mpc)) and lna[na]; read with
+ *  bilinear interpolation in (ln k, ln a), clamped at the edges (Sec. 2.1:
+ *  CLASS supplies these in the paper).
+ *  cdf_t[ncdf], cdf_F[ncdf]: the normalised CDF F(t) of t^2 / (1 + e^t),
+ *  t = q/T, ascending, F[0] = 0; momenta are drawn by piecewise-linear
+ *  inversion (Sec. 2.1, Fermi-Dirac fbar). */
+typedef struct fdf_tables {
+    int32_t nk, na;
+    const double *lnk, *lna;
+    const double *T_psi, *T_phi, *dTphi_dlna;
+    int32_t ncdf;
+    const double *cdf_t, *cdf_F;
+} fdf_tables;
+
+/* Device bytes fdf_create would need for these parameters (admission
+ * control).  Returns FDF_EINVAL for an invalid parameter set. */
+FDF_API int fdf_footprint(const fdf_params* p, size_t* bytes);
+
+/* Validate p and t, copy the tables to the device, allocate (or carve from
+ * arena, a device pointer with arena_bytes >= fdf_footprint) every buffer,
+ * and precompute the background.  stream is a cudaStream_t (may be NULL).
+ * On success *out holds a new context; on failure *out is NULL. */
+FDF_API int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* arena, size_t arena_bytes,
+               fdf_ctx** out);
+
+/* Pre-initial conditions at z_start (Sec. 2.1): draw every particle of every
+ * species (uniform position, Fermi-Dirac |q|, isotropic direction, from
+ * Philox4x32-10 keyed by seed and addressed by the global particle index),
+ * build the fields at a_0 and apply the momentum transform eq:transform with
+ * delta = -2 psi and theta = k^2 tau psi / 2; set q_0 = q and p = |q_sampled|.
+ * Leaves the state at step 0. */
+FDF_API int fdf_sample(fdf_ctx* c);
+
+/* Advance n steps of the kick-drift-kick leapfrog of Sec. 3.3
+ * (eq:releq_approx, eq:geodesic_approx, eq:discrete_drift) with constant
+ * d log a; n < 0 steps backward.  Each step builds the potential-gradient
+ * grids at the new scale factor (spectrum times transfer functions times i k,
+ * inverse FFT) and makes one fused particle pass (drift, periodic wrap,
+ * trilinear gather, kick).  Positions and momenta are synchronised when the
+ * call returns.  FDF_EINVAL if the step index would leave [0, n_steps];
+ * FDF_ESTATE before fdf_sample. */
+FDF_API int fdf_step(fdf_ctx* c, int32_t n);
+
+/* Weighted CIC density estimate of eq:empirical_rho at the current scale
+ * factor: out[n] = sum_k v_k W(x_n - x_k) over the grid nodes n, with v_k
+ * chosen by quantity (FDF_Q_*), over one species (0..n_species-1) or all (-1).
+ * w_k = 1 - fbar(|q_k|)/fbar(p_k) (Sec. 2.2).  The raw sum is returned; the
+ * M/N normalisation is the caller's.  out is N^3 doubles, device memory if
+ * out_on_device else host memory. */
+FDF_API int fdf_deposit(fdf_ctx* c, int32_t species, int32_t quantity, double* out, int32_t out_on_device);
+
+/* Current state of one species in particle-index order: x[3][n_part] (Mpc,
+ * in [0, L)), q[3][n_part] (eV), w[n_part] (delta-f weight, Sec. 2.2).  Any
+ * output pointer may be NULL.  Device or host memory per out_on_device. */
+FDF_API int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_t out_on_device);
+
+/* The pre-initial draw of one species before the momentum transform:
+ * X[3][n_part] (x = L * X / 2^32), q_sampled[3][n_part] (eV) and
+ * p[n_part] = |q_sampled|.  Exact: every operation is a correctly rounded IEEE
+ * operation.  Any pointer may be NULL. */
+FDF_API int fdf_get_initial(fdf_ctx* c, int32_t species, uint32_t* X, double* q_sampled, double* p, int32_t out_on_device);
+
+/* Test and inspection hook: the eight real fields at ln a, as built on the
+ * device for the particle pass, converted to FP64: out[8][N^3] in the slot
+ * order (d_x psi, d_y psi, d_z psi, d_x phi, d_y phi, d_z phi, phi_dot, psi),
+ * phi_dot = a H d phi / d ln a.  Field convention f(x) = sum_n f_n e^{i k.x}. */
+FDF_API int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device);
+
+/* Test hook: freeze the fields.  fields[8][N^3] (same layout as
+ * fdf_build_fields) replace the per-step grid build for every later call;
+ * fields = NULL returns to building them. */
+FDF_API int fdf_set_fields(fdf_ctx* c, const double* fields, int32_t on_device);
+
+/* Current step index (0..n_steps) and its ln a. */
+FDF_API int fdf_state(fdf_ctx* c, int32_t* step, double* lna);
+
+/* Kernel timing with CUDA events recorded on the context's stream around
+ * each launch of the classes FDF_K_*.  fdf_timing(c, 1) clears and starts,
+ * fdf_timing(c, 0) stops; fdf_kernel_time synchronises and returns the summed
+ * milliseconds and the launch count of one class. */
+FDF_API int fdf_timing(fdf_ctx* c, int32_t enable);
+FDF_API int fdf_kernel_time(fdf_ctx* c, int32_t which, double* ms, int64_t* launches);
+
+/* Number of kernels this context has launched since creation. */
+FDF_API int64_t fdf_launch_count(const fdf_ctx* c);
+
+FDF_API const char* fdf_error_string(int code);
+FDF_API const char* fdf_last_error(void);
+
+/* Free everything the context allocated.  NULL is allowed. */
+FDF_API void fdf_destroy(fdf_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDF_H */

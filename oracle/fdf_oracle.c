@@ -563,13 +563,18 @@ typedef struct {
     double complex* R;
 } field_src;
 
-static double* fields_at(field_src* fs, double k, unsigned mask)
+static const double* fields_at(field_src* fs, double k, unsigned mask)
 {
+    if (fs->frozen) return fs->frozen;
     size_t N3 = (size_t)fs->p->n_grid * fs->p->n_grid * fs->p->n_grid;
     double* F = (double*)calloc(8 * N3, sizeof(double));
-    if (fs->frozen) memcpy(F, fs->frozen, sizeof(double) * 8 * N3);
-    else or_fields(fs->p, fs->t, fs->R, or_lna(fs->p, k), mask, F, NULL);
+    or_fields(fs->p, fs->t, fs->R, or_lna(fs->p, k), mask, F, NULL);
     return F;
+}
+
+static void fields_done(field_src* fs, const double* F)
+{
+    if (F != fs->frozen) free((void*)F);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -588,7 +593,7 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
         fs.R = (double complex*)malloc(sizeof(double complex) * N3);
         or_noise(p, fs.R);
     }
-    double* F = fields_at(&fs, 0.0, 0xFFu);
+    const double* F = fields_at(&fs, 0.0, 0xFFu);
     const double a0 = exp(or_lna(p, 0.0));
     const double tau0 = or_tau(p, a0);
     const double L = p->box;
@@ -606,7 +611,7 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
             q0[d * n + i] = qd;
         }
     }
-    free(F);
+    fields_done(&fs, F);
     free(fs.R);
     return 0;
 }
@@ -630,9 +635,9 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
         fs.R = (double complex*)malloc(sizeof(double complex) * N3);
         or_noise(p, fs.R);
     }
-    double* Fk = fields_at(&fs, (double)k_from, 0x7Fu);
+    const double* Fk = fields_at(&fs, (double)k_from, 0x7Fu);
     for (int k = k_from; k != k_to; k += dir) {
-        double* Fn = fields_at(&fs, (double)(k + dir), 0x7Fu);
+        const double* Fn = fields_at(&fs, (double)(k + dir), 0x7Fu);
         double lk = or_lna(p, k), lh = or_lna(p, k + 0.5 * dir), ln = or_lna(p, k + dir);
         or_quad Qopen, Qdrift, Qclose;
         quad_nodes(p, lk, lh, &Qopen);
@@ -660,10 +665,10 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
                 q[d * n + i] = qi[d];
             }
         }
-        free(Fk);
+        fields_done(&fs, Fk);
         Fk = Fn;
     }
-    free(Fk);
+    fields_done(&fs, Fk);
     free(fs.R);
     return 0;
 }

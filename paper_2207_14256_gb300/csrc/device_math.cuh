@@ -1,0 +1,111 @@
+// device_math.cuh -- small device helpers: Philox4x32-10, float-float
+// arithmetic, complex multiply, fixed-point cell lookup.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "fdf_internal.cuh"
+
+namespace fdf {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products mixed with the other two words and the key; the key
+// is bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// ---- float-float (Dekker / Knuth error-free transforms on the FP32 pipe) ----
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)  // |a| >= |b|
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    FF r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    FF r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+// 1/sqrt(s) to about 2^-44 relative: hardware seed and one Newton step whose
+// residual 1 - s y^2 is formed exactly enough in float-float.
+__device__ __forceinline__ FF ff_rsqrt(FF s)
+{
+    const float y = rsqrtf(s.hi);
+    const float y2 = __fmul_rn(y, y);
+    const float y2e = __fmaf_rn(y, y, -y2);
+    const float p = __fmul_rn(s.hi, y2);
+    const float pe = __fmaf_rn(s.hi, y2, -p);
+    const float res = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmaf_rn(s.hi, y2e, __fmul_rn(s.lo, y2)));
+    FF r;
+    fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), res), r.hi, r.lo);
+    return r;
+}
+
+// ---- complex ----
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <typename V> struct Real;
+template <> struct Real<float2> { using T = float; };
+template <> struct Real<double2> { using T = double; };
+
+template <typename V> __device__ __forceinline__ V mk(typename Real<V>::T x, typename Real<V>::T y);
+template <> __device__ __forceinline__ float2 mk<float2>(float x, float y) { return make_float2(x, y); }
+template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) { return make_double2(x, y); }
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmuli(V a) { return mk<V>(-a.y, a.x); }  // i a
+
+// ---- fixed-point periodic coordinate -> (cell, fraction) on an N grid -------
+// X / 2^32 is the position in units of L; cell = floor(X N / 2^32), fraction =
+// ((X N) mod 2^32) / 2^32.
+__device__ __forceinline__ void fixed_cell(uint32_t X, uint32_t N, uint32_t& i0, uint32_t& i1, float& f)
+{
+    i0 = __umulhi(X, N);
+    f = __uint2float_rn(X * N) * 2.3283064365386963e-10f;
+    i1 = (i0 + 1u == N) ? 0u : i0 + 1u;
+}
+
+}  // namespace fdf

@@ -1,0 +1,787 @@
+// fdf_api.cu -- host side of libfdf.so: the C-ABI of include/fdf.h.
+//
+// The context validates the run, owns one device block carved into every
+// buffer, computes the background quantities and the per-pass quadrature
+// coefficients on the host in FP64, and enqueues the kernels on the caller's
+// stream in the order of the method (Elbers 2022):
+//   fdf_sample: sampling (Sec. 2.1), fields at a_0, pre-initial transform
+//               (eq:transform);
+//   fdf_step:   per step, the fields at a_{k+1} and one fused particle pass
+//               of the kick-drift-kick leapfrog of Sec. 3.3; consecutive half
+//               kicks that read the same grid at the same position are merged
+//               into one kick over [a_{k+1/2}, a_{k+3/2}].
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fdf_internal.cuh"
+
+using namespace fdf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+constexpr double kC_over_H100 = 2997.92458;  // c / (100 km/s/Mpc) in Mpc
+constexpr double kBoltzmann_eV = 8.617333262e-5;
+constexpr double kPi = 3.14159265358979323846;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+size_t grid_bytes_per_cell(int prec) { return prec == FDF_PREC_F64 ? 64 : (prec == FDF_PREC_F32 ? 32 : 16); }
+size_t complex_bytes(int prec) { return prec == FDF_PREC_F64 ? 16 : 8; }
+size_t real_bytes(int prec) { return prec == FDF_PREC_F64 ? 8 : 4; }
+
+// Gauss-Legendre rule on [-1, 1] by Newton's method on P_n, with
+// P_n' = n (x P_n - P_{n-1}) / (x^2 - 1).
+void gauss_legendre(int n, double* x, double* w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = -std::cos(kPi * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 60; ++it) {
+            double pm = 1.0, pn = z;
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2 * k - 1) * z * pn - (k - 1) * pm) / k;
+                pm = pn;
+                pn = pk;
+            }
+            const double dz = pn / (n * (z * pn - pm) / (z * z - 1.0));
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double pm = 1.0, pn = z;
+        for (int k = 2; k <= n; ++k) {
+            const double pk = ((2 * k - 1) * z * pn - (k - 1) * pm) / k;
+            pm = pn;
+            pn = pk;
+        }
+        const double d = n * (z * pn - pm) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * d * d);
+    }
+}
+
+// Nodes per step integral.  The integrands 1/(a H sqrt(q^2 + m^2 a^2)) and
+// their kin are analytic in ln a within |Im ln a| < pi/2 (the branch points of
+// sqrt(q^2 + m^2 a^2) sit at a = +-i q/m), so an n-point Gauss-Legendre rule
+// on a step of half-width h converges like rho^(-2n) with rho = b + sqrt(b^2 + 1),
+// b = (pi/2)/h.  Take the smallest n (2..8) with rho^(-2n) < 1e-13.
+int auto_nodes(double dlna)
+{
+    const double h = 0.5 * std::fabs(dlna);
+    const double b = 0.5 * kPi / h;
+    const double rho = b + std::sqrt(b * b + 1.0);
+    int n = 2;
+    while (n < kMaxGL && std::pow(rho, -2.0 * n) > 1e-13) ++n;
+    return n;
+}
+
+FF split_ff(double v)
+{
+    FF r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+}
+
+struct Layout {
+    size_t tabs, cdf_t, cdf_F, tw, W0, W1, G0, G1, X, q0f, dqf, xd, qd, q0d, qs, pmag, id, stage, dep, flag, total;
+};
+
+Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
+{
+    Layout L{};
+    const int prec = p.precision;
+    const size_t N = (size_t)p.n_grid, N3 = N * N * N;
+    const size_t n = (size_t)p.n_part * (size_t)p.n_species;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes ? bytes : 1);
+        return o;
+    };
+    L.tabs = take(3 * (size_t)na * nk * real_bytes(prec));
+    L.cdf_t = take((size_t)ncdf * 8);
+    L.cdf_F = take((size_t)ncdf * 8);
+    L.tw = take(N * complex_bytes(prec));
+    L.W0 = take(4 * N3 * complex_bytes(prec));
+    L.W1 = take(4 * N3 * complex_bytes(prec));
+    L.G0 = take(N3 * grid_bytes_per_cell(prec));
+    L.G1 = take(N3 * grid_bytes_per_cell(prec));
+    L.X = take(3 * n * 4);
+    const bool split = prec != FDF_PREC_F64;
+    L.q0f = take(split ? 3 * n * 4 : 0);
+    L.dqf = take(split ? 3 * n * 4 : 0);
+    L.xd = take(split ? 0 : 3 * n * 8);
+    L.qd = take(split ? 0 : 3 * n * 8);
+    L.q0d = take(split ? 0 : 3 * n * 8);
+    L.qs = take(3 * n * 8);
+    L.pmag = take(n * 8);
+    L.id = take(n * 4);
+    L.stage = take(7 * (size_t)p.n_part * 8);
+    L.dep = take(N3 * 8);
+    L.flag = take(64);
+    L.total = off;
+    return L;
+}
+
+int validate(const fdf_params* p)
+{
+    if (!p) return fail(FDF_EINVAL, "params is NULL");
+    if (!(p->box_mpc > 0) || !std::isfinite(p->box_mpc)) return fail(FDF_EINVAL, "box_mpc must be > 0");
+    if (p->n_part < 0) return fail(FDF_EINVAL, "n_part must be >= 0");
+    if (!is_pow2(p->n_grid) || p->n_grid < 8 || p->n_grid > 512)
+        return fail(FDF_EINVAL, "n_grid must be a power of two in [8, 512]");
+    if (p->n_species < 1 || p->n_species > kMaxSpecies) return fail(FDF_EINVAL, "n_species must be in 1..4");
+    if ((double)p->n_part * p->n_species >= 4294967296.0) return fail(FDF_EINVAL, "more than 2^32 - 1 particles");
+    for (int s = 0; s < p->n_species; ++s)
+        if (!(p->m_ev[s] >= 0) || !std::isfinite(p->m_ev[s])) return fail(FDF_EINVAL, "masses must be >= 0");
+    if (!(p->T_nu_K > 0)) return fail(FDF_EINVAL, "T_nu_K must be > 0");
+    if (!(p->z_start > p->z_end) || !(p->z_end > -1.0) || !std::isfinite(p->z_start))
+        return fail(FDF_EINVAL, "need z_start > z_end > -1");
+    if (p->n_steps < 1) return fail(FDF_EINVAL, "n_steps must be >= 1");
+    if (p->precision < FDF_PREC_F64 || p->precision > FDF_PREC_BF16) return fail(FDF_EINVAL, "unknown precision");
+    if (p->n_gl != 0 && (p->n_gl < 2 || p->n_gl > kMaxGL)) return fail(FDF_EINVAL, "n_gl must be 0 or 2..8");
+    if (!(p->h > 0) || !(p->omega_m >= 0) || !(p->omega_r >= 0) || !(p->A_s > 0) || !(p->k_pivot > 0) ||
+        !std::isfinite(p->n_s))
+        return fail(FDF_EINVAL, "invalid cosmology");
+    const double ol = 1.0 - p->omega_m - p->omega_r;
+    const double a0 = 1.0 / (1.0 + p->z_start);
+    if (!(p->omega_r / (a0 * a0 * a0 * a0) + p->omega_m / (a0 * a0 * a0) + ol > 0))
+        return fail(FDF_EINVAL, "H^2 <= 0 at z_start");
+    if (p->sort_every < 0) return fail(FDF_EINVAL, "sort_every must be >= 0");
+    return FDF_OK;
+}
+
+bool uniform_grid(const double* v, int n, double* v0, double* dv)
+{
+    if (n < 2) return false;
+    const double d = (v[n - 1] - v[0]) / (n - 1);
+    if (!(d > 0)) return false;
+    for (int i = 0; i < n; ++i)
+        if (std::fabs(v[i] - (v[0] + i * d)) > 1e-9 * std::fabs(d) + 1e-12 * std::fabs(v[i])) return false;
+    *v0 = v[0];
+    *dv = d;
+    return true;
+}
+
+}  // namespace
+
+struct fdf_ctx {
+    fdf_params p{};
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    int ngl = 4;
+    double glx[kMaxGL]{}, glw[kMaxGL]{};
+    double T_ev = 0, H0 = 0, ol = 0, lna0 = 0, lnaN = 0, dlna = 0, a0 = 0, tau0 = 0;
+    int nk = 0, na = 0, ncdf = 0;
+    double lnk0 = 0, dlnk = 0, lnat0 = 0, dlnat = 0;
+    Layout lay{};
+    char* block = nullptr;
+    bool own_block = false;
+    void* tabs = nullptr;
+    double* cdf_t = nullptr;
+    double* cdf_F = nullptr;
+    void* tw = nullptr;
+    void* W0 = nullptr;
+    void* W1 = nullptr;
+    void* G[2] = {nullptr, nullptr};
+    int gk[2] = {-1, -1};
+    int cur = 0;
+    void* Gfrozen = nullptr;
+    bool frozen = false;
+    ParticleState st{};
+    double* stage = nullptr;
+    double* dep = nullptr;
+    int* dflag = nullptr;
+    bool sampled = false;
+    bool stepped = false;
+    int k = 0;
+    int64_t launches = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+
+    double hubble(double a) const
+    {
+        return H0 * std::sqrt(p.omega_r / (a * a * a * a) + p.omega_m / (a * a * a) + ol);
+    }
+    double lna(double kk) const { return lna0 + kk * dlna; }
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(FDF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define FDF_CUDA(call, what)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
+    } while (0)
+
+cudaEvent_t take_event(fdf_ctx* c)
+{
+    if (c->pool_used == c->pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->pool.push_back(e);
+    }
+    return c->pool[c->pool_used++];
+}
+
+// Runs one launch, bracketed by events when timing is on.
+template <typename F>
+int timed(fdf_ctx* c, int cls, const char* what, F&& launch)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        if (e0) cudaEventRecord(e0, c->stream);
+    }
+    cudaError_t e = launch();
+    ++c->launches;
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (c->timing && e0 && e1) {
+        cudaEventRecord(e1, c->stream);
+        c->marks.push_back({cls, {e0, e1}});
+    }
+    return FDF_OK;
+}
+
+// Conformal time from a = 0: tau(a0) = int_0^a0 da / (a^2 H), a 32-point
+// Gauss-Legendre rule on [0, a0] (the integrand 1/(H0 sqrt(omega_r + omega_m a
+// + Omega_L a^4)) is smooth there).
+double tau_of(const fdf_ctx* c, double a)
+{
+    double x[32], w[32];
+    gauss_legendre(32, x, w);
+    double s = 0;
+    for (int j = 0; j < 32; ++j) {
+        const double aj = 0.5 * a * (x[j] + 1.0);
+        s += w[j] / std::sqrt(c->p.omega_r + c->p.omega_m * aj + c->ol * aj * aj * aj * aj);
+    }
+    return 0.5 * a * s / c->H0;
+}
+
+// Gauss-Legendre nodes of [l1, l2] in ln a: weights W_j (dtau) and a_j^2.
+void nodes(const fdf_ctx* c, double l1, double l2, double* W, double* a2)
+{
+    const double half = 0.5 * (l2 - l1), mid = 0.5 * (l1 + l2);
+    for (int j = 0; j < c->ngl; ++j) {
+        const double a = std::exp(mid + half * c->glx[j]);
+        W[j] = c->glw[j] * half / (a * c->hubble(a));
+        a2[j] = a * a;
+    }
+}
+
+// Coefficients of one particle pass: drift over [d1, d2] (if any), kick over [k1, k2] (if any).
+void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, double k1, double k2, PushArgs& a)
+{
+    std::memset(&a, 0, sizeof(a));
+    a.n = c->n;
+    a.n_part = c->p.n_part > 0 ? c->p.n_part : 1;
+    a.n_gl = c->ngl;
+    a.do_drift = drift;
+    a.do_kick = kick;
+    a.N = c->p.n_grid;
+    a.L = c->p.box_mpc;
+    a.invL = 1.0 / c->p.box_mpc;
+    a.invh = c->p.n_grid / c->p.box_mpc;
+    a.fx_scale = split_ff(4294967296.0 / c->p.box_mpc);
+    double Wd[kMaxGL], ad[kMaxGL], Wk[kMaxGL], ak[kMaxGL];
+    if (drift) nodes(c, d1, d2, Wd, ad);
+    if (kick) nodes(c, k1, k2, Wk, ak);
+    const int jc = c->ngl / 2;
+    for (int s = 0; s < c->p.n_species; ++s) {
+        SpeciesCoef& sc = a.sp[s];
+        const double m2 = c->p.m_ev[s] * c->p.m_ev[s];
+        if (drift) {
+            double sum = 0;
+            for (int j = 0; j < c->ngl; ++j) {
+                sc.Wd[j] = Wd[j];
+                sc.mud[j] = m2 * ad[j];
+                sum += Wd[j];
+            }
+            sc.Wd_sum = split_ff(sum);
+            sc.mud_c = split_ff(sc.mud[jc]);
+            for (int j = 0; j < c->ngl; ++j) {
+                sc.Wd_f[j] = (float)Wd[j];
+                sc.dmud_f[j] = (float)(sc.mud[j] - sc.mud[jc]);
+            }
+        }
+        if (kick) {
+            double dt = 0;
+            for (int j = 0; j < c->ngl; ++j) {
+                sc.Wk[j] = Wk[j];
+                sc.muk[j] = m2 * ak[j];
+                sc.Wk_f[j] = (float)Wk[j];
+                sc.muk_f[j] = (float)sc.muk[j];
+                dt += Wk[j];
+            }
+            sc.dtau_k = dt;
+            sc.dtau_k_f = (float)dt;
+        }
+    }
+}
+
+int build_fields(fdf_ctx* c, double lna, void* G)
+{
+    FieldArgs a{};
+    a.N = c->p.n_grid;
+    a.logN = ilog2(a.N);
+    a.nk = c->nk;
+    a.na = c->na;
+    a.kf = 2.0 * kPi / c->p.box_mpc;
+    a.lnk0 = c->lnk0;
+    a.inv_dlnk = 1.0 / c->dlnk;
+    double pos = (lna - c->lnat0) / c->dlnat;
+    if (pos <= 0) {
+        a.ia = 0;
+        a.fa = 0;
+    } else if (pos >= c->na - 1) {
+        a.ia = c->na - 2;
+        a.fa = 1;
+    } else {
+        a.ia = (int)pos;
+        a.fa = pos - a.ia;
+    }
+    const double aa = std::exp(lna);
+    a.aH = aa * c->hubble(aa);
+    const double V = c->p.box_mpc * c->p.box_mpc * c->p.box_mpc;
+    a.amp0 = std::sqrt(2.0 * kPi * kPi * c->p.A_s / V);
+    a.half_nsm1 = 0.5 * (c->p.n_s - 1.0);
+    a.lnkp = std::log(c->p.k_pivot);
+    a.key0 = (uint32_t)c->p.seed;
+    a.key1 = (uint32_t)(c->p.seed >> 32);
+    a.fixed_amp = (c->p.flags & FDF_FLAG_FIXED_AMPLITUDE) ? 1 : 0;
+    const int prec = c->p.precision;
+    int rc = timed(c, FDF_K_FIELDS_Z, "fields z pass",
+                   [&] { return launch_fields_z(c->stream, prec, a, c->tabs, c->tw, c->W0); });
+    if (rc) return rc;
+    rc = timed(c, FDF_K_FIELDS_Y, "fields y pass",
+               [&] { return launch_fields_y(c->stream, prec, a, c->tw, c->W0, c->W1); });
+    if (rc) return rc;
+    return timed(c, FDF_K_FIELDS_X, "fields x pass",
+                 [&] { return launch_fields_x(c->stream, prec, a, c->tw, c->W1, G); });
+}
+
+int push(fdf_ctx* c, const PushArgs& a, const void* G)
+{
+    return timed(c, FDF_K_PUSH, "particle pass", [&] { return launch_push(c->stream, c->p.precision, c->st, a, G); });
+}
+
+const void* grid_for_step(fdf_ctx* c, int buf) { return c->frozen ? c->Gfrozen : c->G[buf]; }
+
+}  // namespace
+
+extern "C" {
+
+int fdf_footprint(const fdf_params* p, size_t* bytes)
+{
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!bytes) return fail(FDF_EINVAL, "bytes is NULL");
+    *bytes = make_layout(*p, 1024, 256, 8192).total;
+    return FDF_OK;
+}
+
+int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* arena, size_t arena_bytes,
+               fdf_ctx** out)
+{
+    if (!out) return fail(FDF_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!t || !t->lnk || !t->lna || !t->T_psi || !t->T_phi || !t->dTphi_dlna || !t->cdf_t || !t->cdf_F)
+        return fail(FDF_EINVAL, "tables incomplete");
+    if (t->nk < 2 || t->na < 2 || t->nk > 1024 || t->na > 256 || t->ncdf < 2 || t->ncdf > 8192)
+        return fail(FDF_EINVAL, "table sizes out of range (nk 2..1024, na 2..256, ncdf 2..8192)");
+    fdf_ctx* c = new (std::nothrow) fdf_ctx;
+    if (!c) return fail(FDF_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->stream = (cudaStream_t)stream;
+    c->n = p->n_part * p->n_species;
+    c->H0 = p->h / kC_over_H100;
+    c->ol = 1.0 - p->omega_m - p->omega_r;
+    c->T_ev = p->T_nu_K * kBoltzmann_eV;
+    c->lna0 = -std::log(1.0 + p->z_start);
+    c->lnaN = -std::log(1.0 + p->z_end);
+    c->dlna = (c->lnaN - c->lna0) / p->n_steps;
+    if (c->p.n_gl == 0) c->p.n_gl = auto_nodes(c->dlna);
+    c->ngl = c->p.n_gl;
+    gauss_legendre(c->ngl, c->glx, c->glw);
+    c->a0 = std::exp(c->lna0);
+    c->tau0 = tau_of(c, c->a0);
+    c->nk = t->nk;
+    c->na = t->na;
+    c->ncdf = t->ncdf;
+    if (!uniform_grid(t->lnk, t->nk, &c->lnk0, &c->dlnk) || !uniform_grid(t->lna, t->na, &c->lnat0, &c->dlnat)) {
+        delete c;
+        return fail(FDF_EINVAL, "lnk and lna must be uniform ascending grids");
+    }
+    for (int i = 1; i < t->ncdf; ++i)
+        if (!(t->cdf_t[i] > t->cdf_t[i - 1]) || !(t->cdf_F[i] >= t->cdf_F[i - 1])) {
+            delete c;
+            return fail(FDF_EINVAL, "cdf_t must ascend and cdf_F must not descend");
+        }
+    c->lay = make_layout(c->p, t->nk, t->na, t->ncdf);
+    const Layout& L = c->lay;
+    if (arena) {
+        if (arena_bytes < L.total) {
+            delete c;
+            return fail(FDF_ENOMEM, "arena smaller than the footprint");
+        }
+        c->block = (char*)arena;
+    } else {
+        cudaError_t e = cudaMalloc(&c->block, L.total);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(FDF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        c->own_block = true;
+    }
+    char* b = c->block;
+    c->tabs = b + L.tabs;
+    c->cdf_t = (double*)(b + L.cdf_t);
+    c->cdf_F = (double*)(b + L.cdf_F);
+    c->tw = b + L.tw;
+    c->W0 = b + L.W0;
+    c->W1 = b + L.W1;
+    c->G[0] = b + L.G0;
+    c->G[1] = b + L.G1;
+    c->st.X = (uint32_t*)(b + L.X);
+    c->st.q0f = (float*)(b + L.q0f);
+    c->st.dqf = (float*)(b + L.dqf);
+    c->st.xd = (double*)(b + L.xd);
+    c->st.qd = (double*)(b + L.qd);
+    c->st.q0d = (double*)(b + L.q0d);
+    c->st.qs = (double*)(b + L.qs);
+    c->st.pmag = (double*)(b + L.pmag);
+    c->st.id = (uint32_t*)(b + L.id);
+    c->stage = (double*)(b + L.stage);
+    c->dep = (double*)(b + L.dep);
+    c->dflag = (int*)(b + L.flag);
+    // tables and twiddles
+    const size_t ntab = (size_t)t->na * t->nk;
+    const int N = p->n_grid;
+    std::vector<double> tab(3 * ntab);
+    std::memcpy(tab.data(), t->T_psi, ntab * 8);
+    std::memcpy(tab.data() + ntab, t->T_phi, ntab * 8);
+    std::memcpy(tab.data() + 2 * ntab, t->dTphi_dlna, ntab * 8);
+    std::vector<double> twd(2 * (size_t)N);
+    for (int j = 0; j < N; ++j) {
+        twd[2 * j] = std::cos(2.0 * kPi * j / N);
+        twd[2 * j + 1] = std::sin(2.0 * kPi * j / N);
+    }
+    cudaError_t e = cudaSuccess;
+    if (p->precision == FDF_PREC_F64) {
+        e = cudaMemcpy(c->tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> tf(tab.begin(), tab.end()), twf(twd.begin(), twd.end());
+        e = cudaMemcpy(c->tabs, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(c->cdf_t, t->cdf_t, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->cdf_F, t->cdf_F, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->dflag, 0, 64);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "uploading tables");
+        fdf_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return FDF_OK;
+}
+
+int fdf_sample(fdf_ctx* c)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    FDF_CUDA(cudaMemsetAsync(c->dflag, 0, 64, c->stream), "clearing flags");
+    const uint32_t k0 = (uint32_t)c->p.seed, k1 = (uint32_t)(c->p.seed >> 32);
+    int rc = timed(c, FDF_K_OTHER, "sampling", [&] {
+        return launch_sample(c->stream, c->n, k0, k1, c->T_ev, c->cdf_t, c->cdf_F, c->ncdf, c->st.X, c->st.qs,
+                             c->st.pmag, c->st.id, c->dflag);
+    });
+    if (rc) return rc;
+    c->cur = 0;
+    c->gk[0] = c->gk[1] = -1;
+    if (!c->frozen) {
+        rc = build_fields(c, c->lna(0), c->G[0]);
+        if (rc) return rc;
+        c->gk[0] = 0;
+    }
+    rc = timed(c, FDF_K_OTHER, "initial transform", [&] {
+        return launch_initial(c->stream, c->p.precision, c->st, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
+                              c->p.m_ev, c->a0, c->tau0, c->p.n_grid, c->p.box_mpc, grid_for_step(c, 0));
+    });
+    if (rc) return rc;
+    int flag = 0;
+    FDF_CUDA(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "reading flags");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "sampling");
+    if (flag) return fail(FDF_EINVAL, "a direction could not be drawn in 64 attempts");
+    c->sampled = true;
+    c->stepped = false;
+    c->k = 0;
+    return FDF_OK;
+}
+
+int fdf_step(fdf_ctx* c, int32_t n)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!c->sampled) return fail(FDF_ESTATE, "fdf_step before fdf_sample");
+    const int64_t target = (int64_t)c->k + n;
+    if (target < 0 || target > c->p.n_steps) return fail(FDF_EINVAL, "step index would leave [0, n_steps]");
+    if (n == 0) return FDF_OK;
+    c->stepped = true;
+    const int dir = n > 0 ? 1 : -1;
+    const int steps = n > 0 ? n : -n;
+    int rc;
+    if (!c->frozen && c->gk[c->cur] != c->k) {
+        rc = build_fields(c, c->lna(c->k), c->G[c->cur]);
+        if (rc) return rc;
+        c->gk[c->cur] = c->k;
+    }
+    PushArgs a;
+    fill_push(c, false, 0, 0, true, c->lna(c->k), c->lna(c->k + 0.5 * dir), a);
+    rc = push(c, a, grid_for_step(c, c->cur));
+    if (rc) return rc;
+    for (int i = 0; i < steps; ++i) {
+        const int k1 = c->k + dir;
+        const int nxt = c->cur ^ 1;
+        if (!c->frozen) {
+            rc = build_fields(c, c->lna(k1), c->G[nxt]);
+            if (rc) return rc;
+            c->gk[nxt] = k1;
+        }
+        const bool last = i == steps - 1;
+        fill_push(c, true, c->lna(c->k), c->lna(k1), true, c->lna(c->k + 0.5 * dir),
+                  last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a);
+        rc = push(c, a, grid_for_step(c, nxt));
+        if (rc) return rc;
+        c->cur = nxt;
+        c->k = k1;
+    }
+    return FDF_OK;
+}
+
+int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_t out_on_device)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!c->sampled) return fail(FDF_ESTATE, "fdf_get before fdf_sample");
+    if (species < 0 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
+    const int64_t np = c->p.n_part;
+    if (np == 0) return FDF_OK;
+    const int64_t begin = species * np;
+    double* xs = out_on_device ? x : (x ? c->stage : nullptr);
+    double* qs = out_on_device ? q : (q ? c->stage + 3 * np : nullptr);
+    double* ws = out_on_device ? w : (w ? c->stage + 6 * np : nullptr);
+    int rc = timed(c, FDF_K_OTHER, "export", [&] {
+        return launch_export(c->stream, c->p.precision, c->st, c->n, begin, np, c->p.box_mpc, c->T_ev, xs, qs, ws);
+    });
+    if (rc) return rc;
+    if (!out_on_device) {
+        if (x) FDF_CUDA(cudaMemcpyAsync(x, xs, 3 * np * 8, cudaMemcpyDeviceToHost, c->stream), "copy x");
+        if (q) FDF_CUDA(cudaMemcpyAsync(q, qs, 3 * np * 8, cudaMemcpyDeviceToHost, c->stream), "copy q");
+        if (w) FDF_CUDA(cudaMemcpyAsync(w, ws, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy w");
+    }
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_get");
+    return FDF_OK;
+}
+
+int fdf_get_initial(fdf_ctx* c, int32_t species, uint32_t* X, double* q_sampled, double* pm, int32_t out_on_device)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!c->sampled || c->stepped) return fail(FDF_ESTATE, "valid between fdf_sample and the first fdf_step");
+    if (species < 0 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
+    const int64_t np = c->p.n_part, n = c->n, begin = species * np;
+    if (np == 0) return FDF_OK;
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int d = 0; d < 3; ++d) {
+        if (X) FDF_CUDA(cudaMemcpyAsync(X + d * np, c->st.X + d * n + begin, np * 4, kind, c->stream), "copy X");
+        if (q_sampled)
+            FDF_CUDA(cudaMemcpyAsync(q_sampled + d * np, c->st.qs + d * n + begin, np * 8, kind, c->stream),
+                     "copy q_sampled");
+    }
+    if (pm) FDF_CUDA(cudaMemcpyAsync(pm, c->st.pmag + begin, np * 8, kind, c->stream), "copy p");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_get_initial");
+    return FDF_OK;
+}
+
+int fdf_deposit(fdf_ctx* c, int32_t species, int32_t quantity, double* out, int32_t out_on_device)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!c->sampled) return fail(FDF_ESTATE, "fdf_deposit before fdf_sample");
+    if (species < -1 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
+    if (quantity < FDF_Q_W_EPS || quantity > FDF_Q_COUNT) return fail(FDF_EINVAL, "unknown quantity");
+    if (!out) return fail(FDF_EINVAL, "out is NULL");
+    const size_t N3 = (size_t)c->p.n_grid * c->p.n_grid * c->p.n_grid;
+    double* grid = out_on_device ? out : c->dep;
+    FDF_CUDA(cudaMemsetAsync(grid, 0, N3 * 8, c->stream), "clearing the deposit grid");
+    const int64_t np = c->p.n_part;
+    const int64_t begin = species < 0 ? 0 : species * np;
+    const int64_t count = species < 0 ? c->n : np;
+    const double a = std::exp(c->lna(c->k));
+    int rc = timed(c, FDF_K_OTHER, "deposit", [&] {
+        return launch_deposit(c->stream, c->p.precision, c->st, c->n, begin, count, np > 0 ? np : 1, c->p.m_ev, a,
+                              c->T_ev, quantity, c->p.n_grid, c->p.box_mpc, grid);
+    });
+    if (rc) return rc;
+    if (!out_on_device)
+        FDF_CUDA(cudaMemcpyAsync(out, grid, N3 * 8, cudaMemcpyDeviceToHost, c->stream), "copy deposit");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_deposit");
+    return FDF_OK;
+}
+
+int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!out || !std::isfinite(lna)) return fail(FDF_EINVAL, "bad arguments");
+    const int N = c->p.n_grid;
+    const size_t N3 = (size_t)N * N * N;
+    const int buf = c->cur ^ 1;
+    int rc = build_fields(c, lna, c->G[buf]);
+    if (rc) return rc;
+    c->gk[buf] = -1;
+    double* dst = out;
+    if (!out_on_device) FDF_CUDA(cudaMalloc(&dst, 8 * N3 * 8), "allocating the field copy");
+    rc = timed(c, FDF_K_OTHER, "field export",
+               [&] { return launch_fields_to_f64(c->stream, c->p.precision, N, c->G[buf], dst); });
+    if (!rc && !out_on_device) {
+        cudaError_t e = cudaMemcpyAsync(out, dst, 8 * N3 * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy fields");
+    }
+    if (!out_on_device) cudaFree(dst);
+    if (rc) return rc;
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_build_fields");
+    return FDF_OK;
+}
+
+int fdf_set_fields(fdf_ctx* c, const double* fields, int32_t on_device)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!fields) {
+        c->frozen = false;
+        c->gk[0] = c->gk[1] = -1;
+        return FDF_OK;
+    }
+    const int N = c->p.n_grid;
+    const size_t N3 = (size_t)N * N * N;
+    if (!c->Gfrozen) FDF_CUDA(cudaMalloc(&c->Gfrozen, N3 * grid_bytes_per_cell(c->p.precision)), "allocating");
+    const double* src = fields;
+    double* tmp = nullptr;
+    if (!on_device) {
+        FDF_CUDA(cudaMalloc(&tmp, 8 * N3 * 8), "allocating");
+        cudaError_t e = cudaMemcpyAsync(tmp, fields, 8 * N3 * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_fail(e, "copy fields");
+        }
+        src = tmp;
+    }
+    int rc = timed(c, FDF_K_OTHER, "field import",
+                   [&] { return launch_fields_from_f64(c->stream, c->p.precision, N, src, c->Gfrozen); });
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "fdf_set_fields");
+    c->frozen = true;
+    return FDF_OK;
+}
+
+int fdf_state(fdf_ctx* c, int32_t* step, double* lna)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (step) *step = c->k;
+    if (lna) *lna = c->lna(c->k);
+    return FDF_OK;
+}
+
+int fdf_timing(fdf_ctx* c, int32_t enable)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (enable) {
+        FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_timing");
+        c->marks.clear();
+        c->pool_used = 0;
+    }
+    c->timing = enable != 0;
+    return FDF_OK;
+}
+
+int fdf_kernel_time(fdf_ctx* c, int32_t which, double* ms, int64_t* launches)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (which < 0 || which >= FDF_K_COUNT) return fail(FDF_EINVAL, "unknown kernel class");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_kernel_time");
+    double total = 0;
+    int64_t cnt = 0;
+    for (auto& m : c->marks) {
+        if (m.first != which) continue;
+        float t = 0;
+        FDF_CUDA(cudaEventElapsedTime(&t, m.second.first, m.second.second), "event time");
+        total += t;
+        ++cnt;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = cnt;
+    return FDF_OK;
+}
+
+int64_t fdf_launch_count(const fdf_ctx* c) { return c ? c->launches : 0; }
+
+const char* fdf_error_string(int code)
+{
+    switch (code) {
+        case FDF_OK: return "ok";
+        case FDF_EINVAL: return "invalid argument";
+        case FDF_ENOMEM: return "out of device memory";
+        case FDF_ECUDA: return "CUDA error";
+        case FDF_ESTATE: return "call out of order";
+        case FDF_ETIMEOUT: return "device wait timed out";
+        case FDF_ENAN: return "non-finite value";
+        case FDF_ENOSYS: return "not supported";
+        default: return "unknown error";
+    }
+}
+
+const char* fdf_last_error(void) { return g_last_error.c_str(); }
+
+void fdf_destroy(fdf_ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->Gfrozen) cudaFree(c->Gfrozen);
+    if (c->own_block && c->block) cudaFree(c->block);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// fdf_internal.cuh -- shared declarations of libfdf.so (device kernels and the
+// host context).  Nothing here is part of the C-ABI; include/fdf.h is.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/fdf.h"
+
+namespace fdf {
+
+constexpr int kMaxGL = 8;       // Gauss-Legendre nodes per step integral
+constexpr int kMaxSpecies = 4;
+constexpr int kSlots = 8;       // d psi (3), d phi (3), phi_dot, psi
+
+struct FF {                     // float-float: value = hi + lo, |lo| <= ulp(hi)/2
+    float hi, lo;
+};
+
+// Coefficients of one particle pass for one species.  Every integral is a sum
+// over Gauss-Legendre nodes a_j of the pass's interval in ln a:
+//   int g(a) dtau = sum_j W_j g(a_j),  W_j = w_j (dlna/2) / (a_j H(a_j)).
+struct SpeciesCoef {
+    // drift over [ln a_k, ln a_k+1]: D(q) = sum_j Wd_j / sqrt(q^2 + mud_j)
+    double Wd[kMaxGL];
+    double mud[kMaxGL];
+    FF Wd_sum;                  // sum_j Wd_j
+    FF mud_c;                   // mud at the centre node jc
+    float Wd_f[kMaxGL];
+    float dmud_f[kMaxGL];       // mud_j - mud_c
+    // kick over [lo, hi]: K_psi = sum Wk sqrt(q0^2 + muk), K_phi = sum Wk / sqrt(..)
+    double Wk[kMaxGL];
+    double muk[kMaxGL];
+    double dtau_k;
+    float Wk_f[kMaxGL];
+    float muk_f[kMaxGL];
+    float dtau_k_f;
+};
+
+struct PushArgs {
+    int64_t n;                  // particles in all species
+    int64_t n_part;             // particles per species
+    int n_gl;
+    int do_drift;
+    int do_kick;
+    int N;                      // grid side
+    double L, invL, invh;
+    FF fx_scale;                // 2^32 / L
+    SpeciesCoef sp[kMaxSpecies];
+};
+
+// Field-build arguments for one scale factor.
+struct FieldArgs {
+    int N, logN;
+    int nk, na;
+    double kf;                  // 2 pi / L
+    double lnk0, inv_dlnk;      // uniform ln k grid
+    int ia;                     // a-row of the tables below ln a (clamped)
+    double fa;                  // fraction between rows ia and ia+1
+    double aH;                  // a H(a) (multiplies dT_phi/dln a into phi_dot)
+    double amp0;                // sqrt(2 pi^2 A_s / V)
+    double half_nsm1;           // (n_s - 1) / 2
+    double lnkp;                // ln k_pivot
+    uint32_t key0, key1;        // Philox key (seed)
+    int fixed_amp;
+};
+
+// ----- kernel launchers (each returns cudaGetLastError()) -----------------
+
+// Pre-initial sampling of particles [0, n): X, q_sampled, |q_sampled|, id.
+cudaError_t launch_sample(cudaStream_t s, int64_t n, uint32_t key0, uint32_t key1, double T_ev, const double* cdf_t,
+                          const double* cdf_F, int ncdf, uint32_t* X, double* qs, double* pmag, uint32_t* id,
+                          int* flag);
+
+// Field build: three passes.  precision: FDF_PREC_*.  W0/W1 are two complex
+// work arrays of 4 N^3 elements (float2 or double2), G the gather grid.
+cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* tabs, const void* tw,
+                            void* W0);
+cudaError_t launch_fields_y(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W0,
+                            void* W1);
+cudaError_t launch_fields_x(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W1,
+                            void* G);
+// G (any precision) <-> [8][N^3] FP64.
+cudaError_t launch_fields_to_f64(cudaStream_t s, int precision, int N, const void* G, double* out);
+cudaError_t launch_fields_from_f64(cudaStream_t s, int precision, int N, const double* in, void* G);
+
+// Particle passes.
+struct ParticleState {
+    uint32_t* X;        // [3][n] fixed-point positions (split forms; sampler output in all forms)
+    float* q0f;         // [3][n] (split)
+    float* dqf;         // [3][n] (split)
+    double* xd;         // [3][n] (plain FP64 form)
+    double* qd;
+    double* q0d;
+    double* qs;         // [3][n] sampled momenta
+    double* pmag;       // [n]
+    uint32_t* id;       // [n]
+};
+
+cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t n_part,
+                           const double* m_ev, double a0, double tau0, int N, double L, const void* G);
+cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a, const void* G);
+// Particles [begin, begin + count) of an array of n; outputs in id order
+// (out index = id - begin).
+cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                          int64_t count, double L, double T_ev, double* x, double* q, double* w);
+cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                           int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
+                           int N, double L, double* grid);
+
+}  // namespace fdf

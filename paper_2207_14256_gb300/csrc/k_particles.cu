@@ -1,0 +1,464 @@
+// k_particles.cu -- the per-particle passes of the fastdf method (Elbers 2022):
+//   initial: the pre-initial momentum transform (eq:transform, Sec. 2.1);
+//   push:    one leapfrog pass of the separable equations of motion
+//            (eq:releq_approx, eq:geodesic_approx, Sec. 3.3): drift by the
+//            exact free-streaming integral for frozen q, periodic wrap,
+//            trilinear gather of the gradient grid, kick;
+//   export:  positions, momenta and delta-f weights w = 1 - fbar(q)/fbar(p)
+//            (Sec. 2.2) in particle-index order;
+//   deposit: the weighted CIC density estimate (eq:empirical_rho).
+//
+// Two state forms.  The plain form keeps x, q, q_0 in FP64 and reads an FP64
+// grid.  The split form keeps positions as 32-bit fixed-point fractions of the
+// box (the periodic wrap is the integer overflow), momenta as q = q_0 + dq
+// with both parts in FP32, and evaluates the drift integral in float-float so
+// that no FP64 instruction runs in the per-step pass.
+#include <cuda_bf16.h>
+
+#include "device_math.cuh"
+
+namespace fdf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+unsigned grid_for(int64_t n, int per_sm = 16)
+{
+    int64_t b = (n + kThreads - 1) / kThreads;
+    const int64_t cap = 152LL * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+// ---- grid reads ------------------------------------------------------------
+template <typename Gt> struct Cell;
+template <> struct Cell<float> {
+    __device__ static void load(const float* G, uint32_t c, float v[8])
+    {
+        const float4* g = reinterpret_cast<const float4*>(G) + 2 * (size_t)c;
+        const float4 a = __ldg(g), b = __ldg(g + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+};
+template <> struct Cell<__nv_bfloat16> {
+    __device__ static void load(const __nv_bfloat16* G, uint32_t c, float v[8])
+    {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(G) + c);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __uint_as_float(w[k] << 16);
+            v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+    }
+};
+
+// Trilinear (order r = 1, Sec. 4) read of the 8 slots at a fixed-point position.
+template <typename Gt>
+__device__ __forceinline__ void gather_fixed(const Gt* __restrict__ G, uint32_t N, uint32_t X0, uint32_t X1,
+                                             uint32_t X2, float g[8])
+{
+    uint32_t ix[2], iy[2], iz[2];
+    float fx, fy, fz;
+    fixed_cell(X0, N, ix[0], ix[1], fx);
+    fixed_cell(X1, N, iy[0], iy[1], fy);
+    fixed_cell(X2, N, iz[0], iz[1], fz);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) g[s] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+        const float w = (cx ? fx : 1.f - fx) * (cy ? fy : 1.f - fy) * (cz ? fz : 1.f - fz);
+        float v[8];
+        Cell<Gt>::load(G, (iz[cz] * N + iy[cy]) * N + ix[cx], v);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) g[s] = fmaf(w, v[s], g[s]);
+    }
+}
+
+// FP64 read at an FP64 position in [0, L).
+__device__ __forceinline__ void gather_f64(const double* __restrict__ G, int N, double invh, const double x[3],
+                                           double g[8])
+{
+    int i0[3], i1[3];
+    double f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double u = x[d] * invh;
+        const double fl = floor(u);
+        f[d] = u - fl;
+        int i = (int)fl;
+        if (i >= N) i -= N;
+        if (i < 0) i += N;
+        i0[d] = i;
+        i1[d] = i + 1 == N ? 0 : i + 1;
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) g[s] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+        const double w = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) * (cz ? f[2] : 1.0 - f[2]);
+        const size_t cell = ((size_t)(cz ? i1[2] : i0[2]) * N + (cy ? i1[1] : i0[1])) * N + (cx ? i1[0] : i0[0]);
+        const double2* p = reinterpret_cast<const double2*>(G) + 4 * cell;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double2 v = __ldg(p + k);
+            g[2 * k] += w * v.x;
+            g[2 * k + 1] += w * v.y;
+        }
+    }
+}
+
+__device__ __forceinline__ double wrap_f64(double x, double L, double invL)
+{
+    double y = x - L * floor(x * invL);
+    if (y < 0.0) y += L;
+    if (y >= L) y -= L;
+    return y;
+}
+
+// Round a float-float count of position quanta to the nearest integer, modulo
+// 2^32.  A hi part beyond +-2^31 is a multiple of 256 and is first reduced by an
+// exact multiple of 2^32; what remains converts to int32 exactly, and the
+// fractional part of hi plus lo adds the last quanta.
+__device__ __forceinline__ uint32_t round_mod32(FF d)
+{
+    float h = d.hi;
+    if (fabsf(h) >= 2147483648.f)
+        h = __fsub_rn(h, __fmul_rn(4294967296.f, rintf(__fmul_rn(h, 2.3283064365386963e-10f))));
+    const int i = __float2int_rn(h);
+    const int i2 = __float2int_rn(__fadd_rn(__fsub_rn(h, (float)i), d.lo));
+    return (uint32_t)i + (uint32_t)i2;
+}
+
+// |q| with the sampler's exactly rounded evaluation order, so that an
+// untouched momentum reproduces p = |q_sampled| bit for bit.
+__device__ __forceinline__ double norm3_rn(const double q[3])
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])), __dmul_rn(q[2], q[2])));
+}
+
+struct Masses {
+    double m[kMaxSpecies];
+};
+
+// ---- initial transform -----------------------------------------------------
+// q_i <- q_i (1 - psi/2) - (eps tau_0 / 6) d_i psi  (eq:transform with delta = -2 psi,
+// theta = k^2 tau psi / 2, nu = 4, omega = 4/3), eps = sqrt(p^2 + m^2 a_0^2).
+template <int Prec, typename Gt>
+__global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t n, int64_t n_part, Masses ms,
+                                                      double a0, double tau0, int N, double L,
+                                                      const Gt* __restrict__ G)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double m = ms.m[i / n_part];
+        const uint32_t X0 = st.X[i], X1 = st.X[n + i], X2 = st.X[2 * n + i];
+        double g[8];
+        double x[3];
+        x[0] = L * ((double)X0 * 2.3283064365386963e-10);
+        x[1] = L * ((double)X1 * 2.3283064365386963e-10);
+        x[2] = L * ((double)X2 * 2.3283064365386963e-10);
+        if constexpr (Prec == FDF_PREC_F64) {
+            gather_f64(reinterpret_cast<const double*>(G), N, (double)N / L, x, g);
+        } else {
+            float gf[8];
+            gather_fixed<Gt>(G, (uint32_t)N, X0, X1, X2, gf);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) g[s] = (double)gf[s];
+        }
+        const double p = st.pmag[i];
+        const double eps = sqrt(p * p + m * m * a0 * a0);
+        const double c = eps * tau0 / 6.0;
+        const double r = 1.0 - g[7] / 2.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double q = st.qs[d * n + i] * r - c * g[d];
+            if constexpr (Prec == FDF_PREC_F64) {
+                st.xd[d * n + i] = x[d];
+                st.qd[d * n + i] = q;
+                st.q0d[d * n + i] = q;
+            } else {
+                const float hi = (float)q;
+                st.q0f[d * n + i] = hi;
+                st.dqf[d * n + i] = (float)(q - (double)hi);
+            }
+        }
+    }
+}
+
+// ---- the fused leapfrog pass, split form -------------------------------------
+template <typename Gt>
+__global__ void __launch_bounds__(kThreads) k_push_split(const __grid_constant__ PushArgs a, uint32_t* __restrict__ X,
+                                                         const float* __restrict__ q0f, float* __restrict__ dqf,
+                                                         const Gt* __restrict__ G)
+{
+    const int64_t n = a.n;
+    const uint32_t N = (uint32_t)a.N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const SpeciesCoef& c = a.sp[i / a.n_part];
+        uint32_t X0 = X[i], X1 = X[n + i], X2 = X[2 * n + i];
+        const float qa = q0f[i], qb = q0f[n + i], qc = q0f[2 * n + i];
+        float da = dqf[i], db = dqf[n + i], dc = dqf[2 * n + i];
+        if (a.do_drift) {
+            // q = q_0 + dq exactly, as float-float per component
+            FF t0, t1, t2;
+            two_sum(qa, da, t0.hi, t0.lo);
+            two_sum(qb, db, t1.hi, t1.lo);
+            two_sum(qc, dc, t2.hi, t2.lo);
+            // |q|^2 in float-float
+            FF S = ff_add(ff_add(ff_mul(t0, t0), ff_mul(t1, t1)), ff_mul(t2, t2));
+            // D = sum_j Wd_j (S + mu_j)^-1/2 = r_c [sum_j Wd_j + sum_j Wd_j g(delta_j)],
+            // r_c = (S + mu_c)^-1/2, delta_j = (mu_j - mu_c) r_c^2, g(d) = (1+d)^-1/2 - 1
+            const FF r = ff_rsqrt(ff_add(S, c.mud_c));
+            const float r2 = r.hi * r.hi;
+            float corr = 0.f;
+            for (int j = 0; j < a.n_gl; ++j) {
+                const float d = c.dmud_f[j] * r2;
+                const float sq = sqrtf(1.f + d);
+                corr = fmaf(c.Wd_f[j], -d / (sq * (1.f + sq)), corr);
+            }
+            FF A;
+            fast_two_sum(c.Wd_sum.hi, __fadd_rn(c.Wd_sum.lo, corr), A.hi, A.lo);
+            const FF D = ff_mul(ff_mul(r, A), a.fx_scale);  // position quanta per eV of momentum
+            X0 += round_mod32(ff_mul(D, t0));
+            X1 += round_mod32(ff_mul(D, t1));
+            X2 += round_mod32(ff_mul(D, t2));
+        }
+        if (a.do_kick) {
+            float g[8];
+            gather_fixed<Gt>(G, N, X0, X1, X2, g);
+            const float q02 = qa * qa + qb * qb + qc * qc;
+            float Kpsi = 0.f, Kphi = 0.f;
+            for (int j = 0; j < a.n_gl; ++j) {
+                const float e2 = q02 + c.muk_f[j];
+                const float ie = rsqrtf(e2);
+                Kpsi = fmaf(c.Wk_f[j], e2 * ie, Kpsi);
+                Kphi = fmaf(c.Wk_f[j], ie, Kphi);
+            }
+            const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
+            const float b = qdphi * Kphi + g[6] * c.dtau_k_f;
+            const float a2 = q02 * Kphi;
+            da += -g[0] * Kpsi - g[3] * a2 + qa * b;
+            db += -g[1] * Kpsi - g[4] * a2 + qb * b;
+            dc += -g[2] * Kpsi - g[5] * a2 + qc * b;
+            dqf[i] = da;
+            dqf[n + i] = db;
+            dqf[2 * n + i] = dc;
+        }
+        if (a.do_drift) {
+            X[i] = X0;
+            X[n + i] = X1;
+            X[2 * n + i] = X2;
+        }
+    }
+}
+
+// ---- the fused leapfrog pass, plain FP64 form --------------------------------
+__global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ PushArgs a, double* __restrict__ xd, double* __restrict__ qd,
+                                                       const double* __restrict__ q0d, const double* __restrict__ G)
+{
+    const int64_t n = a.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const SpeciesCoef& c = a.sp[i / a.n_part];
+        double x[3] = {xd[i], xd[n + i], xd[2 * n + i]};
+        double q[3] = {qd[i], qd[n + i], qd[2 * n + i]};
+        const double q0[3] = {q0d[i], q0d[n + i], q0d[2 * n + i]};
+        if (a.do_drift) {
+            const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+            double D = 0.0;
+            for (int j = 0; j < a.n_gl; ++j) D += c.Wd[j] / sqrt(qq + c.mud[j]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) x[d] = wrap_f64(x[d] + D * q[d], a.L, a.invL);
+            xd[i] = x[0];
+            xd[n + i] = x[1];
+            xd[2 * n + i] = x[2];
+        }
+        if (a.do_kick) {
+            double g[8];
+            gather_f64(G, a.N, a.invh, x, g);
+            const double q02 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+            double Kpsi = 0.0, Kphi = 0.0;
+            for (int j = 0; j < a.n_gl; ++j) {
+                const double e = sqrt(q02 + c.muk[j]);
+                Kpsi += c.Wk[j] * e;
+                Kphi += c.Wk[j] / e;
+            }
+            const double qdphi = q0[0] * g[3] + q0[1] * g[4] + q0[2] * g[5];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                q[d] += -g[d] * Kpsi - g[3 + d] * (q02 * Kphi) + q0[d] * (qdphi * Kphi) + q0[d] * (g[6] * c.dtau_k);
+            qd[i] = q[0];
+            qd[n + i] = q[1];
+            qd[2 * n + i] = q[2];
+        }
+    }
+}
+
+// ---- state read-back ------------------------------------------------------------
+template <int Prec>
+__device__ __forceinline__ void load_state(const ParticleState& st, int64_t n, int64_t i, double L, double x[3],
+                                           double q[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if constexpr (Prec == FDF_PREC_F64) {
+            x[d] = st.xd[d * n + i];
+            q[d] = st.qd[d * n + i];
+        } else {
+            x[d] = L * ((double)st.X[d * n + i] * 2.3283064365386963e-10);
+            q[d] = (double)st.q0f[d * n + i] + (double)st.dqf[d * n + i];
+        }
+    }
+}
+
+// delta-f weight (Sec. 2.2), w = 1 - fbar(|q|)/fbar(p), in the cancellation-free form
+// w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)).
+__device__ __forceinline__ double dfweight(double qm, double p, double T)
+{
+    return -expm1((p - qm) / T) / (1.0 + exp(-qm / T));
+}
+
+template <int Prec>
+__global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n, int64_t begin, int64_t count,
+                                                     double L, double T, double* __restrict__ xo,
+                                                     double* __restrict__ qo, double* __restrict__ wo)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = begin + j;
+        const int64_t o = (int64_t)st.id[i] - begin;
+        double x[3], q[3];
+        load_state<Prec>(st, n, i, L, x, q);
+        if (xo) {
+            xo[o] = x[0];
+            xo[count + o] = x[1];
+            xo[2 * count + o] = x[2];
+        }
+        if (qo) {
+            qo[o] = q[0];
+            qo[count + o] = q[1];
+            qo[2 * count + o] = q[2];
+        }
+        if (wo) wo[o] = dfweight(norm3_rn(q), st.pmag[i], T);
+    }
+}
+
+template <int Prec>
+__global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t n, int64_t begin, int64_t count,
+                                                      int64_t n_part, Masses ms, double a, double T, int quantity,
+                                                      int N, double L, double* __restrict__ grid)
+{
+    const double invh = (double)N / L;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = begin + j;
+        const double m = ms.m[i / n_part];
+        double x[3], q[3];
+        load_state<Prec>(st, n, i, L, x, q);
+        const double qm = norm3_rn(q);
+        const double eps = sqrt(qm * qm + m * m * a * a);
+        double v = 1.0;
+        if (quantity == FDF_Q_W_EPS) v = dfweight(qm, st.pmag[i], T) * eps;
+        else if (quantity == FDF_Q_W) v = dfweight(qm, st.pmag[i], T);
+        else if (quantity == FDF_Q_EPS) v = eps;
+        int i0[3], i1[3];
+        double f[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if constexpr (Prec == FDF_PREC_F64) {
+                const double u = x[d] * invh;
+                const double fl = floor(u);
+                f[d] = u - fl;
+                int ii = (int)fl;
+                if (ii >= N) ii -= N;
+                if (ii < 0) ii += N;
+                i0[d] = ii;
+            } else {
+                const uint32_t Xd = st.X[d * n + i];
+                i0[d] = (int)__umulhi(Xd, (uint32_t)N);
+                f[d] = (double)(Xd * (uint32_t)N) * 2.3283064365386963e-10;
+            }
+            i1[d] = i0[d] + 1 == N ? 0 : i0[d] + 1;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+            const double w = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) * (cz ? f[2] : 1.0 - f[2]);
+            const size_t cell =
+                ((size_t)(cz ? i1[2] : i0[2]) * N + (cy ? i1[1] : i0[1])) * N + (cx ? i1[0] : i0[0]);
+            atomicAdd(grid + cell, w * v);
+        }
+    }
+}
+
+Masses masses_of(const double* m_ev)
+{
+    Masses ms;
+    for (int s = 0; s < kMaxSpecies; ++s) ms.m[s] = m_ev[s];
+    return ms;
+}
+
+}  // namespace
+
+cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t n_part,
+                           const double* m_ev, double a0, double tau0, int N, double L, const void* G)
+{
+    if (n <= 0) return cudaSuccess;
+    const unsigned b = grid_for(n);
+    const Masses ms = masses_of(m_ev);
+    if (precision == FDF_PREC_F64)
+        k_initial<FDF_PREC_F64, double><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, N, L, (const double*)G);
+    else if (precision == FDF_PREC_F32)
+        k_initial<FDF_PREC_F32, float><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, N, L, (const float*)G);
+    else
+        k_initial<FDF_PREC_BF16, __nv_bfloat16>
+            <<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, N, L, (const __nv_bfloat16*)G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a, const void* G)
+{
+    if (a.n <= 0) return cudaSuccess;
+    const unsigned b = grid_for(a.n);
+    if (precision == FDF_PREC_F64)
+        k_push_f64<<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d, (const double*)G);
+    else if (precision == FDF_PREC_F32)
+        k_push_split<float><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf, (const float*)G);
+    else
+        k_push_split<__nv_bfloat16><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf, (const __nv_bfloat16*)G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                          int64_t count, double L, double T_ev, double* x, double* q, double* w)
+{
+    if (count <= 0) return cudaSuccess;
+    const unsigned b = grid_for(count);
+    if (precision == FDF_PREC_F64)
+        k_export<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
+    else
+        k_export<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                           int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
+                           int N, double L, double* grid)
+{
+    if (count <= 0) return cudaSuccess;
+    const unsigned b = grid_for(count);
+    const Masses ms = masses_of(m_ev);
+    if (precision == FDF_PREC_F64)
+        k_deposit<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, N, L,
+                                                        grid);
+    else
+        k_deposit<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, N, L,
+                                                        grid);
+    return cudaGetLastError();
+}
+
+}  // namespace fdf

@@ -1,0 +1,94 @@
+// k_sample.cu -- pre-initial particle sampling (Sec. 2.1 of Elbers 2022):
+// positions uniform in the periodic box, |q| from the Fermi-Dirac distribution
+// fbar(q) = 1/(1 + e^{q/T}) by inversion of its tabulated CDF, and an
+// isotropic direction by rejection from the cube.
+//
+// Every particle is addressed by its global index g (species-major) so the
+// draw does not depend on the launch shape.  Philox4x32-10 keyed by the seed
+// with counter (g_lo, g_hi, stream, attempt):
+//   stream 0: X_c = word c (c = 0, 1, 2); x_c = L X_c / 2^32
+//   stream 1: u from words 0,1 (53 bits) -> t = F^{-1}(u) -> |q| = T t
+//   streams 2, 3 (attempt a): v = 2 u - 1 from (2: words 0,1), (2: words 2,3),
+//     (3: words 0,1); accept 1e-300 < |v|^2 <= 1; n = v / |v|.
+// Only correctly rounded IEEE operations are used (explicit _rn intrinsics, so
+// no FMA contraction), which makes the result exact and reproducible.
+#include "device_math.cuh"
+
+namespace fdf {
+
+__device__ __forceinline__ double u53(uint32_t w0, uint32_t w1)
+{
+    return __dmul_rn(__dadd_rn(__dmul_rn((double)(w0 >> 5), 67108864.0), (double)(w1 >> 6)),
+                     1.1102230246251565404e-16);  // 2^-53
+}
+
+__device__ __forceinline__ double fd_inverse(const double* __restrict__ t, const double* __restrict__ F, int n,
+                                             double u)
+{
+    if (u >= F[n - 1]) return t[n - 1];
+    int lo = 0, hi = n - 1;  // F[lo] <= u < F[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (F[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    const double du = __dsub_rn(u, F[lo]);
+    const double dt = __dsub_rn(t[lo + 1], t[lo]);
+    const double dF = __dsub_rn(F[lo + 1], F[lo]);
+    return __dadd_rn(t[lo], __ddiv_rn(__dmul_rn(du, dt), dF));
+}
+
+__global__ void __launch_bounds__(256) k_sample(int64_t n, uint32_t key0, uint32_t key1, double T_ev,
+                                                const double* __restrict__ cdf_t, const double* __restrict__ cdf_F,
+                                                int ncdf, uint32_t* __restrict__ X, double* __restrict__ qs,
+                                                double* __restrict__ pmag, uint32_t* __restrict__ id, int* flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t g0 = (uint32_t)i, g1 = (uint32_t)((uint64_t)i >> 32);
+        uint4 w = philox4x32_10(make_uint4(g0, g1, 0u, 0u), key0, key1);
+        X[i] = w.x;
+        X[n + i] = w.y;
+        X[2 * n + i] = w.z;
+        w = philox4x32_10(make_uint4(g0, g1, 1u, 0u), key0, key1);
+        const double qmag = __dmul_rn(T_ev, fd_inverse(cdf_t, cdf_F, ncdf, u53(w.x, w.y)));
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, r2 = 0.0;
+        bool ok = false;
+        for (uint32_t att = 0; att < 64u && !ok; ++att) {
+            const uint4 a = philox4x32_10(make_uint4(g0, g1, 2u, att), key0, key1);
+            const uint4 b = philox4x32_10(make_uint4(g0, g1, 3u, att), key0, key1);
+            v0 = __dadd_rn(__dmul_rn(2.0, u53(a.x, a.y)), -1.0);
+            v1 = __dadd_rn(__dmul_rn(2.0, u53(a.z, a.w)), -1.0);
+            v2 = __dadd_rn(__dmul_rn(2.0, u53(b.x, b.y)), -1.0);
+            r2 = __dadd_rn(__dadd_rn(__dmul_rn(v0, v0), __dmul_rn(v1, v1)), __dmul_rn(v2, v2));
+            ok = (r2 > 1e-300) && (r2 <= 1.0);
+        }
+        if (!ok) {
+            atomicOr(flag, 1);
+            r2 = 1.0;
+            v0 = 1.0;
+            v1 = v2 = 0.0;
+        }
+        const double s = __dsqrt_rn(r2);
+        const double q0 = __dmul_rn(qmag, __ddiv_rn(v0, s));
+        const double q1 = __dmul_rn(qmag, __ddiv_rn(v1, s));
+        const double q2 = __dmul_rn(qmag, __ddiv_rn(v2, s));
+        qs[i] = q0;
+        qs[n + i] = q1;
+        qs[2 * n + i] = q2;
+        pmag[i] = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
+        id[i] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_sample(cudaStream_t s, int64_t n, uint32_t key0, uint32_t key1, double T_ev, const double* cdf_t,
+                          const double* cdf_F, int ncdf, uint32_t* X, double* qs, double* pmag, uint32_t* id,
+                          int* flag)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_sample<<<(unsigned)blocks, 256, 0, s>>>(n, key0, key1, T_ev, cdf_t, cdf_F, ncdf, X, qs, pmag, id, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace fdf

@@ -32,7 +32,7 @@ def base_params(**over) -> dict:
     h = 0.67
     p = dict(box=1000.0, n_part=32 ** 3, n_grid=32, n_species=1, m_ev=[0.1], T_K=1.95, z_start=1e9, z_end=31.0,
              n_steps=100, flags=0, seed=1, h=h, omega_m=0.31, omega_r=omega_radiation(h), A_s=2.1e-9, n_s=0.965,
-             k_pivot=0.05, precision=0, n_gl=4, sort_every=0)
+             k_pivot=0.05, precision=0, n_gl=0, sort_every=0)
     p.update(over)
     return p
 

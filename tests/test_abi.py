@@ -1,0 +1,113 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry point
+that include/fdf.h declares; the ctypes structures match the C layout; host-only
+validation works without a device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fdf():
+    from paper_2207_14256_gb300 import build
+    from paper_2207_14256_gb300 import fdf as F
+
+    build.build()
+    F.lib()
+    return F
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fdf.h")).read()
+    return sorted(set(re.findall(r"^FDF_API [^(]*?\b(fdf_\w+)\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(fdf):
+    names = declared_symbols()
+    assert len(names) >= 16
+    L = C.CDLL(fdf.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", fdf.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (fdf_\w+)$", out, re.M))
+    assert set(names) <= exported
+    # nothing else of ours leaks out of the library
+    assert {n for n in exported if n.startswith("fdf")} == set(names)
+
+
+def _c_offsets():
+    code = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "fdf.h"
+#define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("fdf_params %zu\n", sizeof(fdf_params));
+  printf("fdf_tables %zu\n", sizeof(fdf_tables));
+  O(fdf_params, box_mpc); O(fdf_params, n_part); O(fdf_params, n_grid); O(fdf_params, n_species);
+  O(fdf_params, m_ev); O(fdf_params, T_nu_K); O(fdf_params, z_start); O(fdf_params, z_end);
+  O(fdf_params, n_steps); O(fdf_params, precision); O(fdf_params, seed); O(fdf_params, h);
+  O(fdf_params, omega_m); O(fdf_params, omega_r); O(fdf_params, A_s); O(fdf_params, n_s);
+  O(fdf_params, k_pivot); O(fdf_params, flags); O(fdf_params, n_gl); O(fdf_params, sort_every);
+  O(fdf_tables, nk); O(fdf_tables, na); O(fdf_tables, lnk); O(fdf_tables, lna); O(fdf_tables, T_psi);
+  O(fdf_tables, T_phi); O(fdf_tables, dTphi_dlna); O(fdf_tables, ncdf); O(fdf_tables, cdf_t);
+  O(fdf_tables, cdf_F);
+  return 0;
+}
+'''
+    tmp = os.path.join(ROOT, "_build_abi_check")
+    os.makedirs(tmp, exist_ok=True)
+    src = os.path.join(tmp, "layout.c")
+    exe = os.path.join(tmp, "layout")
+    open(src, "w").write(code)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    return dict((l.split()[0], int(l.split()[1])) for l in out.strip().splitlines())
+
+
+def test_struct_layout_matches_c(fdf):
+    c = _c_offsets()
+    assert c["fdf_params"] == C.sizeof(fdf.fdf_params)
+    assert c["fdf_tables"] == C.sizeof(fdf.fdf_tables)
+    for name, cls in (("fdf_params", fdf.fdf_params), ("fdf_tables", fdf.fdf_tables)):
+        for f in cls._fields_:
+            key = "%s.%s" % (name, f[0])
+            if key in c:
+                assert getattr(cls, f[0]).offset == c[key], key
+
+
+def test_host_only_calls(fdf, inputs):
+    assert fdf.fdf_error_string(0) == "ok"
+    assert fdf.fdf_error_string(-4) == "call out of order"
+    p = fdf.make_params(inputs.config("c3_3x256"))
+    b = fdf.fdf_footprint(p)
+    n = 3 * 256 ** 3
+    assert b > n * (12 + 12 + 12 + 24 + 8 + 4)
+    assert b < 16 * 2 ** 30
+    bad = fdf.make_params(inputs.config("c1_32", n_grid=48))
+    with pytest.raises(fdf.FdfError) as e:
+        fdf.fdf_footprint(bad)
+    assert e.value.code == fdf.FDF_EINVAL
+    assert "power of two" in fdf.fdf_last_error()
+    bad = fdf.make_params(inputs.config("c1_32", z_end=2e9))
+    with pytest.raises(fdf.FdfError):
+        fdf.fdf_footprint(bad)
+    bad = fdf.make_params(inputs.config("c1_32", n_species=5, m_ev=[0.1] * 4))
+    with pytest.raises(fdf.FdfError):
+        fdf.fdf_footprint(bad)
+
+
+def test_create_rejects_bad_tables_before_touching_the_device(fdf, inputs, c1_tables):
+    p = inputs.config("c1_32")
+    t = dict(c1_tables)
+    t["lnk"] = t["lnk"].copy()
+    t["lnk"][5] += 0.01  # not uniform
+    P = fdf.make_params(p)
+    T, keep = fdf.make_tables(t)
+    with pytest.raises(fdf.FdfError) as e:
+        fdf.fdf_create(P, T)
+    assert e.value.code == fdf.FDF_EINVAL
