@@ -184,6 +184,28 @@ FDF_API int fdf_get_initial(fdf_ctx* c, int32_t species, uint32_t* X, double* q_
  * phi_dot = a H d phi / d ln a.  Field convention f(x) = sum_n f_n e^{i k.x}. */
 FDF_API int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device);
 
+/* fdf_build_fields without a context and without allocating: for callers that
+ * must not allocate device memory, such as a simulation code embedding this
+ * library whose own allocator owns the device budget, or a serving loop that
+ * forbids cudaMalloc/cudaFree after start-up because those calls synchronise
+ * the device and fragment its memory.  The paper has no counterpart; this is
+ * an interface convenience.
+ *  p, t: as for fdf_create (host memory; t's arrays are uploaded on each call,
+ *  cdf_t and cdf_F are not used).  lna: ln a of the fields.  out: DEVICE memory
+ *  of 8 N^3 doubles, written as by fdf_build_fields.  stream: a cudaStream_t or
+ *  NULL.  The call synchronises that stream before returning.
+ *  Work arrays live in one static device array of FDF_NOALLOC_SCRATCH_BYTES
+ *  that every GPU loading the library holds until the process exits; the call
+ *  performs no cudaMalloc or cudaFree.  FDF_EINVAL, with a message naming both
+ *  sizes, when the grid needs more scratch than that (n_grid <= 64 in FP32,
+ *  <= 32 in FP64).  The first call on each device looks up the array's device
+ *  address with that device current; make that first call before any stream
+ *  capture.  All calls share the one array and overwrite it: calls that
+ *  overlap on the GPU (other host threads, other streams) race. */
+#define FDF_NOALLOC_SCRATCH_BYTES (20u << 20)
+FDF_API int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t, double lna, double* out,
+                                     void* stream);
+
 /* Test hook: freeze the fields.  fields[8][N^3] (same layout as
  * fdf_build_fields) replace the per-step grid build for every later call;
  * fields = NULL returns to building them. */

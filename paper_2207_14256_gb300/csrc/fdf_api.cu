@@ -25,11 +25,7 @@ namespace {
 
 thread_local std::string g_last_error;
 
-int fail(int code, const std::string& msg)
-{
-    g_last_error = msg;
-    return code;
-}
+int fail(int code, const std::string& msg) { return fdf::set_error(code, msg.c_str()); }
 
 constexpr double kC_over_H100 = 2997.92458;  // c / (100 km/s/Mpc) in Mpc
 constexpr double kBoltzmann_eV = 8.617333262e-5;
@@ -144,7 +140,15 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     return L;
 }
 
-int validate(const fdf_params* p)
+}  // namespace
+
+int fdf::set_error(int code, const char* msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int fdf::validate_params(const fdf_params* p)
 {
     if (!p) return fail(FDF_EINVAL, "params is NULL");
     if (!(p->box_mpc > 0) || !std::isfinite(p->box_mpc)) return fail(FDF_EINVAL, "box_mpc must be > 0");
@@ -172,7 +176,7 @@ int validate(const fdf_params* p)
     return FDF_OK;
 }
 
-bool uniform_grid(const double* v, int n, double* v0, double* dv)
+bool fdf::uniform_grid(const double* v, int n, double* v0, double* dv)
 {
     if (n < 2) return false;
     const double d = (v[n - 1] - v[0]) / (n - 1);
@@ -184,6 +188,8 @@ bool uniform_grid(const double* v, int n, double* v0, double* dv)
     return true;
 }
 
+namespace {
+int validate(const fdf_params* p) { return fdf::validate_params(p); }
 }  // namespace
 
 struct fdf_ctx {
@@ -351,34 +357,7 @@ void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, do
 
 int build_fields(fdf_ctx* c, double lna, void* G)
 {
-    FieldArgs a{};
-    a.N = c->p.n_grid;
-    a.logN = ilog2(a.N);
-    a.nk = c->nk;
-    a.na = c->na;
-    a.kf = 2.0 * kPi / c->p.box_mpc;
-    a.lnk0 = c->lnk0;
-    a.inv_dlnk = 1.0 / c->dlnk;
-    double pos = (lna - c->lnat0) / c->dlnat;
-    if (pos <= 0) {
-        a.ia = 0;
-        a.fa = 0;
-    } else if (pos >= c->na - 1) {
-        a.ia = c->na - 2;
-        a.fa = 1;
-    } else {
-        a.ia = (int)pos;
-        a.fa = pos - a.ia;
-    }
-    const double aa = std::exp(lna);
-    a.aH = aa * c->hubble(aa);
-    const double V = c->p.box_mpc * c->p.box_mpc * c->p.box_mpc;
-    a.amp0 = std::sqrt(2.0 * kPi * kPi * c->p.A_s / V);
-    a.half_nsm1 = 0.5 * (c->p.n_s - 1.0);
-    a.lnkp = std::log(c->p.k_pivot);
-    a.key0 = (uint32_t)c->p.seed;
-    a.key1 = (uint32_t)(c->p.seed >> 32);
-    a.fixed_amp = (c->p.flags & FDF_FLAG_FIXED_AMPLITUDE) ? 1 : 0;
+    const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
     const int prec = c->p.precision;
     int rc = timed(c, FDF_K_FIELDS_Z, "fields z pass",
                    [&] { return launch_fields_z(c->stream, prec, a, c->tabs, c->tw, c->W0); });
@@ -398,6 +377,43 @@ int push(fdf_ctx* c, const PushArgs& a, const void* G)
 const void* grid_for_step(fdf_ctx* c, int buf) { return c->frozen ? c->Gfrozen : c->G[buf]; }
 
 }  // namespace
+
+FieldArgs fdf::make_field_args(const fdf_params& p, int nk, int na, double lnk0, double dlnk, double lnat0,
+                               double dlnat, double lna)
+{
+    FieldArgs a{};
+    a.N = p.n_grid;
+    a.logN = ilog2(a.N);
+    a.nk = nk;
+    a.na = na;
+    a.kf = 2.0 * kPi / p.box_mpc;
+    a.lnk0 = lnk0;
+    a.inv_dlnk = 1.0 / dlnk;
+    const double pos = (lna - lnat0) / dlnat;
+    if (pos <= 0) {
+        a.ia = 0;
+        a.fa = 0;
+    } else if (pos >= na - 1) {
+        a.ia = na - 2;
+        a.fa = 1;
+    } else {
+        a.ia = (int)pos;
+        a.fa = pos - a.ia;
+    }
+    const double aa = std::exp(lna);
+    const double H0 = p.h / kC_over_H100;
+    const double H = H0 * std::sqrt(p.omega_r / (aa * aa * aa * aa) + p.omega_m / (aa * aa * aa) +
+                                    (1.0 - p.omega_m - p.omega_r));
+    a.aH = aa * H;
+    const double V = p.box_mpc * p.box_mpc * p.box_mpc;
+    a.amp0 = std::sqrt(2.0 * kPi * kPi * p.A_s / V);
+    a.half_nsm1 = 0.5 * (p.n_s - 1.0);
+    a.lnkp = std::log(p.k_pivot);
+    a.key0 = (uint32_t)p.seed;
+    a.key1 = (uint32_t)(p.seed >> 32);
+    a.fixed_amp = (p.flags & FDF_FLAG_FIXED_AMPLITUDE) ? 1 : 0;
+    return a;
+}
 
 extern "C" {
 

@@ -65,6 +65,13 @@ struct FieldArgs {
     int fixed_amp;
 };
 
+// ----- host helpers shared by the entry points (fdf_api.cu) ----------------
+int set_error(int code, const char* msg);       // records the message fdf_last_error() returns
+int validate_params(const fdf_params* p);       // FDF_OK or FDF_EINVAL with a message
+bool uniform_grid(const double* v, int n, double* v0, double* dv);
+FieldArgs make_field_args(const fdf_params& p, int nk, int na, double lnk0, double dlnk, double lnat0,
+                          double dlnat, double lna);
+
 // ----- kernel launchers (each returns cudaGetLastError()) -----------------
 
 // Pre-initial sampling of particles [0, n): X, q_sampled, |q_sampled|, id.

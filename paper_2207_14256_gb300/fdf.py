@@ -93,6 +93,7 @@ def lib():
             "fdf_get_initial": (C.c_int, [_V, C.c_int32, _V, _V, _V, C.c_int32]),
             "fdf_build_fields": (C.c_int, [_V, C.c_double, _V, C.c_int32]),
             "fdf_set_fields": (C.c_int, [_V, _V, C.c_int32]),
+            "fdf_build_fields_noalloc": (C.c_int, [P, T, C.c_double, _V, _V]),
             "fdf_state": (C.c_int, [_V, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
             "fdf_timing": (C.c_int, [_V, C.c_int32]),
             "fdf_kernel_time": (C.c_int, [_V, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -222,6 +223,17 @@ def fdf_get_initial(ctx, species, X=None, q_sampled=None, p=None):
 def fdf_build_fields(ctx, lna, out):
     p, dev = _ptr(out)
     _check(lib().fdf_build_fields(ctx, float(lna), p, dev), "fdf_build_fields")
+    return out
+
+
+def fdf_build_fields_noalloc(params, tables, lna, out, stream=None):
+    """out: a CUDA tensor of 8 N^3 float64 (the entry point allocates nothing)."""
+    p, dev = _ptr(out)
+    if not dev:
+        raise ValueError("fdf_build_fields_noalloc writes device memory: pass a CUDA tensor")
+    s = getattr(stream, "cuda_stream", stream)
+    _check(lib().fdf_build_fields_noalloc(C.byref(params), C.byref(tables), float(lna), p, s),
+           "fdf_build_fields_noalloc")
     return out
 
 
