@@ -118,6 +118,9 @@ def bench_ours(args, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     p = I.config(args.workload, seed=I.config(args.workload)["seed"] + 1000 * rank)
+    if args.n_species:
+        p["n_species"] = args.n_species
+        p["m_ev"] = (p["m_ev"] * 4)[:args.n_species]
     tables = I.transfer_tables(p)
     stream = torch.cuda.Stream(device=dev)
     P = fdf.make_params(p)
@@ -254,6 +257,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--n-species", type=int, default=0,
+                    help="override the species count (smaller device footprint for profiler captures)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -83,7 +83,8 @@ extern "C" {
 #define FDF_K_FIELDS_Y 2  /* inverse DFT along y */
 #define FDF_K_FIELDS_X 3  /* inverse DFT along x + interleave into the gather grid */
 #define FDF_K_OTHER    4  /* sampling, initial transform, weights, deposit, export */
-#define FDF_K_COUNT    5
+#define FDF_K_SORT     5  /* re-bucketing of particles by position */
+#define FDF_K_COUNT    6
 
 typedef struct fdf_ctx fdf_ctx;
 
@@ -109,7 +110,9 @@ typedef struct fdf_params {
     int32_t  n_gl;             /* Gauss-Legendre nodes per step integral, 2..8; 0 = the
                                   smallest count whose error bound is below 1e-13 for
                                   this step size (4 at d ln a = 0.17) */
-    int32_t  sort_every;       /* re-bucket particles by cell every this many steps (0 = never) */
+    int32_t  sort_every;       /* re-bucket particles by position (gather locality): 0 = after
+                                  sampling and whenever the typical displacement since the last
+                                  sort exceeds four sort tiles; k > 0 = every k steps; -1 = never */
     int32_t  reserved;
 } fdf_params;
 

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -99,9 +100,20 @@ FF split_ff(double v)
     return r;
 }
 
-struct Layout {
-    size_t tabs, cdf_t, cdf_F, tw, W0, W1, G0, G1, X, q0f, dqf, xd, qd, q0d, qs, pmag, id, stage, dep, flag, total;
+struct StateLayout {
+    size_t X, q0f, dqf, xd, qd, q0d, pmag, id;
 };
+
+struct Layout {
+    size_t tabs, modeA, cdf_t, cdf_F, tw, W0, W1, G0, G1, qs, stage, dep, flag, key, hist, bsum, total;
+    StateLayout s[2];
+};
+
+int sort_bins(const fdf_params& p)
+{
+    const int tpa = p.n_grid >> sort_tile_shift(p.n_grid);
+    return tpa * tpa * tpa * p.n_species;
+}
 
 Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
 {
@@ -115,7 +127,8 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
         off += align_up(bytes ? bytes : 1);
         return o;
     };
-    L.tabs = take(3 * (size_t)na * nk * real_bytes(prec));
+    L.tabs = take(3 * (size_t)na * nk * 8);
+    L.modeA = take(4 * (size_t)mode_table_size(p.n_grid) * real_bytes(prec));
     L.cdf_t = take((size_t)ncdf * 8);
     L.cdf_F = take((size_t)ncdf * 8);
     L.tw = take(N * complex_bytes(prec));
@@ -123,16 +136,26 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     L.W1 = take(4 * N3 * complex_bytes(prec));
     L.G0 = take(N3 * grid_bytes_per_cell(prec));
     L.G1 = take(N3 * grid_bytes_per_cell(prec));
-    L.X = take(3 * n * 4);
     const bool split = prec != FDF_PREC_F64;
-    L.q0f = take(split ? 3 * n * 4 : 0);
-    L.dqf = take(split ? 3 * n * 4 : 0);
-    L.xd = take(split ? 0 : 3 * n * 8);
-    L.qd = take(split ? 0 : 3 * n * 8);
-    L.q0d = take(split ? 0 : 3 * n * 8);
+    const bool sorts = p.sort_every >= 0;
+    for (int h = 0; h < (sorts ? 2 : 1); ++h) {
+        StateLayout& S = L.s[h];
+        // the plain form's live positions are FP64; its sampled fixed-point
+        // positions are written once and never permuted, so they are not doubled
+        S.X = (h == 0 || split) ? take(3 * n * 4) : L.s[0].X;
+        S.q0f = take(split ? 3 * n * 4 : 0);
+        S.dqf = take(split ? 3 * n * 4 : 0);
+        S.xd = take(split ? 0 : 3 * n * 8);
+        S.qd = take(split ? 0 : 3 * n * 8);
+        S.q0d = take(split ? 0 : 3 * n * 8);
+        S.pmag = take(n * 8);
+        S.id = take(n * 4);
+    }
+    if (!sorts) L.s[1] = L.s[0];
     L.qs = take(3 * n * 8);
-    L.pmag = take(n * 8);
-    L.id = take(n * 4);
+    L.key = take(sorts ? n * 4 : 0);
+    L.hist = take(sorts ? (size_t)sort_bins(p) * 4 : 0);
+    L.bsum = take(sorts ? 1024 * 4 : 0);
     L.stage = take(7 * (size_t)p.n_part * 8);
     L.dep = take(N3 * 8);
     L.flag = take(64);
@@ -172,7 +195,7 @@ int fdf::validate_params(const fdf_params* p)
     const double a0 = 1.0 / (1.0 + p->z_start);
     if (!(p->omega_r / (a0 * a0 * a0 * a0) + p->omega_m / (a0 * a0 * a0) + ol > 0))
         return fail(FDF_EINVAL, "H^2 <= 0 at z_start");
-    if (p->sort_every < 0) return fail(FDF_EINVAL, "sort_every must be >= 0");
+    if (p->sort_every < -1) return fail(FDF_EINVAL, "sort_every must be -1, 0 or a step count");
     return FDF_OK;
 }
 
@@ -204,7 +227,8 @@ struct fdf_ctx {
     Layout lay{};
     char* block = nullptr;
     bool own_block = false;
-    void* tabs = nullptr;
+    double* tabs = nullptr;   // FP64 [3][na][nk]
+    void* modeA = nullptr;    // per-step amplitude table
     double* cdf_t = nullptr;
     double* cdf_F = nullptr;
     void* tw = nullptr;
@@ -215,7 +239,13 @@ struct fdf_ctx {
     int cur = 0;
     void* Gfrozen = nullptr;
     bool frozen = false;
-    ParticleState st{};
+    ParticleState st{};       // the live state
+    ParticleState st_alt{};   // the other half of the double buffer (sort target)
+    uint32_t* key = nullptr;
+    uint32_t* hist = nullptr;
+    uint32_t* bsum = nullptr;
+    double disp = 0;          // typical displacement (Mpc) since the last sort
+    int64_t sorts = 0;
     double* stage = nullptr;
     double* dep = nullptr;
     int* dflag = nullptr;
@@ -359,8 +389,11 @@ int build_fields(fdf_ctx* c, double lna, void* G)
 {
     const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
     const int prec = c->p.precision;
-    int rc = timed(c, FDF_K_FIELDS_Z, "fields z pass",
-                   [&] { return launch_fields_z(c->stream, prec, a, c->tabs, c->tw, c->W0); });
+    int rc = timed(c, FDF_K_FIELDS_Z, "mode table",
+                   [&] { return launch_mode_table(c->stream, prec, a, c->tabs, c->modeA); });
+    if (rc) return rc;
+    rc = timed(c, FDF_K_FIELDS_Z, "fields z pass",
+               [&] { return launch_fields_z(c->stream, prec, a, c->modeA, c->tw, c->W0); });
     if (rc) return rc;
     rc = timed(c, FDF_K_FIELDS_Y, "fields y pass",
                [&] { return launch_fields_y(c->stream, prec, a, c->tw, c->W0, c->W1); });
@@ -375,6 +408,53 @@ int push(fdf_ctx* c, const PushArgs& a, const void* G)
 }
 
 const void* grid_for_step(fdf_ctx* c, int buf) { return c->frozen ? c->Gfrozen : c->G[buf]; }
+
+int sort_particles(fdf_ctx* c)
+{
+    int rc = timed(c, FDF_K_SORT, "sort", [&] {
+        return launch_sort(c->stream, c->p.precision, c->st, c->st_alt, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
+                           c->p.n_species, c->p.n_grid, c->p.box_mpc, c->key, c->hist, c->bsum);
+    });
+    if (rc) return rc;
+    std::swap(c->st, c->st_alt);
+    c->disp = 0;
+    ++c->sorts;
+    return FDF_OK;
+}
+
+// Typical displacement over one step from ln a = l1 to l2: the mean
+// Fermi-Dirac momentum <q> = 3.151 T moving at <q>/eps, for the fastest species.
+double typical_displacement(const fdf_ctx* c, double l1, double l2)
+{
+    const double q = 3.15137 * c->T_ev;
+    const double a = std::exp(0.5 * (l1 + l2));
+    double mmin = c->p.m_ev[0];
+    for (int s = 1; s < c->p.n_species; ++s) mmin = std::min(mmin, c->p.m_ev[s]);
+    double W[kMaxGL], a2[kMaxGL];
+    nodes(c, l1, l2, W, a2);
+    double dt = 0;
+    for (int j = 0; j < c->ngl; ++j) dt += W[j];
+    return std::fabs(dt) * q / std::sqrt(q * q + mmin * mmin * a * a);
+}
+
+// Sort after the pass that moved the particles over [l1, l2] if the schedule says so.
+int maybe_sort(fdf_ctx* c, int steps_done, double l1, double l2)
+{
+    const int every = c->p.sort_every;
+    if (every < 0 || c->n == 0) return FDF_OK;
+    c->disp += typical_displacement(c, l1, l2);
+    bool go;
+    if (every > 0) {
+        go = steps_done % every == 0;
+    } else {
+        // The gather's working set stays in L2 long after a sort (the touched
+        // region grows with the displacement but stays far below L2), so sort
+        // when the typical particle has crossed four tiles.
+        const double tile = (double)(1 << sort_tile_shift(c->p.n_grid)) * c->p.box_mpc / c->p.n_grid;
+        go = c->disp > 4.0 * tile;
+    }
+    return go ? sort_particles(c) : FDF_OK;
+}
 
 }  // namespace
 
@@ -482,7 +562,8 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
         c->own_block = true;
     }
     char* b = c->block;
-    c->tabs = b + L.tabs;
+    c->tabs = (double*)(b + L.tabs);
+    c->modeA = b + L.modeA;
     c->cdf_t = (double*)(b + L.cdf_t);
     c->cdf_F = (double*)(b + L.cdf_F);
     c->tw = b + L.tw;
@@ -490,15 +571,22 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     c->W1 = b + L.W1;
     c->G[0] = b + L.G0;
     c->G[1] = b + L.G1;
-    c->st.X = (uint32_t*)(b + L.X);
-    c->st.q0f = (float*)(b + L.q0f);
-    c->st.dqf = (float*)(b + L.dqf);
-    c->st.xd = (double*)(b + L.xd);
-    c->st.qd = (double*)(b + L.qd);
-    c->st.q0d = (double*)(b + L.q0d);
-    c->st.qs = (double*)(b + L.qs);
-    c->st.pmag = (double*)(b + L.pmag);
-    c->st.id = (uint32_t*)(b + L.id);
+    ParticleState* S2[2] = {&c->st, &c->st_alt};
+    for (int h = 0; h < 2; ++h) {
+        const StateLayout& S = L.s[h];
+        S2[h]->X = (uint32_t*)(b + S.X);
+        S2[h]->q0f = (float*)(b + S.q0f);
+        S2[h]->dqf = (float*)(b + S.dqf);
+        S2[h]->xd = (double*)(b + S.xd);
+        S2[h]->qd = (double*)(b + S.qd);
+        S2[h]->q0d = (double*)(b + S.q0d);
+        S2[h]->qs = (double*)(b + L.qs);
+        S2[h]->pmag = (double*)(b + S.pmag);
+        S2[h]->id = (uint32_t*)(b + S.id);
+    }
+    c->key = (uint32_t*)(b + L.key);
+    c->hist = (uint32_t*)(b + L.hist);
+    c->bsum = (uint32_t*)(b + L.bsum);
     c->stage = (double*)(b + L.stage);
     c->dep = (double*)(b + L.dep);
     c->dflag = (int*)(b + L.flag);
@@ -514,14 +602,14 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
         twd[2 * j] = std::cos(2.0 * kPi * j / N);
         twd[2 * j + 1] = std::sin(2.0 * kPi * j / N);
     }
-    cudaError_t e = cudaSuccess;
-    if (p->precision == FDF_PREC_F64) {
-        e = cudaMemcpy(c->tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c->tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice);
-    } else {
-        std::vector<float> tf(tab.begin(), tab.end()), twf(twd.begin(), twd.end());
-        e = cudaMemcpy(c->tabs, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c->tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(c->tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (p->precision == FDF_PREC_F64) {
+            e = cudaMemcpy(c->tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> twf(twd.begin(), twd.end());
+            e = cudaMemcpy(c->tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice);
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpy(c->cdf_t, t->cdf_t, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->cdf_F, t->cdf_F, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
@@ -557,6 +645,10 @@ int fdf_sample(fdf_ctx* c)
                               c->p.m_ev, c->a0, c->tau0, c->p.n_grid, c->p.box_mpc, grid_for_step(c, 0));
     });
     if (rc) return rc;
+    if (c->p.sort_every >= 0 && c->n > 0) {
+        rc = sort_particles(c);
+        if (rc) return rc;
+    }
     int flag = 0;
     FDF_CUDA(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "reading flags");
     FDF_CUDA(cudaStreamSynchronize(c->stream), "sampling");
@@ -600,6 +692,10 @@ int fdf_step(fdf_ctx* c, int32_t n)
                   last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a);
         rc = push(c, a, grid_for_step(c, nxt));
         if (rc) return rc;
+        if (!last) {
+            rc = maybe_sort(c, k1, c->lna(c->k), c->lna(k1));
+            if (rc) return rc;
+        }
         c->cur = nxt;
         c->k = k1;
     }
@@ -638,13 +734,21 @@ int fdf_get_initial(fdf_ctx* c, int32_t species, uint32_t* X, double* q_sampled,
     const int64_t np = c->p.n_part, n = c->n, begin = species * np;
     if (np == 0) return FDF_OK;
     const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    for (int d = 0; d < 3; ++d) {
-        if (X) FDF_CUDA(cudaMemcpyAsync(X + d * np, c->st.X + d * n + begin, np * 4, kind, c->stream), "copy X");
-        if (q_sampled)
-            FDF_CUDA(cudaMemcpyAsync(q_sampled + d * np, c->st.qs + d * n + begin, np * 8, kind, c->stream),
-                     "copy q_sampled");
+    // positions and |q_sampled| follow the particle permutation: un-permute by id
+    uint32_t* Xs = out_on_device ? X : (X ? (uint32_t*)c->stage : nullptr);
+    double* ps = out_on_device ? pm : (pm ? c->stage + 2 * np : nullptr);
+    int rc = timed(c, FDF_K_OTHER, "export initial", [&] {
+        return launch_export_initial(c->stream, c->p.precision, c->st, n, begin, np, Xs, ps);
+    });
+    if (rc) return rc;
+    if (!out_on_device) {
+        if (X) FDF_CUDA(cudaMemcpyAsync(X, Xs, 3 * np * 4, cudaMemcpyDeviceToHost, c->stream), "copy X");
+        if (pm) FDF_CUDA(cudaMemcpyAsync(pm, ps, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy p");
     }
-    if (pm) FDF_CUDA(cudaMemcpyAsync(pm, c->st.pmag + begin, np * 8, kind, c->stream), "copy p");
+    // the sampled momenta are not permuted
+    for (int d = 0; d < 3 && q_sampled; ++d)
+        FDF_CUDA(cudaMemcpyAsync(q_sampled + d * np, c->st.qs + d * n + begin, np * 8, kind, c->stream),
+                 "copy q_sampled");
     FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_get_initial");
     return FDF_OK;
 }

@@ -65,6 +65,13 @@ struct FieldArgs {
     int fixed_amp;
 };
 
+inline int ilog2_host(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
 // ----- host helpers shared by the entry points (fdf_api.cu) ----------------
 int set_error(int code, const char* msg);       // records the message fdf_last_error() returns
 int validate_params(const fdf_params* p);       // FDF_OK or FDF_EINVAL with a message
@@ -81,7 +88,11 @@ cudaError_t launch_sample(cudaStream_t s, int64_t n, uint32_t key0, uint32_t key
 
 // Field build: three passes.  precision: FDF_PREC_*.  W0/W1 are two complex
 // work arrays of 4 N^3 elements (float2 or double2), G the gather grid.
-cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* tabs, const void* tw,
+// Per-step amplitude table A[4 M] (M = mode_table_size(N)) from the FP64
+// tables [3][na][nk]; read by the z pass.
+int mode_table_size(int N);
+cudaError_t launch_mode_table(cudaStream_t s, int precision, const FieldArgs& a, const double* tabs64, void* A);
+cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* A, const void* tw,
                             void* W0);
 cudaError_t launch_fields_y(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W0,
                             void* W1);
@@ -107,10 +118,20 @@ struct ParticleState {
 cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t n_part,
                            const double* m_ev, double a0, double tau0, int N, double L, const void* G);
 cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a, const void* G);
+
+// Counting sort of the particle state a into b by (species, Morton index of
+// the particle's tile of 2^tile_shift cells per axis).  key: n words; hist:
+// n_species * tiles words; bsum: 1024 words.
+int sort_tile_shift(int N);
+cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, const ParticleState& b, int64_t n,
+                        int64_t n_part, int n_species, int N, double L, uint32_t* key, uint32_t* hist,
+                        uint32_t* bsum);
 // Particles [begin, begin + count) of an array of n; outputs in id order
 // (out index = id - begin).
 cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                           int64_t count, double L, double T_ev, double* x, double* q, double* w);
+cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                                  int64_t count, uint32_t* X, double* p);
 cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                            int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
                            int N, double L, double* grid);

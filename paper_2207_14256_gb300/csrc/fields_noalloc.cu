@@ -49,12 +49,6 @@ int scratch_address(unsigned char** out)
     return FDF_OK;
 }
 
-__global__ void k_tables_to_f32(size_t n, const double* __restrict__ in, float* __restrict__ out)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        out[i] = (float)in[i];
-}
-
 // tw[j] = exp(2 pi i j / N)
 template <typename V>
 __global__ void k_twiddles(int N, V* __restrict__ tw)
@@ -87,10 +81,11 @@ extern "C" int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t
     const size_t N = (size_t)p->n_grid, N3 = N * N * N;
     const size_t csz = f64 ? 16 : 8, rsz = f64 ? 8 : 4;
     const size_t ntab = 3 * (size_t)t->na * t->nk;
-    // scratch layout: W0 | W1 | FP64 tables | tables in the build precision | twiddles;
-    // the interleaved grid G of the last pass reuses W0 (same size or smaller).
+    // scratch layout: W0 | W1 | FP64 tables | amplitude table | twiddles; the
+    // interleaved grid G of the last pass reuses W0 (same size or smaller).
+    const size_t M = (size_t)mode_table_size(p->n_grid);
     const size_t oW0 = 0, oW1 = oW0 + align256(4 * N3 * csz), oT64 = oW1 + align256(4 * N3 * csz);
-    const size_t oT = oT64 + align256(ntab * 8), oTw = oT + align256(ntab * rsz), need = oTw + align256(N * csz);
+    const size_t oA = oT64 + align256(ntab * 8), oTw = oA + align256(4 * M * rsz), need = oTw + align256(N * csz);
     if (need > FDF_NOALLOC_SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof msg,
@@ -109,19 +104,14 @@ extern "C" int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t
     if (e == cudaSuccess) e = cudaMemcpyAsync(T64 + nt, t->T_phi, nt * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T64 + 2 * nt, t->dTphi_dlna, nt * 8, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(FDF_ECUDA, (std::string("table upload: ") + cudaGetErrorString(e)).c_str());
-    void* tabs = T64;
-    if (!f64) {
-        k_tables_to_f32<<<64, 256, 0, st>>>(ntab, T64, (float*)(s + oT));
-        tabs = s + oT;
-        k_twiddles<float2><<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int)N, (float2*)(s + oTw));
-    } else {
-        k_twiddles<double2><<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int)N, (double2*)(s + oTw));
-    }
+    if (!f64) k_twiddles<float2><<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int)N, (float2*)(s + oTw));
+    else k_twiddles<double2><<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int)N, (double2*)(s + oTw));
     e = cudaGetLastError();
     const FieldArgs a = make_field_args(*p, t->nk, t->na, lnk0, dlnk, lnat0, dlnat, lna);
     void* W0 = s + oW0;
     void* W1 = s + oW1;
-    if (e == cudaSuccess) e = launch_fields_z(st, p->precision, a, tabs, s + oTw, W0);
+    if (e == cudaSuccess) e = launch_mode_table(st, p->precision, a, T64, s + oA);
+    if (e == cudaSuccess) e = launch_fields_z(st, p->precision, a, s + oA, s + oTw, W0);
     if (e == cudaSuccess) e = launch_fields_y(st, p->precision, a, s + oTw, W0, W1);
     if (e == cudaSuccess) e = launch_fields_x(st, p->precision, a, s + oTw, W1, W0);
     if (e == cudaSuccess) e = launch_fields_to_f64(st, p->precision, p->n_grid, W0, out);

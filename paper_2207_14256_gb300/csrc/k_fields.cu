@@ -83,8 +83,6 @@ __device__ void smem_ifft_lines(V* a, V* b, int N, int logN, int nl, int ls, con
 // ---- precision-dependent scalar math -------------------------------------
 __device__ __forceinline__ float f_log(float x) { return logf(x); }
 __device__ __forceinline__ double f_log(double x) { return log(x); }
-__device__ __forceinline__ float f_exp(float x) { return expf(x); }
-__device__ __forceinline__ double f_exp(double x) { return exp(x); }
 __device__ __forceinline__ float f_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ void f_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
@@ -92,10 +90,12 @@ __device__ __forceinline__ void f_sincospi(double x, double* s, double* c) { sin
 
 __device__ __forceinline__ int sidx(int j, int N) { return j < (N >> 1) ? j : j - N; }
 
-// The four packed spectra of one mode (jx, jy, jz).
+// The four packed spectra of one mode (jx, jy, jz).  A[m], m = |n|^2, holds the
+// amplitude sqrt(P_R(k)/V) times T_psi, T_phi and a H dT_phi/dln a at this scale
+// factor (built in FP64 by k_mode_table); the mode supplies its unit Gaussian.
 template <typename V>
-__device__ void mode_values(const FieldArgs& a, const typename Real<V>::T* __restrict__ trow, int jx, int jy, int jz,
-                            V out[4])
+__device__ __forceinline__ void mode_values(const FieldArgs& a, const typename Real<V>::T* __restrict__ A, int jx,
+                                            int jy, int jz, V out[4])
 {
     using T = typename Real<V>::T;
     const int N = a.N;
@@ -112,55 +112,75 @@ __device__ void mode_values(const FieldArgs& a, const typename Real<V>::T* __res
     const uint4 w = philox4x32_10(make_uint4((uint32_t)pack, (uint32_t)(pack >> 32), 16u, 0u), a.key0, a.key1);
     const T u1 = (T)((w.x >> 8) + 1u) * (T)5.9604644775390625e-08;  // (0, 1]
     const T u2 = (T)(w.y >> 8) * (T)5.9604644775390625e-08;         // [0, 1)
-    const T n2 = (T)(nx * nx + ny * ny + nz * nz);
-    const T kf = (T)a.kf;
-    const T k = kf * f_sqrt(n2);
-    const T lnk = f_log(k);
-    const T amp = (T)a.amp0 / (k * f_sqrt(k)) * f_exp((T)a.half_nsm1 * (lnk - (T)a.lnkp));
     T s, c;
     f_sincospi((T)2 * u2, &s, &c);
     T re, im;
     if (a.fixed_amp) {
-        re = amp * c;
-        im = amp * s;
+        re = c;
+        im = s;
     } else {
-        const T r = amp * f_sqrt((T)-2 * f_log(u1)) * (T)0.70710678118654752440;
+        const T r = f_sqrt((T)-2 * f_log(u1)) * (T)0.70710678118654752440;
         re = r * c;
         im = r * s;
     }
     if (!canon) im = -im;
-    // transfer functions, linear in ln k on the a-interpolated rows
-    const T pos = (lnk - (T)a.lnk0) * (T)a.inv_dlnk;
-    int ik;
-    T fk;
-    if (pos <= T(0)) {
-        ik = 0;
-        fk = T(0);
-    } else if (pos >= (T)(a.nk - 1)) {
-        ik = a.nk - 2;
-        fk = T(1);
-    } else {
-        ik = (int)pos;
-        fk = pos - (T)ik;
-    }
-    const T* rp = trow;
-    const T* rf = trow + a.nk;
-    const T* rd = trow + 2 * a.nk;
-    const T Tpsi = (T(1) - fk) * rp[ik] + fk * rp[ik + 1];
-    const T Tphi = (T(1) - fk) * rf[ik] + fk * rf[ik + 1];
-    const T dT = (T(1) - fk) * rd[ik] + fk * rd[ik + 1];
+    const int m = nx * nx + ny * ny + nz * nz;
+    const T Apsi = A[4 * m], Aphi = A[4 * m + 1], Adot = A[4 * m + 2];
+    const T kf = (T)a.kf;
     const T kx = kf * (T)nx, ky = kf * (T)ny, kz = kf * (T)nz;
     const V R = mk<V>(re, im);
     const V iR = cmuli(R);
     // P0 = i kx Tpsi R + i (i ky Tpsi R) = Tpsi (kx iR - ky R)
-    out[0] = mk<V>(Tpsi * (kx * iR.x - ky * R.x), Tpsi * (kx * iR.y - ky * R.y));
+    out[0] = mk<V>(Apsi * (kx * iR.x - ky * R.x), Apsi * (kx * iR.y - ky * R.y));
     // P1 = i kz Tpsi R - kx Tphi R
-    out[1] = mk<V>(kz * Tpsi * iR.x - kx * Tphi * R.x, kz * Tpsi * iR.y - kx * Tphi * R.y);
+    out[1] = mk<V>(kz * Apsi * iR.x - kx * Aphi * R.x, kz * Apsi * iR.y - kx * Aphi * R.y);
     // P2 = i ky Tphi R - kz Tphi R
-    out[2] = mk<V>(Tphi * (ky * iR.x - kz * R.x), Tphi * (ky * iR.y - kz * R.y));
+    out[2] = mk<V>(Aphi * (ky * iR.x - kz * R.x), Aphi * (ky * iR.y - kz * R.y));
     // P3 = aH dT R + i Tpsi R
-    const T aHdT = (T)a.aH * dT;
-    out[3] = mk<V>(aHdT * R.x + Tpsi * iR.x, aHdT * R.y + Tpsi * iR.y);
+    out[3] = mk<V>(Adot * R.x + Apsi * iR.x, Adot * R.y + Apsi * iR.y);
+}
+
+// Per scale factor, in FP64, for every m = |n|^2 in [0, M): k = k_f sqrt(m),
+// the amplitude sqrt(P_R(k)/V) = sqrt(2 pi^2 A_s / V) k^-3/2 (k/k_pivot)^((n_s-1)/2)
+// times T_psi, T_phi and a H dT_phi/dln a, read bilinearly in (ln k, ln a) with
+// clamping from the FP64 tables [3][na][nk].
+template <typename T>
+__global__ void __launch_bounds__(256) k_mode_table(FieldArgs a, int M, const double* __restrict__ tabs,
+                                                    T* __restrict__ A)
+{
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        double v[3] = {0.0, 0.0, 0.0};
+        if (m > 0) {
+            const double k = a.kf * sqrt((double)m);
+            const double lnk = log(k);
+            const double amp = a.amp0 / (k * sqrt(k)) * exp(a.half_nsm1 * (lnk - a.lnkp));
+            const double pos = (lnk - a.lnk0) * a.inv_dlnk;
+            int ik;
+            double fk;
+            if (pos <= 0.0) {
+                ik = 0;
+                fk = 0.0;
+            } else if (pos >= a.nk - 1) {
+                ik = a.nk - 2;
+                fk = 1.0;
+            } else {
+                ik = (int)pos;
+                fk = pos - ik;
+            }
+            for (int t = 0; t < 3; ++t) {
+                const double* r0 = tabs + ((size_t)t * a.na + a.ia) * a.nk;
+                const double* r1 = r0 + a.nk;
+                const double v0 = (1.0 - fk) * r0[ik] + fk * r0[ik + 1];
+                const double v1 = (1.0 - fk) * r1[ik] + fk * r1[ik + 1];
+                v[t] = amp * ((1.0 - a.fa) * v0 + a.fa * v1);
+            }
+            v[2] *= a.aH;
+        }
+        A[4 * m] = (T)v[0];
+        A[4 * m + 1] = (T)v[1];
+        A[4 * m + 2] = (T)v[2];
+        A[4 * m + 3] = T(0);
+    }
 }
 
 template <typename V>
@@ -172,31 +192,20 @@ __device__ void load_twiddles(V* s_tw, const V* __restrict__ tw, int N)
 // ---- pass z: spectrum + inverse DFT along z ---------------------------------
 // Block (x-tile, jy): TX columns of N modes along z, all four packed spectra.
 template <typename V, int TX>
-__global__ void __launch_bounds__(kThreads) k_fields_z(FieldArgs a, const typename Real<V>::T* __restrict__ tabs,
+__global__ void __launch_bounds__(kThreads) k_fields_z(FieldArgs a, const typename Real<V>::T* __restrict__ A,
                                                        const V* __restrict__ tw, V* __restrict__ W0)
 {
-    using T = typename Real<V>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N, LS = N + 1;
     V* tiles = reinterpret_cast<V*>(smem_raw);
     V* scratch = tiles + 4 * TX * LS;
     V* s_tw = scratch + TX * LS;
-    T* trow = reinterpret_cast<T*>(s_tw + N);
     load_twiddles(s_tw, tw, N);
-    // the three tables interpolated to this ln a: trow[t][k], tabs is [3][na][nk]
-    const int nk = a.nk;
-    const T fa = (T)a.fa;
-    for (int i = threadIdx.x; i < 3 * nk; i += blockDim.x) {
-        const int t = i / nk, k = i - t * nk;
-        const T* r0 = tabs + ((size_t)t * a.na + a.ia) * nk;
-        trow[i] = (T(1) - fa) * r0[k] + fa * r0[nk + k];
-    }
-    __syncthreads();
     const int x0 = blockIdx.x * TX, jy = blockIdx.y;
     for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
         const int xo = e % TX, z = e / TX;
         V v[4];
-        mode_values<V>(a, trow, x0 + xo, jy, z, v);
+        mode_values<V>(a, A, x0 + xo, jy, z, v);
 #pragma unroll
         for (int p = 0; p < 4; ++p) tiles[p * TX * LS + xo * LS + z] = v[p];
     }
@@ -344,9 +353,9 @@ __global__ void k_fields_from_f64(size_t N3, const double* __restrict__ in, Gt* 
 constexpr int kTile = 8;
 
 template <typename V>
-size_t smem_z(int N, int nk)
+size_t smem_z(int N)
 {
-    return (size_t)(5 * kTile * (N + 1) + N) * sizeof(V) + 3 * (size_t)nk * sizeof(typename Real<V>::T);
+    return (size_t)(5 * kTile * (N + 1) + N) * sizeof(V);
 }
 template <typename V>
 size_t smem_y(int N)
@@ -367,21 +376,32 @@ cudaError_t set_smem(K kernel, size_t bytes)
 
 }  // namespace
 
-cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* tabs, const void* tw,
+int mode_table_size(int N) { return 3 * (N / 2 - 1) * (N / 2 - 1) + 1; }
+
+cudaError_t launch_mode_table(cudaStream_t s, int precision, const FieldArgs& a, const double* tabs64, void* A)
+{
+    const int M = mode_table_size(a.N);
+    const unsigned blocks = (unsigned)((M + 255) / 256);
+    if (precision == FDF_PREC_F64) k_mode_table<double><<<blocks, 256, 0, s>>>(a, M, tabs64, (double*)A);
+    else k_mode_table<float><<<blocks, 256, 0, s>>>(a, M, tabs64, (float*)A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* A, const void* tw,
                             void* W0)
 {
     const dim3 grid(a.N / kTile, a.N);
     if (precision == FDF_PREC_F64) {
-        const size_t sm = smem_z<double2>(a.N, a.nk);
+        const size_t sm = smem_z<double2>(a.N);
         cudaError_t e = set_smem(k_fields_z<double2, kTile>, sm);
         if (e != cudaSuccess) return e;
-        k_fields_z<double2, kTile><<<grid, kThreads, sm, s>>>(a, (const double*)tabs, (const double2*)tw,
+        k_fields_z<double2, kTile><<<grid, kThreads, sm, s>>>(a, (const double*)A, (const double2*)tw,
                                                               (double2*)W0);
     } else {
-        const size_t sm = smem_z<float2>(a.N, a.nk);
+        const size_t sm = smem_z<float2>(a.N);
         cudaError_t e = set_smem(k_fields_z<float2, kTile>, sm);
         if (e != cudaSuccess) return e;
-        k_fields_z<float2, kTile><<<grid, kThreads, sm, s>>>(a, (const float*)tabs, (const float2*)tw, (float2*)W0);
+        k_fields_z<float2, kTile><<<grid, kThreads, sm, s>>>(a, (const float*)A, (const float2*)tw, (float2*)W0);
     }
     return cudaGetLastError();
 }

@@ -347,6 +347,29 @@ __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n
     }
 }
 
+// The pre-initial draw in particle-index order.  The split form's fixed-point
+// positions are the live state and follow the permutation; the plain form keeps
+// them in id order.  |q_sampled| follows the permutation in both forms.
+template <int Prec>
+__global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, int64_t n, int64_t begin,
+                                                             int64_t count, uint32_t* __restrict__ Xo,
+                                                             double* __restrict__ po)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = begin + j;
+        const int64_t o = (int64_t)st.id[i] - begin;
+        if (Xo) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if constexpr (Prec == FDF_PREC_F64) Xo[d * count + j] = st.X[d * n + i];
+                else Xo[d * count + o] = st.X[d * n + i];
+            }
+        }
+        if (po) po[o] = st.pmag[i];
+    }
+}
+
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                       int64_t n_part, Masses ms, double a, double T, int quantity,
@@ -442,6 +465,18 @@ cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st
         k_export<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
     else
         k_export<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                                  int64_t count, uint32_t* X, double* p)
+{
+    if (count <= 0) return cudaSuccess;
+    const unsigned b = grid_for(count);
+    if (precision == FDF_PREC_F64)
+        k_export_initial<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p);
+    else
+        k_export_initial<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p);
     return cudaGetLastError();
 }
 

@@ -67,19 +67,17 @@ def test_sampler_bit_exact(F, inputs, c1_tables, prec):
         assert np.array_equal(got[s][2].view(np.uint64), pm.view(np.uint64))
 
 
-@pytest.mark.parametrize("prec,tol,tol6", [(0, 1e-12, 1e-12), (1, 3e-6, 3e-4), (2, 1e-2, 1e-2)])
-def test_fields_match_oracle(F, inputs, c1_tables, prec, tol, tol6):
-    """Each slot against the oracle, relative to the scale its inputs set.  For
-    the gradients and psi that is the field's maximum.  phi_dot = a H dT/dln a R
-    nearly cancels in the eras where dT/dln a ~ 0 (its interpolation subtracts
-    table entries far larger than the result), so its scale is
-    a H max|dT| sqrt(sum |R_n|^2) over the table rows the interpolation reads.
-    In FP32 the table position ln k carries ~2^-24 |ln k| of rounding, i.e. ~1e-5
-    of a table interval, times the jump of dT/dln a between neighbouring nodes."""
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 3e-6), (2, 1e-2)])
+def test_fields_match_oracle(F, inputs, c1_tables, prec, tol):
+    """Each slot against the oracle.  Slots are transformed in packed pairs
+    (d_x psi + i d_y psi, d_z psi + i d_x phi, d_y phi + i d_z phi, phi_dot + i psi);
+    an FFT's rounding is relative to the magnitude of the complex signal it
+    transforms, so each slot's error is measured against the larger maximum of
+    its pair.  (phi_dot, near zero in the radiation and matter eras, shares its
+    transform with psi.)"""
     p = inputs.config("c1_32", n_grid=32, precision=prec, seed=31)
     o = O.Oracle(p, c1_tables)
     R = o.noise()
-    lna_t = c1_tables["lna"]
     errs = []
     with F.Run(p, c1_tables) as r:
         for k in (0, 37, 80, 100):
@@ -87,16 +85,12 @@ def test_fields_match_oracle(F, inputs, c1_tables, prec, tol, tol6):
             g = r.build_fields(lna)
             ref, _ = o.fields(lna, 0xFF, R)
             for s in range(8):
-                scale = np.max(np.abs(ref[s]))
-                if s == 6:
-                    a = math.exp(lna)
-                    ia = min(max(int((lna - lna_t[0]) / (lna_t[1] - lna_t[0])), 0), len(lna_t) - 2)
-                    dT = np.max(np.abs(c1_tables["dTphi_dlna"][ia:ia + 2]))
-                    scale = a * o.hubble(a) * dT * math.sqrt(np.sum(np.abs(R) ** 2))
-                errs.append((k, s, scale, np.max(np.abs(g[s] - ref[s])) / scale))
+                pair = s & ~1
+                scale = max(np.max(np.abs(ref[pair])), np.max(np.abs(ref[pair + 1])))
+                errs.append((k, s, np.max(np.abs(ref[s])), np.max(np.abs(g[s] - ref[s])) / scale))
     for e in errs:
-        print("k %3d slot %d  scale %.3e  rel err %.3e" % e)
-    assert all(e[2] > 0 and e[3] < (tol6 if e[1] == 6 else tol) for e in errs)
+        print("k %3d slot %d  max|ref| %.3e  err / pair scale %.3e" % e)
+    assert all(e[2] > 0 and e[3] < tol for e in errs)
 
 
 def test_run_c1_plain_fp64(F, inputs, c1_tables):
