@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <climits>
 #include <new>
 #include <string>
 #include <vector>
@@ -341,6 +342,8 @@ void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, do
     std::memset(&a, 0, sizeof(a));
     a.n = c->n;
     a.n_part = c->p.n_part > 0 ? c->p.n_part : 1;
+    for (int s = 0; s < kMaxSpecies; ++s)
+        a.sp_begin[s] = s + 1 < c->p.n_species ? (int64_t)(s + 1) * c->p.n_part : INT64_MAX;
     a.n_gl = c->ngl;
     a.do_drift = drift;
     a.do_kick = kick;

@@ -40,6 +40,7 @@ struct SpeciesCoef {
 struct PushArgs {
     int64_t n;                  // particles in all species
     int64_t n_part;             // particles per species
+    int64_t sp_begin[kMaxSpecies];  // first particle of species 1, 2, 3 (n beyond the last species)
     int n_gl;
     int do_drift;
     int do_kick;

@@ -191,18 +191,50 @@ __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t 
 }
 
 // ---- the fused leapfrog pass, split form -------------------------------------
+__device__ __forceinline__ int species_of(const PushArgs& a, int64_t i)
+{
+    return (int)(i >= a.sp_begin[0]) + (int)(i >= a.sp_begin[1]) + (int)(i >= a.sp_begin[2]);
+}
+
+struct SplitState {
+    uint32_t X0, X1, X2;
+    float qa, qb, qc, da, db, dc;
+};
+
+__device__ __forceinline__ SplitState load_split(const uint32_t* __restrict__ X, const float* __restrict__ q0f,
+                                                 const float* __restrict__ dqf, int64_t n, int64_t i)
+{
+    SplitState s;
+    s.X0 = __ldcs(X + i);
+    s.X1 = __ldcs(X + n + i);
+    s.X2 = __ldcs(X + 2 * n + i);
+    s.qa = __ldcs(q0f + i);
+    s.qb = __ldcs(q0f + n + i);
+    s.qc = __ldcs(q0f + 2 * n + i);
+    s.da = __ldcs(dqf + i);
+    s.db = __ldcs(dqf + n + i);
+    s.dc = __ldcs(dqf + 2 * n + i);
+    return s;
+}
+
 template <typename Gt>
-__global__ void __launch_bounds__(kThreads) k_push_split(const __grid_constant__ PushArgs a, uint32_t* __restrict__ X,
-                                                         const float* __restrict__ q0f, float* __restrict__ dqf,
-                                                         const Gt* __restrict__ G)
+__global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constant__ PushArgs a,
+                                                            uint32_t* __restrict__ X, const float* __restrict__ q0f,
+                                                            float* __restrict__ dqf, const Gt* __restrict__ G)
 {
     const int64_t n = a.n;
     const uint32_t N = (uint32_t)a.N;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const SpeciesCoef& c = a.sp[i / a.n_part];
-        uint32_t X0 = X[i], X1 = X[n + i], X2 = X[2 * n + i];
-        const float qa = q0f[i], qb = q0f[n + i], qc = q0f[2 * n + i];
-        float da = dqf[i], db = dqf[n + i], dc = dqf[2 * n + i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    SplitState nx{};
+    if (i < n) nx = load_split(X, q0f, dqf, n, i);
+    for (; i < n; i += stride) {
+        const SplitState cur = nx;
+        if (i + stride < n) nx = load_split(X, q0f, dqf, n, i + stride);  // next particle's state in flight
+        const SpeciesCoef& c = a.sp[species_of(a, i)];
+        uint32_t X0 = cur.X0, X1 = cur.X1, X2 = cur.X2;
+        const float qa = cur.qa, qb = cur.qb, qc = cur.qc;
+        float da = cur.da, db = cur.db, dc = cur.dc;
         if (a.do_drift) {
             // q = q_0 + dq exactly, as float-float per component
             FF t0, t1, t2;
@@ -210,16 +242,19 @@ __global__ void __launch_bounds__(kThreads) k_push_split(const __grid_constant__
             two_sum(qb, db, t1.hi, t1.lo);
             two_sum(qc, dc, t2.hi, t2.lo);
             // |q|^2 in float-float
-            FF S = ff_add(ff_add(ff_mul(t0, t0), ff_mul(t1, t1)), ff_mul(t2, t2));
+            const FF S = ff_add(ff_add(ff_mul(t0, t0), ff_mul(t1, t1)), ff_mul(t2, t2));
             // D = sum_j Wd_j (S + mu_j)^-1/2 = r_c [sum_j Wd_j + sum_j Wd_j g(delta_j)],
             // r_c = (S + mu_c)^-1/2, delta_j = (mu_j - mu_c) r_c^2, g(d) = (1+d)^-1/2 - 1
+            // = -d y / (1 + (1+d) y) with y = (1+d)^-1/2.  The corrections are small
+            // next to sum_j Wd_j, so hardware rsqrt and reciprocal (2^-22) suffice.
             const FF r = ff_rsqrt(ff_add(S, c.mud_c));
             const float r2 = r.hi * r.hi;
             float corr = 0.f;
             for (int j = 0; j < a.n_gl; ++j) {
                 const float d = c.dmud_f[j] * r2;
-                const float sq = sqrtf(1.f + d);
-                corr = fmaf(c.Wd_f[j], -d / (sq * (1.f + sq)), corr);
+                const float t = 1.f + d;
+                const float y = rsqrtf(t);
+                corr = fmaf(c.Wd_f[j], -d * y * __frcp_rn(fmaf(t, y, 1.f)), corr);
             }
             FF A;
             fast_two_sum(c.Wd_sum.hi, __fadd_rn(c.Wd_sum.lo, corr), A.hi, A.lo);
@@ -245,14 +280,14 @@ __global__ void __launch_bounds__(kThreads) k_push_split(const __grid_constant__
             da += -g[0] * Kpsi - g[3] * a2 + qa * b;
             db += -g[1] * Kpsi - g[4] * a2 + qb * b;
             dc += -g[2] * Kpsi - g[5] * a2 + qc * b;
-            dqf[i] = da;
-            dqf[n + i] = db;
-            dqf[2 * n + i] = dc;
+            __stcs(dqf + i, da);
+            __stcs(dqf + n + i, db);
+            __stcs(dqf + 2 * n + i, dc);
         }
         if (a.do_drift) {
-            X[i] = X0;
-            X[n + i] = X1;
-            X[2 * n + i] = X2;
+            __stcs(X + i, X0);
+            __stcs(X + n + i, X1);
+            __stcs(X + 2 * n + i, X2);
         }
     }
 }
@@ -263,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ P
 {
     const int64_t n = a.n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const SpeciesCoef& c = a.sp[i / a.n_part];
+        const SpeciesCoef& c = a.sp[(int)(i >= a.sp_begin[0]) + (int)(i >= a.sp_begin[1]) + (int)(i >= a.sp_begin[2])];
         double x[3] = {xd[i], xd[n + i], xd[2 * n + i]};
         double q[3] = {qd[i], qd[n + i], qd[2 * n + i]};
         const double q0[3] = {q0d[i], q0d[n + i], q0d[2 * n + i]};

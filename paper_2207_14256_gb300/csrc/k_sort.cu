@@ -127,8 +127,24 @@ __global__ void __launch_bounds__(kThreads) k_sort_scatter(ParticleState a, Part
                                                            const uint32_t* __restrict__ key,
                                                            uint32_t* __restrict__ offset)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = atomicAdd(offset + key[i], 1u);
+    // Grid-stride loop with a warp-uniform trip count, so that every lane can take
+    // part in the warp-aggregated atomic: lanes sharing a key (the common case once
+    // the state is nearly sorted) take one atomicAdd through their leader.
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool live = i < n;
+        const unsigned active = __ballot_sync(0xffffffffu, live);
+        if (!live) continue;
+        const uint32_t k = key[i];
+        const unsigned peers = __match_any_sync(active, k);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(offset + k, (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        const int64_t j = (int64_t)base + rank;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             if constexpr (Prec == FDF_PREC_F64) {
