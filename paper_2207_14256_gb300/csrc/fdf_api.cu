@@ -106,7 +106,7 @@ struct StateLayout {
 };
 
 struct Layout {
-    size_t tabs, modeA, cdf_t, cdf_F, tw, W0, W1, G0, G1, qs, stage, dep, flag, key, hist, bsum, total;
+    size_t tabs, modeA, noise, cdf_t, cdf_F, tw, W0, W1, G0, G1, qs, stage, dep, flag, key, hist, bsum, total;
     StateLayout s[2];
 };
 
@@ -130,6 +130,7 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     };
     L.tabs = take(3 * (size_t)na * nk * 8);
     L.modeA = take(4 * (size_t)mode_table_size(p.n_grid) * real_bytes(prec));
+    L.noise = take(N3 * complex_bytes(prec));
     L.cdf_t = take((size_t)ncdf * 8);
     L.cdf_F = take((size_t)ncdf * 8);
     L.tw = take(N * complex_bytes(prec));
@@ -230,6 +231,8 @@ struct fdf_ctx {
     bool own_block = false;
     double* tabs = nullptr;   // FP64 [3][na][nk]
     void* modeA = nullptr;    // per-step amplitude table
+    void* noise = nullptr;    // unit Gaussian field of the run
+    bool noise_ready = false;
     double* cdf_t = nullptr;
     double* cdf_F = nullptr;
     void* tw = nullptr;
@@ -388,15 +391,28 @@ void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, do
     }
 }
 
+// The unit Gaussian field of the run (a function of the seed and the mesh only).
+int draw_noise(fdf_ctx* c)
+{
+    const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, c->lna0);
+    int rc = timed(c, FDF_K_FIELDS_Z, "noise", [&] { return launch_noise(c->stream, c->p.precision, a, c->noise); });
+    if (rc == FDF_OK) c->noise_ready = true;
+    return rc;
+}
+
 int build_fields(fdf_ctx* c, double lna, void* G)
 {
+    if (!c->noise_ready) {
+        int rc0 = draw_noise(c);
+        if (rc0) return rc0;
+    }
     const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
     const int prec = c->p.precision;
     int rc = timed(c, FDF_K_FIELDS_Z, "mode table",
                    [&] { return launch_mode_table(c->stream, prec, a, c->tabs, c->modeA); });
     if (rc) return rc;
     rc = timed(c, FDF_K_FIELDS_Z, "fields z pass",
-               [&] { return launch_fields_z(c->stream, prec, a, c->modeA, c->tw, c->W0); });
+               [&] { return launch_fields_z(c->stream, prec, a, c->modeA, c->noise, c->tw, c->W0); });
     if (rc) return rc;
     rc = timed(c, FDF_K_FIELDS_Y, "fields y pass",
                [&] { return launch_fields_y(c->stream, prec, a, c->tw, c->W0, c->W1); });
@@ -567,6 +583,7 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     char* b = c->block;
     c->tabs = (double*)(b + L.tabs);
     c->modeA = b + L.modeA;
+    c->noise = b + L.noise;
     c->cdf_t = (double*)(b + L.cdf_t);
     c->cdf_F = (double*)(b + L.cdf_F);
     c->tw = b + L.tw;
@@ -638,6 +655,8 @@ int fdf_sample(fdf_ctx* c)
     if (rc) return rc;
     c->cur = 0;
     c->gk[0] = c->gk[1] = -1;
+    rc = draw_noise(c);
+    if (rc) return rc;
     if (!c->frozen) {
         rc = build_fields(c, c->lna(0), c->G[0]);
         if (rc) return rc;

@@ -93,8 +93,10 @@ cudaError_t launch_sample(cudaStream_t s, int64_t n, uint32_t key0, uint32_t key
 // tables [3][na][nk]; read by the z pass.
 int mode_table_size(int N);
 cudaError_t launch_mode_table(cudaStream_t s, int precision, const FieldArgs& a, const double* tabs64, void* A);
-cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* A, const void* tw,
-                            void* W0);
+// The unit Gaussian field R_n / sqrt(P_R/V) on the N^3 mode array (drawn once per run).
+cudaError_t launch_noise(cudaStream_t s, int precision, const FieldArgs& a, void* R);
+cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* A, const void* R,
+                            const void* tw, void* W0);
 cudaError_t launch_fields_y(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W0,
                             void* W1);
 cudaError_t launch_fields_x(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W1,

@@ -81,11 +81,12 @@ extern "C" int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t
     const size_t N = (size_t)p->n_grid, N3 = N * N * N;
     const size_t csz = f64 ? 16 : 8, rsz = f64 ? 8 : 4;
     const size_t ntab = 3 * (size_t)t->na * t->nk;
-    // scratch layout: W0 | W1 | FP64 tables | amplitude table | twiddles; the
+    // scratch layout: W0 | W1 | FP64 tables | amplitude table | twiddles | noise; the
     // interleaved grid G of the last pass reuses W0 (same size or smaller).
     const size_t M = (size_t)mode_table_size(p->n_grid);
     const size_t oW0 = 0, oW1 = oW0 + align256(4 * N3 * csz), oT64 = oW1 + align256(4 * N3 * csz);
-    const size_t oA = oT64 + align256(ntab * 8), oTw = oA + align256(4 * M * rsz), need = oTw + align256(N * csz);
+    const size_t oA = oT64 + align256(ntab * 8), oTw = oA + align256(4 * M * rsz), oR = oTw + align256(N * csz);
+    const size_t need = oR + align256(N3 * csz);
     if (need > FDF_NOALLOC_SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof msg,
@@ -110,8 +111,9 @@ extern "C" int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t
     const FieldArgs a = make_field_args(*p, t->nk, t->na, lnk0, dlnk, lnat0, dlnat, lna);
     void* W0 = s + oW0;
     void* W1 = s + oW1;
+    if (e == cudaSuccess) e = launch_noise(st, p->precision, a, s + oR);
     if (e == cudaSuccess) e = launch_mode_table(st, p->precision, a, T64, s + oA);
-    if (e == cudaSuccess) e = launch_fields_z(st, p->precision, a, s + oA, s + oTw, W0);
+    if (e == cudaSuccess) e = launch_fields_z(st, p->precision, a, s + oA, s + oR, s + oTw, W0);
     if (e == cudaSuccess) e = launch_fields_y(st, p->precision, a, s + oTw, W0, W1);
     if (e == cudaSuccess) e = launch_fields_x(st, p->precision, a, s + oTw, W1, W0);
     if (e == cudaSuccess) e = launch_fields_to_f64(st, p->precision, p->n_grid, W0, out);

@@ -20,64 +20,179 @@
 //   x: transform along x and write the interleaved gather grid G[cell][8].
 #include <cuda_bf16.h>
 
+#include <utility>
+
 #include "device_math.cuh"
 
 namespace fdf {
 
 namespace {
 
-constexpr int kThreads = 256;
+// ---- in-register DFTs ----------------------------------------------------------
+// e^{2 pi i j / 32}, j = 0..31 (exact zeros and ones on the axes).
+#define C0 0.9807852804032304491262
+#define C1 0.9238795325112867561282
+#define C2 0.8314696123025452370788
+#define C3 0.7071067811865475244008
+#define C4 0.5555702330196022247428
+#define C5 0.3826834323650897717285
+#define C6 0.1950903220161282678483
+__constant__ double2 kTw32d[32] = {
+    {1, 0}, {C0, C6}, {C1, C5}, {C2, C4}, {C3, C3}, {C4, C2}, {C5, C1}, {C6, C0},
+    {0, 1}, {-C6, C0}, {-C5, C1}, {-C4, C2}, {-C3, C3}, {-C2, C4}, {-C1, C5}, {-C0, C6},
+    {-1, 0}, {-C0, -C6}, {-C1, -C5}, {-C2, -C4}, {-C3, -C3}, {-C4, -C2}, {-C5, -C1}, {-C6, -C0},
+    {0, -1}, {C6, -C0}, {C5, -C1}, {C4, -C2}, {C3, -C3}, {C2, -C4}, {C1, -C5}, {C0, -C6}};
+__constant__ float2 kTw32f[32] = {
+    {1, 0}, {(float)C0, (float)C6}, {(float)C1, (float)C5}, {(float)C2, (float)C4}, {(float)C3, (float)C3},
+    {(float)C4, (float)C2}, {(float)C5, (float)C1}, {(float)C6, (float)C0}, {0, 1}, {(float)-C6, (float)C0},
+    {(float)-C5, (float)C1}, {(float)-C4, (float)C2}, {(float)-C3, (float)C3}, {(float)-C2, (float)C4},
+    {(float)-C1, (float)C5}, {(float)-C0, (float)C6}, {-1, 0}, {(float)-C0, (float)-C6}, {(float)-C1, (float)-C5},
+    {(float)-C2, (float)-C4}, {(float)-C3, (float)-C3}, {(float)-C4, (float)-C2}, {(float)-C5, (float)-C1},
+    {(float)-C6, (float)-C0}, {0, -1}, {(float)C6, (float)-C0}, {(float)C5, (float)-C1}, {(float)C4, (float)-C2},
+    {(float)C3, (float)-C3}, {(float)C2, (float)-C4}, {(float)C1, (float)-C5}, {(float)C0, (float)-C6}};
+#undef C0
+#undef C1
+#undef C2
+#undef C3
+#undef C4
+#undef C5
+#undef C6
 
-template <typename V>
-__device__ void smem_ifft_lines(V* a, V* b, int N, int logN, int nl, int ls, const V* __restrict__ tw)
+template <typename V> __device__ __forceinline__ V tw32(int j);
+template <> __device__ __forceinline__ float2 tw32<float2>(int j) { return kTw32f[j]; }
+template <> __device__ __forceinline__ double2 tw32<double2>(int j) { return kTw32d[j]; }
+
+// Compile-time loops: f(Idx<I>) for I = 0..N-1, so that every register-array index
+// below is a constant expression.
+template <int I> struct Idx {
+    static constexpr int value = I;
+    __host__ __device__ constexpr operator int() const { return I; }
+};
+template <typename F, int... Is>
+__device__ __forceinline__ void sfor_impl(F&& f, std::integer_sequence<int, Is...>)
 {
-    int n4 = logN >> 1, n2 = logN & 1;
-    if ((n4 + n2) & 1) {
-        n4 -= 1;
-        n2 += 2;
-    }
-    int logNs = 0;
-    V* src = a;
-    V* dst = b;
-    for (int st = 0; st < n2 + n4; ++st) {
-        const int logR = st < n2 ? 1 : 2;
-        const int lognb = logN - logR;
-        const int nb = 1 << lognb;
-        const int Ns = 1 << logNs;
-        const int total = nl << lognb;
-        const int twshift = logN - logNs - logR;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int line = t >> lognb, j = t & (nb - 1);
-            const int k = j & (Ns - 1);
-            const V* in = src + line * ls;
-            V* out = dst + line * ls;
-            const int tws = k << twshift;
-            if (logR == 1) {
-                const V v0 = in[j];
-                const V v1 = cmul(in[j + nb], tw[tws]);
-                const int base = ((j >> logNs) << (logNs + 1)) + k;
-                out[base] = cadd(v0, v1);
-                out[base + Ns] = csub(v0, v1);
-            } else {
-                const V v0 = in[j];
-                const V v1 = cmul(in[j + nb], tw[tws]);
-                const V v2 = cmul(in[j + 2 * nb], tw[2 * tws]);
-                const V v3 = cmul(in[j + 3 * nb], tw[3 * tws]);
-                const V s02 = cadd(v0, v2), d02 = csub(v0, v2);
-                const V s13 = cadd(v1, v3), d13 = cmuli(csub(v1, v3));
-                const int base = ((j >> logNs) << (logNs + 2)) + k;
-                out[base] = cadd(s02, s13);
-                out[base + Ns] = cadd(d02, d13);
-                out[base + 2 * Ns] = csub(s02, s13);
-                out[base + 3 * Ns] = csub(d02, d13);
-            }
+    (f(Idx<Is>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void sfor(F&& f)
+{
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+__host__ __device__ constexpr int bitrev(int i, int R)
+{
+    int j = 0;
+    for (int b = 1; b < R; b <<= 1, i >>= 1) j = (j << 1) | (i & 1);
+    return j;
+}
+__host__ __device__ constexpr int ilog2c(int R) { return R <= 1 ? 0 : 1 + ilog2c(R / 2); }
+
+// In-place inverse DFT of R <= 32 values in registers, X_k = sum_n v_n e^{+2 pi i n k / R}:
+// iterative radix-2 Cooley-Tukey on a bit-reversed copy.
+template <int R, typename V>
+__device__ __forceinline__ void dft_reg(V* v)
+{
+    sfor<R>([&](auto I) {
+        constexpr int i = I, j = bitrev(I, R);
+        if constexpr (i < j) {
+            const V t = v[i];
+            v[i] = v[j];
+            v[j] = t;
         }
-        __syncthreads();
-        V* t = src;
-        src = dst;
-        dst = t;
-        logNs += logR;
+    });
+    sfor<ilog2c(R)>([&](auto S) {
+        constexpr int len = 2 << S;
+        sfor<R / len>([&](auto B) {
+            constexpr int i = B * len;
+            sfor<len / 2>([&](auto K) {
+                constexpr int k = K;
+                const V u = v[i + k];
+                V t = v[i + k + len / 2];
+                if constexpr (k != 0) {
+                    if constexpr (4 * k == len) t = cmuli(t);
+                    else t = cmul(t, tw32<V>(k * (32 / len)));
+                }
+                v[i + k] = cadd(u, t);
+                v[i + k + len / 2] = csub(u, t);
+            });
+        });
+    });
+}
+
+// ---- the line transform: N = N1 N2, two levels ----------------------------------
+// X[k1 + N1 k2] = sum_n2 w_N2^(n2 k2) [ w_N^(n2 k1) sum_n1 x[N2 n1 + n2] w_N1^(n1 k1) ],
+// w_M = e^{2 pi i / M}.  Thread n2 holds x[N2 n1 + n2] (n1 = 0..N1-1), transforms them
+// and applies w_N^(n2 k1); one padded shared-memory transpose; thread t then does
+// the N2-point transforms of k1 = t, t + N2, ... (G = N1 / N2 of them).
+template <int N> struct Split;
+template <> struct Split<8> { static constexpr int N1 = 4, N2 = 2; };
+template <> struct Split<16> { static constexpr int N1 = 4, N2 = 4; };
+template <> struct Split<32> { static constexpr int N1 = 8, N2 = 4; };
+template <> struct Split<64> { static constexpr int N1 = 8, N2 = 8; };
+template <> struct Split<128> { static constexpr int N1 = 16, N2 = 8; };
+template <> struct Split<256> { static constexpr int N1 = 16, N2 = 16; };
+template <> struct Split<512> { static constexpr int N1 = 32, N2 = 16; };
+
+template <int N> struct Shape {
+    static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = N1 / N2;
+    static constexpr int T = N2;                               // threads per line
+    static constexpr int TS0 = N2 * (N1 + 1);                  // transpose buffer per line (elements)
+    // y and z passes: TX lines (consecutive x) per block, lane = xo + TX t, so the
+    // 32 lanes of a warp cover 32/TX values of t; a line stride TS = 32/TX (mod 16)
+    // spreads them over each pair of banks exactly twice (2 wavefronts per access).
+    static constexpr int TX0 = 128 / T > 16 ? 128 / T : 16;
+    static constexpr int TX = TX0 < N ? TX0 : N;
+    static constexpr int THREADS = TX * T;
+    static constexpr int SYZ = (32 / TX) % 16;
+    static constexpr int TS = TS0 + ((SYZ - TS0 % 16) + 16) % 16;
+    // x pass: TL lines per block, lane = t + T lo; stride TSX = T (mod 16).
+    static constexpr int TL0 = 128 / T;
+    static constexpr int TL = TL0 < N ? TL0 : N;
+    static constexpr int THREADS_X = TL * T;
+    static constexpr int SX = T % 16;
+    static constexpr int TSX = TS0 + ((SX - TS0 % 16) + 16) % 16;
+    static constexpr int TWS = N2 * (N1 + 1);                  // per-thread twiddle rows, padded
+    // z pass: 128 threads (its per-thread amplitudes live in shared memory).
+    static constexpr int TZ0 = 128 / T;
+    static constexpr int TZ = TZ0 < N ? TZ0 : N;
+    static constexpr int THREADS_Z = TZ * T;
+    static constexpr int SZ = (32 / TZ) % 16;
+    static constexpr int TSZ = TS0 + ((SZ - TS0 % 16) + 16) % 16;
+};
+
+// Twiddles of the first level, w_N^(n2 k1) at [n2 (N1 + 1) + k1]: a thread reads its
+// own row, and lanes with different n2 fall in different banks.
+template <typename V, int N>
+__device__ __forceinline__ void load_line_twiddles(V* s_tw2, const V* __restrict__ tw)
+{
+    constexpr int N1 = Shape<N>::N1, N2 = Shape<N>::N2;
+    for (int i = threadIdx.x; i < N1 * N2; i += blockDim.x) {
+        const int n2 = i / N1, k1 = i - n2 * N1;
+        s_tw2[n2 * (N1 + 1) + k1] = tw[(n2 * k1) & (N - 1)];
     }
+}
+
+template <typename V, int N>
+__device__ __forceinline__ void line_first(V* v, int n2, const V* __restrict__ s_tw, V* tr)
+{
+    constexpr int N1 = Shape<N>::N1;
+    dft_reg<N1>(v);
+    const V* row = s_tw + n2 * (N1 + 1);
+    sfor<N1>([&](auto K1) { tr[n2 * (N1 + 1) + K1] = cmul(v[K1], row[K1]); });
+}
+
+// Second level for k1 = t + g N2; out(k2, value) receives X[k1 + N1 k2].
+template <typename V, int N, typename Out>
+__device__ __forceinline__ void line_second(int t, const V* tr, Out&& out)
+{
+    constexpr int N1 = Shape<N>::N1, N2 = Shape<N>::N2, G = Shape<N>::G;
+    sfor<G>([&](auto Gi) {
+        const int k1 = t + Gi * N2;
+        V u[N2];
+        sfor<N2>([&](auto N2i) { u[N2i] = tr[N2i * (N1 + 1) + k1]; });
+        dft_reg<N2>(u);
+        sfor<N2>([&](auto K2) { out(k1 + N1 * K2, u[K2]); });
+    });
 }
 
 // ---- precision-dependent scalar math -------------------------------------
@@ -90,21 +205,17 @@ __device__ __forceinline__ void f_sincospi(double x, double* s, double* c) { sin
 
 __device__ __forceinline__ int sidx(int j, int N) { return j < (N >> 1) ? j : j - N; }
 
-// The four packed spectra of one mode (jx, jy, jz).  A[m], m = |n|^2, holds the
-// amplitude sqrt(P_R(k)/V) times T_psi, T_phi and a H dT_phi/dln a at this scale
-// factor (built in FP64 by k_mode_table); the mode supplies its unit Gaussian.
+// The unit Gaussian of mode (jx, jy, jz), R/sqrt(P_R/V): zero for the mean and the
+// Nyquist planes, conj of the mirror mode for non-canonical n.  Drawn once per run
+// by k_noise.
 template <typename V>
-__device__ __forceinline__ void mode_values(const FieldArgs& a, const typename Real<V>::T* __restrict__ A, int jx,
-                                            int jy, int jz, V out[4])
+__device__ __forceinline__ V mode_unit(const FieldArgs& a, int jx, int jy, int jz)
 {
     using T = typename Real<V>::T;
     const int N = a.N;
     const int nx = sidx(jx, N), ny = sidx(jy, N), nz = sidx(jz, N);
     const int h = -(N >> 1);
-    if (nx == h || ny == h || nz == h || (nx == 0 && ny == 0 && nz == 0)) {
-        out[0] = out[1] = out[2] = out[3] = mk<V>(T(0), T(0));
-        return;
-    }
+    if (nx == h || ny == h || nz == h || (nx == 0 && ny == 0 && nz == 0)) return mk<V>(T(0), T(0));
     const bool canon = nz > 0 || (nz == 0 && (ny > 0 || (ny == 0 && nx > 0)));
     const int mx = canon ? nx : -nx, my = canon ? ny : -ny, mz = canon ? nz : -nz;
     const uint64_t pack = (uint64_t)(uint32_t)(mx + (1 << 20)) | ((uint64_t)(uint32_t)(my + (1 << 20)) << 21) |
@@ -124,20 +235,37 @@ __device__ __forceinline__ void mode_values(const FieldArgs& a, const typename R
         im = r * s;
     }
     if (!canon) im = -im;
-    const int m = nx * nx + ny * ny + nz * nz;
-    const T Apsi = A[4 * m], Aphi = A[4 * m + 1], Adot = A[4 * m + 2];
-    const T kf = (T)a.kf;
-    const T kx = kf * (T)nx, ky = kf * (T)ny, kz = kf * (T)nz;
-    const V R = mk<V>(re, im);
+    return mk<V>(re, im);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_noise(FieldArgs a, V* __restrict__ R)
+{
+    const int N = a.N;
+    const size_t N3 = (size_t)N * N * N;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N3; c += (size_t)gridDim.x * blockDim.x) {
+        const int jx = (int)(c % N), jy = (int)((c / N) % N), jz = (int)(c / ((size_t)N * N));
+        R[c] = mode_unit<V>(a, jx, jy, jz);
+    }
+}
+
+// Packed spectrum p of a mode with unit Gaussian R and amplitudes (Apsi, Aphi, Adot):
+//   P0 = i kx Apsi R + i (i ky Apsi R)      (d_x psi + i d_y psi)
+//   P1 = i kz Apsi R + i (i kx Aphi R)      (d_z psi + i d_x phi)
+//   P2 = i ky Aphi R + i (i kz Aphi R)      (d_y phi + i d_z phi)
+//   P3 = Adot R + i Apsi R                  (phi_dot + i psi)
+template <typename V>
+__device__ __forceinline__ V packed(int p, V R, typename Real<V>::T Apsi, typename Real<V>::T Aphi,
+                                    typename Real<V>::T Adot, typename Real<V>::T kx, typename Real<V>::T ky,
+                                    typename Real<V>::T kz)
+{
     const V iR = cmuli(R);
-    // P0 = i kx Tpsi R + i (i ky Tpsi R) = Tpsi (kx iR - ky R)
-    out[0] = mk<V>(Apsi * (kx * iR.x - ky * R.x), Apsi * (kx * iR.y - ky * R.y));
-    // P1 = i kz Tpsi R - kx Tphi R
-    out[1] = mk<V>(kz * Apsi * iR.x - kx * Aphi * R.x, kz * Apsi * iR.y - kx * Aphi * R.y);
-    // P2 = i ky Tphi R - kz Tphi R
-    out[2] = mk<V>(Aphi * (ky * iR.x - kz * R.x), Aphi * (ky * iR.y - kz * R.y));
-    // P3 = aH dT R + i Tpsi R
-    out[3] = mk<V>(Adot * R.x + Apsi * iR.x, Adot * R.y + Apsi * iR.y);
+    switch (p) {
+        case 0: return mk<V>(Apsi * (kx * iR.x - ky * R.x), Apsi * (kx * iR.y - ky * R.y));
+        case 1: return mk<V>(kz * Apsi * iR.x - kx * Aphi * R.x, kz * Apsi * iR.y - kx * Aphi * R.y);
+        case 2: return mk<V>(Aphi * (ky * iR.x - kz * R.x), Aphi * (ky * iR.y - kz * R.y));
+        default: return mk<V>(Adot * R.x + Apsi * iR.x, Adot * R.y + Apsi * iR.y);
+    }
 }
 
 // Per scale factor, in FP64, for every m = |n|^2 in [0, M): k = k_f sqrt(m),
@@ -183,144 +311,159 @@ __global__ void __launch_bounds__(256) k_mode_table(FieldArgs a, int M, const do
     }
 }
 
-template <typename V>
-__device__ void load_twiddles(V* s_tw, const V* __restrict__ tw, int N)
-{
-    for (int i = threadIdx.x; i < N; i += blockDim.x) s_tw[i] = tw[i];
-}
-
 // ---- pass z: spectrum + inverse DFT along z ---------------------------------
-// Block (x-tile, jy): TX columns of N modes along z, all four packed spectra.
-template <typename V, int TX>
-__global__ void __launch_bounds__(kThreads) k_fields_z(FieldArgs a, const typename Real<V>::T* __restrict__ A,
-                                                       const V* __restrict__ tw, V* __restrict__ W0)
+// Block (x-tile, jy): TX columns along z.  Each thread reads the unit Gaussians of
+// its N1 modes once, with their amplitudes A[|n|^2] at this scale factor, then forms,
+// transforms and writes each of the four packed grids in turn.
+template <typename V, int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k_fields_z(FieldArgs a,
+                                                                  const typename Real<V>::T* __restrict__ A,
+                                                                  const V* __restrict__ R, const V* __restrict__ tw,
+                                                                  V* __restrict__ W0)
 {
+    using T = typename Real<V>::T;
+    using S = Shape<N>;
+    constexpr int TX = S::TZ, N1 = S::N1, N2 = S::N2, NT = S::THREADS_Z;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, LS = N + 1;
-    V* tiles = reinterpret_cast<V*>(smem_raw);
-    V* scratch = tiles + 4 * TX * LS;
-    V* s_tw = scratch + TX * LS;
-    load_twiddles(s_tw, tw, N);
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* tr = s_tw + S::TWS;                                  // TX * TSZ
+    T* As = reinterpret_cast<T*>(tr + TX * S::TSZ);         // [3][N1][NT]: each thread's own column
+    load_line_twiddles<V, N>(s_tw, tw);
+    const int xo = threadIdx.x % TX, t = threadIdx.x / TX;
     const int x0 = blockIdx.x * TX, jy = blockIdx.y;
-    for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
-        const int xo = e % TX, z = e / TX;
-        V v[4];
-        mode_values<V>(a, A, x0 + xo, jy, z, v);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) tiles[p * TX * LS + xo * LS + z] = v[p];
-    }
+    const int nx = sidx(x0 + xo, N), ny = sidx(jy, N), h = -(N >> 1);
+    const T kf = (T)a.kf;
+    const T kx = kf * (T)nx, ky = kf * (T)ny;
+    const size_t NN = (size_t)N * N;
+    V Rv[N1];
+    sfor<N1>([&](auto I) {
+        const int z = N2 * I + t;
+        const int nz = sidx(z, N);
+        Rv[I] = R[(size_t)z * NN + (size_t)jy * N + x0 + xo];
+        T ap = T(0), af = T(0), ad = T(0);
+        if (nx != h && ny != h && nz != h) {
+            const T* am = A + 4 * (nx * nx + ny * ny + nz * nz);
+            ap = am[0];
+            af = am[1];
+            ad = am[2];
+        }
+        As[(0 * N1 + I) * NT + threadIdx.x] = ap;
+        As[(1 * N1 + I) * NT + threadIdx.x] = af;
+        As[(2 * N1 + I) * NT + threadIdx.x] = ad;
+    });
     __syncthreads();
-    for (int p = 0; p < 4; ++p) smem_ifft_lines(tiles + p * TX * LS, scratch, N, a.logN, TX, LS, s_tw);
-    const size_t N3 = (size_t)N * N * N;
-    for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
-        const int xo = e % TX, z = e / TX;
-        const size_t g = ((size_t)z * N + jy) * N + x0 + xo;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) W0[p * N3 + g] = tiles[p * TX * LS + xo * LS + z];
+    const size_t N3 = NN * N;
+#pragma unroll 1
+    for (int p = 0; p < 4; ++p) {
+        V v[N1];
+        sfor<N1>([&](auto I) {
+            const T kz = kf * (T)sidx(N2 * I + t, N);
+            v[I] = packed<V>(p, Rv[I], As[(0 * N1 + I) * NT + threadIdx.x], As[(1 * N1 + I) * NT + threadIdx.x],
+                             As[(2 * N1 + I) * NT + threadIdx.x], kx, ky, kz);
+        });
+        line_first<V, N>(v, t, s_tw, tr + xo * S::TSZ);
+        __syncthreads();
+        V* dst = W0 + p * N3 + (size_t)jy * N + x0 + xo;
+        line_second<V, N>(t, tr + xo * S::TSZ, [&](int z, V val) { dst[(size_t)z * NN] = val; });
+        __syncthreads();
     }
 }
 
 // ---- pass y: inverse DFT along y --------------------------------------------
-// Block (x-tile, jz, packed grid p).
-template <typename V, int TX>
-__global__ void __launch_bounds__(kThreads) k_fields_y(FieldArgs a, const V* __restrict__ tw,
-                                                       const V* __restrict__ W0, V* __restrict__ W1)
+// Block (x-tile, jz, packed grid p): TX lines along y, read and written in rows of
+// TX consecutive x.
+template <typename V, int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS) k_fields_y(FieldArgs a, const V* __restrict__ tw,
+                                                                const V* __restrict__ W0, V* __restrict__ W1)
 {
+    using S = Shape<N>;
+    constexpr int TX = S::TX, N1 = S::N1, N2 = S::N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, LS = N + 1;
-    V* tile = reinterpret_cast<V*>(smem_raw);
-    V* scratch = tile + TX * LS;
-    V* s_tw = scratch + TX * LS;
-    load_twiddles(s_tw, tw, N);
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* tr = s_tw + S::TWS;
+    load_line_twiddles<V, N>(s_tw, tw);
+    const int xo = threadIdx.x % TX, t = threadIdx.x / TX;
     const int x0 = blockIdx.x * TX, jz = blockIdx.y, p = blockIdx.z;
     const size_t N3 = (size_t)N * N * N;
-    const V* src = W0 + p * N3 + (size_t)jz * N * N + x0;
-    for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
-        const int xo = e % TX, y = e / TX;
-        tile[xo * LS + y] = src[(size_t)y * N + xo];
-    }
+    const V* src = W0 + p * N3 + (size_t)jz * N * N + x0 + xo;
+    V v[N1];
+    sfor<N1>([&](auto N1i) { v[N1i] = src[(size_t)(N2 * N1i + t) * N]; });
     __syncthreads();
-    smem_ifft_lines(tile, scratch, N, a.logN, TX, LS, s_tw);
-    V* dst = W1 + p * N3 + (size_t)jz * N * N + x0;
-    for (int e = threadIdx.x; e < TX * N; e += blockDim.x) {
-        const int xo = e % TX, y = e / TX;
-        dst[(size_t)y * N + xo] = tile[xo * LS + y];
-    }
+    line_first<V, N>(v, t, s_tw, tr + xo * S::TS);
+    __syncthreads();
+    V* dst = W1 + p * N3 + (size_t)jz * N * N + x0 + xo;
+    line_second<V, N>(t, tr + xo * S::TS, [&](int y, V val) { dst[(size_t)y * N] = val; });
 }
 
 // ---- pass x: inverse DFT along x, interleave into G[cell][8] ----------------
-template <typename G> struct GStore;
-template <> struct GStore<float> {
-    __device__ static void put(float* G, size_t cell, const float v[8])
+// Block: TL consecutive x-lines (line index = jz * N + jy).  Grids 0..2 are parked
+// in shared memory as they finish; grid 3's results are written together with them,
+// so every cell's 8-slot record goes out in one piece.
+template <typename Gt, typename V> struct GRec;
+template <> struct GRec<float, float2> {
+    __device__ static void put(float* G, size_t cell, float2 a, float2 b, float2 c, float2 d)
     {
         float4* g = reinterpret_cast<float4*>(G) + 2 * cell;
-        g[0] = make_float4(v[0], v[1], v[2], v[3]);
-        g[1] = make_float4(v[4], v[5], v[6], v[7]);
+        g[0] = make_float4(a.x, a.y, b.x, b.y);
+        g[1] = make_float4(c.x, c.y, d.x, d.y);
     }
 };
-template <> struct GStore<double> {
-    __device__ static void put(double* G, size_t cell, const double v[8])
+template <> struct GRec<double, double2> {
+    __device__ static void put(double* G, size_t cell, double2 a, double2 b, double2 c, double2 d)
     {
         double2* g = reinterpret_cast<double2*>(G) + 4 * cell;
-        g[0] = make_double2(v[0], v[1]);
-        g[1] = make_double2(v[2], v[3]);
-        g[2] = make_double2(v[4], v[5]);
-        g[3] = make_double2(v[6], v[7]);
+        g[0] = a;
+        g[1] = b;
+        g[2] = c;
+        g[3] = d;
     }
 };
-template <> struct GStore<__nv_bfloat16> {
-    __device__ static void put(__nv_bfloat16* G, size_t cell, const float v[8])
+template <> struct GRec<__nv_bfloat16, float2> {
+    __device__ static void put(__nv_bfloat16* G, size_t cell, float2 a, float2 b, float2 c, float2 d)
     {
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y), h1 = __floats2bfloat162_rn(b.x, b.y);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(c.x, c.y), h3 = __floats2bfloat162_rn(d.x, d.y);
         uint4 u;
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]);
-        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[2], v[3]);
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]);
-        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[6], v[7]);
-        u.x = *reinterpret_cast<uint32_t*>(&h0);
-        u.y = *reinterpret_cast<uint32_t*>(&h1);
-        u.z = *reinterpret_cast<uint32_t*>(&h2);
-        u.w = *reinterpret_cast<uint32_t*>(&h3);
+        u.x = *reinterpret_cast<const uint32_t*>(&h0);
+        u.y = *reinterpret_cast<const uint32_t*>(&h1);
+        u.z = *reinterpret_cast<const uint32_t*>(&h2);
+        u.w = *reinterpret_cast<const uint32_t*>(&h3);
         reinterpret_cast<uint4*>(G)[cell] = u;
     }
 };
 
-// Block: TL consecutive x-lines (line index = jz * N + jy), all four grids.
-template <typename V, typename Gt, int TL>
-__global__ void __launch_bounds__(kThreads) k_fields_x(FieldArgs a, const V* __restrict__ tw,
-                                                       const V* __restrict__ W1, Gt* __restrict__ G)
+template <typename V, typename Gt, int N>
+__global__ void __launch_bounds__(Shape<N>::THREADS_X) k_fields_x(FieldArgs a, const V* __restrict__ tw,
+                                                                  const V* __restrict__ W1, Gt* __restrict__ G)
 {
-    using T = typename Real<V>::T;
+    using S = Shape<N>;
+    constexpr int TL = S::TL, N1 = S::N1, N2 = S::N2, T = S::T, LS = N + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = a.N, LS = N + 1;
-    V* tiles = reinterpret_cast<V*>(smem_raw);
-    V* scratch = tiles + 4 * TL * LS;
-    V* s_tw = scratch + TL * LS;
-    load_twiddles(s_tw, tw, N);
+    V* s_tw = reinterpret_cast<V*>(smem_raw);
+    V* tr = s_tw + S::TWS;          // TL * TSX
+    V* park = tr + TL * S::TSX;     // 3 * TL * LS: grids 0..2
+    load_line_twiddles<V, N>(s_tw, tw);
+    const int t = threadIdx.x % T, lo = threadIdx.x / T;
     const size_t N3 = (size_t)N * N * N;
-    const size_t l0 = (size_t)blockIdx.x * TL;
-    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
-        const int lo = e / N, x = e - lo * N;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) tiles[p * TL * LS + lo * LS + x] = W1[p * N3 + (l0 + lo) * N + x];
-    }
-    __syncthreads();
-    for (int p = 0; p < 4; ++p) smem_ifft_lines(tiles + p * TL * LS, scratch, N, a.logN, TL, LS, s_tw);
-    for (int e = threadIdx.x; e < TL * N; e += blockDim.x) {
-        const int lo = e / N, x = e - lo * N;
-        T v[8];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const V c = tiles[p * TL * LS + lo * LS + x];
-            v[2 * p] = c.x;
-            v[2 * p + 1] = c.y;
-        }
-        if constexpr (sizeof(Gt) == 2) {
-            float f[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) f[i] = (float)v[i];
-            GStore<Gt>::put(G, (l0 + lo) * N + x, f);
+    const size_t line = (size_t)blockIdx.x * TL + lo;
+#pragma unroll 1
+    for (int p = 0; p < 4; ++p) {
+        const V* src = W1 + p * N3 + line * N;
+        V v[N1];
+        sfor<N1>([&](auto N1i) { v[N1i] = src[N2 * N1i + t]; });
+        __syncthreads();
+        line_first<V, N>(v, t, s_tw, tr + lo * S::TSX);
+        __syncthreads();
+        if (p < 3) {
+            V* pk = park + (p * TL + lo) * LS;
+            line_second<V, N>(t, tr + lo * S::TSX, [&](int x, V val) { pk[x] = val; });
         } else {
-            GStore<Gt>::put(G, (l0 + lo) * N + x, v);
+            const V* p0 = park + lo * LS;
+            const V* p1 = park + (TL + lo) * LS;
+            const V* p2 = park + (2 * TL + lo) * LS;
+            line_second<V, N>(t, tr + lo * S::TSX, [&](int x, V val) {
+                GRec<Gt, V>::put(G, line * N + x, p0[x], p1[x], p2[x], val);
+            });
         }
     }
 }
@@ -350,29 +493,58 @@ __global__ void k_fields_from_f64(size_t N3, const double* __restrict__ in, Gt* 
         }
 }
 
-constexpr int kTile = 8;
-
-template <typename V>
-size_t smem_z(int N)
-{
-    return (size_t)(5 * kTile * (N + 1) + N) * sizeof(V);
-}
-template <typename V>
-size_t smem_y(int N)
-{
-    return (size_t)(2 * kTile * (N + 1) + N) * sizeof(V);
-}
-template <typename V>
-size_t smem_x(int N)
-{
-    return (size_t)(5 * kTile * (N + 1) + N) * sizeof(V);
-}
-
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes)
 {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
+
+template <typename V, int N>
+cudaError_t run_z(cudaStream_t s, const FieldArgs& a, const void* A, const void* R, const void* tw, void* W0)
+{
+    using S = Shape<N>;
+    using T = typename Real<V>::T;
+    const size_t sm = (size_t)(S::TWS + S::TZ * S::TSZ) * sizeof(V) + (size_t)3 * S::N1 * S::THREADS_Z * sizeof(T);
+    cudaError_t e = set_smem(k_fields_z<V, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_fields_z<V, N><<<dim3(N / S::TZ, N), S::THREADS_Z, sm, s>>>(a, (const T*)A, (const V*)R, (const V*)tw, (V*)W0);
+    return cudaGetLastError();
+}
+
+template <typename V, int N>
+cudaError_t run_y(cudaStream_t s, const FieldArgs& a, const void* tw, const void* W0, void* W1)
+{
+    using S = Shape<N>;
+    const size_t sm = (size_t)(S::TWS + S::TX * S::TS) * sizeof(V);
+    cudaError_t e = set_smem(k_fields_y<V, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_fields_y<V, N><<<dim3(N / S::TX, N, 4), S::THREADS, sm, s>>>(a, (const V*)tw, (const V*)W0, (V*)W1);
+    return cudaGetLastError();
+}
+
+template <typename V, typename Gt, int N>
+cudaError_t run_x(cudaStream_t s, const FieldArgs& a, const void* tw, const void* W1, void* G)
+{
+    using S = Shape<N>;
+    const size_t sm = (size_t)(S::TWS + S::TL * S::TSX + 3 * S::TL * (N + 1)) * sizeof(V);
+    cudaError_t e = set_smem(k_fields_x<V, Gt, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_fields_x<V, Gt, N><<<(unsigned)((size_t)N * N / S::TL), S::THREADS_X, sm, s>>>(a, (const V*)tw, (const V*)W1,
+                                                                                    (Gt*)G);
+    return cudaGetLastError();
+}
+
+#define FDF_DISPATCH_N(N, CALL)                     \
+    switch (N) {                                    \
+        case 8: return CALL(8);                     \
+        case 16: return CALL(16);                   \
+        case 32: return CALL(32);                   \
+        case 64: return CALL(64);                   \
+        case 128: return CALL(128);                 \
+        case 256: return CALL(256);                 \
+        case 512: return CALL(512);                 \
+        default: return cudaErrorInvalidValue;      \
+    }
 
 }  // namespace
 
@@ -387,68 +559,49 @@ cudaError_t launch_mode_table(cudaStream_t s, int precision, const FieldArgs& a,
     return cudaGetLastError();
 }
 
-cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* A, const void* tw,
-                            void* W0)
+cudaError_t launch_noise(cudaStream_t s, int precision, const FieldArgs& a, void* R)
 {
-    const dim3 grid(a.N / kTile, a.N);
-    if (precision == FDF_PREC_F64) {
-        const size_t sm = smem_z<double2>(a.N);
-        cudaError_t e = set_smem(k_fields_z<double2, kTile>, sm);
-        if (e != cudaSuccess) return e;
-        k_fields_z<double2, kTile><<<grid, kThreads, sm, s>>>(a, (const double*)A, (const double2*)tw,
-                                                              (double2*)W0);
-    } else {
-        const size_t sm = smem_z<float2>(a.N);
-        cudaError_t e = set_smem(k_fields_z<float2, kTile>, sm);
-        if (e != cudaSuccess) return e;
-        k_fields_z<float2, kTile><<<grid, kThreads, sm, s>>>(a, (const float*)A, (const float2*)tw, (float2*)W0);
-    }
+    const size_t N3 = (size_t)a.N * a.N * a.N;
+    const unsigned blocks = (unsigned)((N3 + 255) / 256 < 152 * 32 ? (N3 + 255) / 256 : 152 * 32);
+    if (precision == FDF_PREC_F64) k_noise<double2><<<blocks, 256, 0, s>>>(a, (double2*)R);
+    else k_noise<float2><<<blocks, 256, 0, s>>>(a, (float2*)R);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fields_z(cudaStream_t s, int precision, const FieldArgs& a, const void* A, const void* R,
+                            const void* tw, void* W0)
+{
+#define Z64(n) run_z<double2, n>(s, a, A, R, tw, W0)
+#define Z32(n) run_z<float2, n>(s, a, A, R, tw, W0)
+    if (precision == FDF_PREC_F64) FDF_DISPATCH_N(a.N, Z64)
+    FDF_DISPATCH_N(a.N, Z32)
+#undef Z64
+#undef Z32
 }
 
 cudaError_t launch_fields_y(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W0,
                             void* W1)
 {
-    const dim3 grid(a.N / kTile, a.N, 4);
-    if (precision == FDF_PREC_F64) {
-        const size_t sm = smem_y<double2>(a.N);
-        cudaError_t e = set_smem(k_fields_y<double2, kTile>, sm);
-        if (e != cudaSuccess) return e;
-        k_fields_y<double2, kTile><<<grid, kThreads, sm, s>>>(a, (const double2*)tw, (const double2*)W0,
-                                                              (double2*)W1);
-    } else {
-        const size_t sm = smem_y<float2>(a.N);
-        cudaError_t e = set_smem(k_fields_y<float2, kTile>, sm);
-        if (e != cudaSuccess) return e;
-        k_fields_y<float2, kTile><<<grid, kThreads, sm, s>>>(a, (const float2*)tw, (const float2*)W0, (float2*)W1);
-    }
-    return cudaGetLastError();
+#define Y64(n) run_y<double2, n>(s, a, tw, W0, W1)
+#define Y32(n) run_y<float2, n>(s, a, tw, W0, W1)
+    if (precision == FDF_PREC_F64) FDF_DISPATCH_N(a.N, Y64)
+    FDF_DISPATCH_N(a.N, Y32)
+#undef Y64
+#undef Y32
 }
 
 cudaError_t launch_fields_x(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W1,
                             void* G)
 {
-    const unsigned blocks = (unsigned)((size_t)a.N * a.N / kTile);
-    if (precision == FDF_PREC_F64) {
-        const size_t sm = smem_x<double2>(a.N);
-        cudaError_t e = set_smem(k_fields_x<double2, double, kTile>, sm);
-        if (e != cudaSuccess) return e;
-        k_fields_x<double2, double, kTile><<<blocks, kThreads, sm, s>>>(a, (const double2*)tw, (const double2*)W1,
-                                                                       (double*)G);
-    } else if (precision == FDF_PREC_F32) {
-        const size_t sm = smem_x<float2>(a.N);
-        cudaError_t e = set_smem(k_fields_x<float2, float, kTile>, sm);
-        if (e != cudaSuccess) return e;
-        k_fields_x<float2, float, kTile><<<blocks, kThreads, sm, s>>>(a, (const float2*)tw, (const float2*)W1,
-                                                                     (float*)G);
-    } else {
-        const size_t sm = smem_x<float2>(a.N);
-        cudaError_t e = set_smem(k_fields_x<float2, __nv_bfloat16, kTile>, sm);
-        if (e != cudaSuccess) return e;
-        k_fields_x<float2, __nv_bfloat16, kTile><<<blocks, kThreads, sm, s>>>(a, (const float2*)tw,
-                                                                             (const float2*)W1, (__nv_bfloat16*)G);
-    }
-    return cudaGetLastError();
+#define X64(n) run_x<double2, double, n>(s, a, tw, W1, G)
+#define X32(n) run_x<float2, float, n>(s, a, tw, W1, G)
+#define X16(n) run_x<float2, __nv_bfloat16, n>(s, a, tw, W1, G)
+    if (precision == FDF_PREC_F64) FDF_DISPATCH_N(a.N, X64)
+    if (precision == FDF_PREC_F32) FDF_DISPATCH_N(a.N, X32)
+    FDF_DISPATCH_N(a.N, X16)
+#undef X64
+#undef X32
+#undef X16
 }
 
 cudaError_t launch_fields_to_f64(cudaStream_t s, int precision, int N, const void* G, double* out)

@@ -35,12 +35,13 @@ unsigned grid_for(int64_t n, int per_sm = 16)
 // ---- grid reads ------------------------------------------------------------
 template <typename Gt> struct Cell;
 template <> struct Cell<float> {
+    // one 256-bit load per cell (a cell's 8 slots are 32 contiguous, 32-byte aligned bytes)
     __device__ static void load(const float* G, uint32_t c, float v[8])
     {
-        const float4* g = reinterpret_cast<const float4*>(G) + 2 * (size_t)c;
-        const float4 a = __ldg(g), b = __ldg(g + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        const float* g = G + 8 * (size_t)c;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+            : "l"(g));
     }
 };
 template <> struct Cell<__nv_bfloat16> {
