@@ -113,7 +113,9 @@ typedef struct fdf_params {
     int32_t  sort_every;       /* re-bucket particles by position (gather locality): 0 = after
                                   sampling and whenever the typical displacement since the last
                                   sort exceeds four sort tiles; k > 0 = every k steps; -1 = never */
-    int32_t  reserved;
+    int32_t  steps_per_pass;   /* leapfrog steps per particle pass, 1..4: the particle state is
+                                  read and written once per pass (0 = 4 for the split forms,
+                                  1 for the plain FP64 form) */
 } fdf_params;
 
 /* Input tables, host memory, copied by fdf_create.

@@ -105,14 +105,29 @@ struct StateLayout {
     size_t X, q0f, dqf, xd, qd, q0d, pmag, id;
 };
 
+// Steps per particle pass: the caller's choice, else 4 for the split forms (the
+// particle state is read and written once per 4 steps) and 1 for the plain form.
+int steps_per_pass(const fdf_params& p)
+{
+    if (p.steps_per_pass > 0) return p.steps_per_pass;
+    return p.precision == FDF_PREC_F64 ? 1 : kMaxSub - 1;
+}
+
+// Grids held at once: the current pass's (its steps plus the opening kick's) and
+// the next pass's, which are built on a second stream while the current pass runs.
+constexpr int kMaxBuf = 2 * (kMaxSub - 1) + 1;
+int grid_buffers(const fdf_params& p) { return std::min(kMaxBuf, 2 * steps_per_pass(p) + 1); }
+
 struct Layout {
-    size_t tabs, modeA, noise, cdf_t, cdf_F, tw, W0, W1, G0, G1, qs, stage, dep, flag, key, hist, bsum, total;
+    size_t tabs, modeA, noise, cdf_t, cdf_F, tw, W0, W1, G[kMaxBuf], qs, stage, dep, flag, key, hist, bsum, recs,
+        total;
+    int nbuf;
     StateLayout s[2];
 };
 
-int sort_bins(const fdf_params& p)
+int64_t sort_bins(const fdf_params& p)
 {
-    const int tpa = p.n_grid >> sort_tile_shift(p.n_grid);
+    const int64_t tpa = p.n_grid >> sort_tile_shift(p.n_grid);
     return tpa * tpa * tpa * p.n_species;
 }
 
@@ -136,8 +151,8 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     L.tw = take(N * complex_bytes(prec));
     L.W0 = take(4 * N3 * complex_bytes(prec));
     L.W1 = take(4 * N3 * complex_bytes(prec));
-    L.G0 = take(N3 * grid_bytes_per_cell(prec));
-    L.G1 = take(N3 * grid_bytes_per_cell(prec));
+    L.nbuf = grid_buffers(p);
+    for (int b = 0; b < L.nbuf; ++b) L.G[b] = take(N3 * grid_bytes_per_cell(prec));
     const bool split = prec != FDF_PREC_F64;
     const bool sorts = p.sort_every >= 0;
     for (int h = 0; h < (sorts ? 2 : 1); ++h) {
@@ -157,7 +172,9 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     L.qs = take(3 * n * 8);
     L.key = take(sorts ? n * 4 : 0);
     L.hist = take(sorts ? (size_t)sort_bins(p) * 4 : 0);
-    L.bsum = take(sorts ? 1024 * 4 : 0);
+    // scan totals of every level: bins/1024 + bins/1024^2 + ... < bins/1000 + 3
+    L.bsum = take(sorts ? ((size_t)sort_bins(p) / 1000 + 64) * 4 : 0);
+    L.recs = take(sorts ? n * sort_record_bytes(prec) : 0);
     L.stage = take(7 * (size_t)p.n_part * 8);
     L.dep = take(N3 * 8);
     L.flag = take(64);
@@ -198,6 +215,8 @@ int fdf::validate_params(const fdf_params* p)
     if (!(p->omega_r / (a0 * a0 * a0 * a0) + p->omega_m / (a0 * a0 * a0) + ol > 0))
         return fail(FDF_EINVAL, "H^2 <= 0 at z_start");
     if (p->sort_every < -1) return fail(FDF_EINVAL, "sort_every must be -1, 0 or a step count");
+    if (p->steps_per_pass < 0 || p->steps_per_pass > kMaxSub - 1)
+        return fail(FDF_EINVAL, "steps_per_pass must be 0 (automatic) or 1..4");
     return FDF_OK;
 }
 
@@ -221,8 +240,10 @@ struct fdf_ctx {
     fdf_params p{};
     cudaStream_t stream = nullptr;
     int64_t n = 0;
-    int ngl = 4;
-    double glx[kMaxGL]{}, glw[kMaxGL]{};
+    int ngl = 4, nkick = 4;
+    double glx[kMaxGL]{}, glw[kMaxGL]{};    // drift rule
+    double glxk[kMaxGL]{}, glwk[kMaxGL]{};  // kick rule
+    int uniform = 0;                        // all species share one mass
     double T_ev = 0, H0 = 0, ol = 0, lna0 = 0, lnaN = 0, dlna = 0, a0 = 0, tau0 = 0;
     int nk = 0, na = 0, ncdf = 0;
     double lnk0 = 0, dlnk = 0, lnat0 = 0, dlnat = 0;
@@ -238,9 +259,15 @@ struct fdf_ctx {
     void* tw = nullptr;
     void* W0 = nullptr;
     void* W1 = nullptr;
-    void* G[2] = {nullptr, nullptr};
-    int gk[2] = {-1, -1};
-    int cur = 0;
+    int nbuf = 0;
+    void* G[kMaxBuf] = {};
+    int gk[kMaxBuf];                     // step index whose fields each buffer holds (-1: none)
+    cudaEvent_t built[kMaxBuf] = {};     // recorded on the fields stream after a build
+    cudaEvent_t released[kMaxBuf] = {};  // recorded on the main stream after the last read
+    bool has_release[kMaxBuf] = {};
+    cudaStream_t sf = nullptr;           // the fields stream
+    cudaEvent_t joined = nullptr;
+    int spp = 1;                         // steps per particle pass
     void* Gfrozen = nullptr;
     bool frozen = false;
     ParticleState st{};       // the live state
@@ -248,6 +275,7 @@ struct fdf_ctx {
     uint32_t* key = nullptr;
     uint32_t* hist = nullptr;
     uint32_t* bsum = nullptr;
+    void* recs = nullptr;
     double disp = 0;          // typical displacement (Mpc) since the last sort
     int64_t sorts = 0;
     double* stage = nullptr;
@@ -293,24 +321,30 @@ cudaEvent_t take_event(fdf_ctx* c)
     return c->pool[c->pool_used++];
 }
 
-// Runs one launch, bracketed by events when timing is on.
+// Runs one launch on stream s, bracketed by events when timing is on.
 template <typename F>
-int timed(fdf_ctx* c, int cls, const char* what, F&& launch)
+int timed_on(fdf_ctx* c, cudaStream_t s, int cls, const char* what, F&& launch)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->timing) {
         e0 = take_event(c);
         e1 = take_event(c);
-        if (e0) cudaEventRecord(e0, c->stream);
+        if (e0) cudaEventRecord(e0, s);
     }
     cudaError_t e = launch();
     ++c->launches;
     if (e != cudaSuccess) return cuda_fail(e, what);
     if (c->timing && e0 && e1) {
-        cudaEventRecord(e1, c->stream);
+        cudaEventRecord(e1, s);
         c->marks.push_back({cls, {e0, e1}});
     }
     return FDF_OK;
+}
+
+template <typename F>
+int timed(fdf_ctx* c, int cls, const char* what, F&& launch)
+{
+    return timed_on(c, c->stream, cls, what, launch);
 }
 
 // Conformal time from a = 0: tau(a0) = int_0^a0 da / (a^2 H), a 32-point
@@ -328,19 +362,23 @@ double tau_of(const fdf_ctx* c, double a)
     return 0.5 * a * s / c->H0;
 }
 
-// Gauss-Legendre nodes of [l1, l2] in ln a: weights W_j (dtau) and a_j^2.
-void nodes(const fdf_ctx* c, double l1, double l2, double* W, double* a2)
+// Gauss-Legendre nodes of [l1, l2] in ln a (the drift rule, or the kick rule if
+// kick): weights W_j (dtau) and a_j^2.
+void nodes(const fdf_ctx* c, double l1, double l2, double* W, double* a2, bool kick = false)
 {
     const double half = 0.5 * (l2 - l1), mid = 0.5 * (l1 + l2);
-    for (int j = 0; j < c->ngl; ++j) {
-        const double a = std::exp(mid + half * c->glx[j]);
-        W[j] = c->glw[j] * half / (a * c->hubble(a));
+    const int n = kick ? c->nkick : c->ngl;
+    const double* x = kick ? c->glxk : c->glx;
+    const double* w = kick ? c->glwk : c->glw;
+    for (int j = 0; j < n; ++j) {
+        const double a = std::exp(mid + half * x[j]);
+        W[j] = w[j] * half / (a * c->hubble(a));
         a2[j] = a * a;
     }
 }
 
-// Coefficients of one particle pass: drift over [d1, d2] (if any), kick over [k1, k2] (if any).
-void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, double k1, double k2, PushArgs& a)
+// Constants of a particle pass that do not depend on the sub-steps.
+void fill_pass(const fdf_ctx* c, PushArgs& a)
 {
     std::memset(&a, 0, sizeof(a));
     a.n = c->n;
@@ -348,19 +386,29 @@ void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, do
     for (int s = 0; s < kMaxSpecies; ++s)
         a.sp_begin[s] = s + 1 < c->p.n_species ? (int64_t)(s + 1) * c->p.n_part : INT64_MAX;
     a.n_gl = c->ngl;
-    a.do_drift = drift;
-    a.do_kick = kick;
+    a.n_kick = c->nkick;
+    a.uniform_species = c->uniform;
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
     a.invL = 1.0 / c->p.box_mpc;
     a.invh = c->p.n_grid / c->p.box_mpc;
     a.fx_scale = split_ff(4294967296.0 / c->p.box_mpc);
+}
+
+// Coefficients of one sub-step: drift over [d1, d2] (if any), kick over [k1, k2] (if any).
+// The split form's drift weights carry the factor 2^32/L (position quanta per Mpc).
+void fill_substep(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, double k1, double k2, SubStep& u)
+{
+    std::memset(&u, 0, sizeof(u));
+    u.do_drift = drift;
+    u.do_kick = kick;
     double Wd[kMaxGL], ad[kMaxGL], Wk[kMaxGL], ak[kMaxGL];
     if (drift) nodes(c, d1, d2, Wd, ad);
-    if (kick) nodes(c, k1, k2, Wk, ak);
+    if (kick) nodes(c, k1, k2, Wk, ak, true);
     const int jc = c->ngl / 2;
+    const double q32 = 4294967296.0 / c->p.box_mpc;
     for (int s = 0; s < c->p.n_species; ++s) {
-        SpeciesCoef& sc = a.sp[s];
+        SpeciesCoef& sc = u.sp[s];
         const double m2 = c->p.m_ev[s] * c->p.m_ev[s];
         if (drift) {
             double sum = 0;
@@ -369,16 +417,16 @@ void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, do
                 sc.mud[j] = m2 * ad[j];
                 sum += Wd[j];
             }
-            sc.Wd_sum = split_ff(sum);
+            sc.Wd_sum = split_ff(sum * q32);
             sc.mud_c = split_ff(sc.mud[jc]);
             for (int j = 0; j < c->ngl; ++j) {
-                sc.Wd_f[j] = (float)Wd[j];
+                sc.Wd_f[j] = (float)(Wd[j] * q32);
                 sc.dmud_f[j] = (float)(sc.mud[j] - sc.mud[jc]);
             }
         }
         if (kick) {
             double dt = 0;
-            for (int j = 0; j < c->ngl; ++j) {
+            for (int j = 0; j < c->nkick; ++j) {
                 sc.Wk[j] = Wk[j];
                 sc.muk[j] = m2 * ak[j];
                 sc.Wk_f[j] = (float)Wk[j];
@@ -391,48 +439,117 @@ void fill_push(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, do
     }
 }
 
-// The unit Gaussian field of the run (a function of the seed and the mesh only).
+// The unit Gaussian field of the run (a function of the seed and the mesh only),
+// on the fields stream.
 int draw_noise(fdf_ctx* c)
 {
     const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, c->lna0);
-    int rc = timed(c, FDF_K_FIELDS_Z, "noise", [&] { return launch_noise(c->stream, c->p.precision, a, c->noise); });
+    int rc = timed_on(c, c->sf, FDF_K_FIELDS_Z, "noise",
+                      [&] { return launch_noise(c->sf, c->p.precision, a, c->noise); });
     if (rc == FDF_OK) c->noise_ready = true;
     return rc;
 }
 
-int build_fields(fdf_ctx* c, double lna, void* G)
+// The eight fields at ln a into G, on stream s.
+int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s)
 {
     if (!c->noise_ready) {
+        if (s != c->sf) FDF_CUDA(cudaStreamSynchronize(c->stream), "sync");
         int rc0 = draw_noise(c);
         if (rc0) return rc0;
+        if (s != c->sf) FDF_CUDA(cudaStreamSynchronize(c->sf), "sync");
     }
     const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
     const int prec = c->p.precision;
-    int rc = timed(c, FDF_K_FIELDS_Z, "mode table",
-                   [&] { return launch_mode_table(c->stream, prec, a, c->tabs, c->modeA); });
+    int rc = timed_on(c, s, FDF_K_FIELDS_Z, "mode table",
+                      [&] { return launch_mode_table(s, prec, a, c->tabs, c->modeA); });
     if (rc) return rc;
-    rc = timed(c, FDF_K_FIELDS_Z, "fields z pass",
-               [&] { return launch_fields_z(c->stream, prec, a, c->modeA, c->noise, c->tw, c->W0); });
+    rc = timed_on(c, s, FDF_K_FIELDS_Z, "fields z pass",
+                  [&] { return launch_fields_z(s, prec, a, c->modeA, c->noise, c->tw, c->W0); });
     if (rc) return rc;
-    rc = timed(c, FDF_K_FIELDS_Y, "fields y pass",
-               [&] { return launch_fields_y(c->stream, prec, a, c->tw, c->W0, c->W1); });
+    rc = timed_on(c, s, FDF_K_FIELDS_Y, "fields y pass",
+                  [&] { return launch_fields_y(s, prec, a, c->tw, c->W0, c->W1); });
     if (rc) return rc;
-    return timed(c, FDF_K_FIELDS_X, "fields x pass",
-                 [&] { return launch_fields_x(c->stream, prec, a, c->tw, c->W1, G); });
+    return timed_on(c, s, FDF_K_FIELDS_X, "fields x pass",
+                    [&] { return launch_fields_x(s, prec, a, c->tw, c->W1, G); });
 }
 
-int push(fdf_ctx* c, const PushArgs& a, const void* G)
+int push(fdf_ctx* c, const PushArgs& a)
 {
-    return timed(c, FDF_K_PUSH, "particle pass", [&] { return launch_push(c->stream, c->p.precision, c->st, a, G); });
+    return timed(c, FDF_K_PUSH, "particle pass", [&] { return launch_push(c->stream, c->p.precision, c->st, a); });
 }
 
-const void* grid_for_step(fdf_ctx* c, int buf) { return c->frozen ? c->Gfrozen : c->G[buf]; }
+// The buffer holding the fields of step k, or -1.
+int find_grid(const fdf_ctx* c, int k)
+{
+    for (int b = 0; b < c->nbuf; ++b)
+        if (c->gk[b] == k) return b;
+    return -1;
+}
+
+// Make the fields of step k available: the frozen set, a buffer that holds them
+// already, or a buffer outside `busy` (a bit mask) built now on the fields
+// stream, after the last pass that read that buffer.  The caller makes the main
+// stream wait for c->built[*buf] before reading.
+int ensure_grid(fdf_ctx* c, int k, unsigned busy, const void** G, int* buf)
+{
+    if (c->frozen) {
+        *G = c->Gfrozen;
+        *buf = -1;
+        return FDF_OK;
+    }
+    int b = find_grid(c, k);
+    if (b < 0) {
+        for (int i = 0; i < c->nbuf; ++i) {
+            const int cand = ((k % c->nbuf) + c->nbuf + i) % c->nbuf;
+            if (!(busy & (1u << cand))) {
+                b = cand;
+                break;
+            }
+        }
+        if (b < 0) return fail(FDF_EINVAL, "no free grid buffer");
+        c->gk[b] = -1;
+        if (c->has_release[b]) FDF_CUDA(cudaStreamWaitEvent(c->sf, c->released[b], 0), "wait release");
+        int rc = build_fields(c, c->lna(k), c->G[b], c->sf);
+        if (rc) return rc;
+        FDF_CUDA(cudaEventRecord(c->built[b], c->sf), "record build");
+        c->gk[b] = k;
+    }
+    *G = c->G[b];
+    *buf = b;
+    return FDF_OK;
+}
+
+// The main stream reads buffer b next: wait for its build.
+int acquire_grid(fdf_ctx* c, int b)
+{
+    if (b >= 0) FDF_CUDA(cudaStreamWaitEvent(c->stream, c->built[b], 0), "wait build");
+    return FDF_OK;
+}
+
+// The main stream has issued its last read of buffer b.
+int release_grid(fdf_ctx* c, int b)
+{
+    if (b >= 0) {
+        FDF_CUDA(cudaEventRecord(c->released[b], c->stream), "record release");
+        c->has_release[b] = true;
+    }
+    return FDF_OK;
+}
+
+// Everything issued on the fields stream precedes later work on the main stream.
+int join_fields(fdf_ctx* c)
+{
+    FDF_CUDA(cudaEventRecord(c->joined, c->sf), "record join");
+    FDF_CUDA(cudaStreamWaitEvent(c->stream, c->joined, 0), "wait join");
+    return FDF_OK;
+}
 
 int sort_particles(fdf_ctx* c)
 {
     int rc = timed(c, FDF_K_SORT, "sort", [&] {
         return launch_sort(c->stream, c->p.precision, c->st, c->st_alt, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
-                           c->p.n_species, c->p.n_grid, c->p.box_mpc, c->key, c->hist, c->bsum);
+                           c->p.n_species, c->p.n_grid, c->p.box_mpc, c->key, c->hist, c->bsum, c->recs);
     });
     if (rc) return rc;
     std::swap(c->st, c->st_alt);
@@ -456,15 +573,14 @@ double typical_displacement(const fdf_ctx* c, double l1, double l2)
     return std::fabs(dt) * q / std::sqrt(q * q + mmin * mmin * a * a);
 }
 
-// Sort after the pass that moved the particles over [l1, l2] if the schedule says so.
-int maybe_sort(fdf_ctx* c, int steps_done, double l1, double l2)
+// Sort between passes if the schedule says so (c->disp accumulates per step).
+int maybe_sort(fdf_ctx* c, int steps_done)
 {
     const int every = c->p.sort_every;
     if (every < 0 || c->n == 0) return FDF_OK;
-    c->disp += typical_displacement(c, l1, l2);
     bool go;
     if (every > 0) {
-        go = steps_done % every == 0;
+        go = steps_done % every < c->spp;
     } else {
         // The gather's working set stays in L2 long after a sort (the touched
         // region grows with the displacement but stays far below L2), so sort
@@ -549,7 +665,21 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     c->dlna = (c->lnaN - c->lna0) / p->n_steps;
     if (c->p.n_gl == 0) c->p.n_gl = auto_nodes(c->dlna);
     c->ngl = c->p.n_gl;
+    if (c->p.precision != FDF_PREC_F64) {
+        // the split form's pass is compiled for 3, 4, 5, 6 or 8 drift nodes, and its
+        // kick (needed to ~1e-7) takes half as many: the error of an n-point rule falls
+        // like rho^(-2n), so ceil(n/2) nodes give about the square root of the drift's
+        static const int supported[] = {3, 3, 3, 4, 5, 6, 8, 8, 8};
+        c->ngl = supported[c->ngl];
+        c->nkick = (c->ngl + 1) / 2;
+    } else {
+        c->nkick = c->ngl;
+    }
     gauss_legendre(c->ngl, c->glx, c->glw);
+    gauss_legendre(c->nkick, c->glxk, c->glwk);
+    c->uniform = 1;
+    for (int s = 1; s < p->n_species; ++s)
+        if (p->m_ev[s] != p->m_ev[0]) c->uniform = 0;
     c->a0 = std::exp(c->lna0);
     c->tau0 = tau_of(c, c->a0);
     c->nk = t->nk;
@@ -589,8 +719,10 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     c->tw = b + L.tw;
     c->W0 = b + L.W0;
     c->W1 = b + L.W1;
-    c->G[0] = b + L.G0;
-    c->G[1] = b + L.G1;
+    c->nbuf = L.nbuf;
+    c->spp = steps_per_pass(c->p);
+    for (int i = 0; i < kMaxBuf; ++i) c->gk[i] = -1;
+    for (int i = 0; i < L.nbuf; ++i) c->G[i] = b + L.G[i];
     ParticleState* S2[2] = {&c->st, &c->st_alt};
     for (int h = 0; h < 2; ++h) {
         const StateLayout& S = L.s[h];
@@ -607,6 +739,7 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     c->key = (uint32_t*)(b + L.key);
     c->hist = (uint32_t*)(b + L.hist);
     c->bsum = (uint32_t*)(b + L.bsum);
+    c->recs = b + L.recs;
     c->stage = (double*)(b + L.stage);
     c->dep = (double*)(b + L.dep);
     c->dflag = (int*)(b + L.flag);
@@ -634,6 +767,12 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     if (e == cudaSuccess) e = cudaMemcpy(c->cdf_t, t->cdf_t, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->cdf_F, t->cdf_F, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->dflag, 0, 64);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sf, cudaStreamNonBlocking);
+    for (int i = 0; i < c->nbuf && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&c->built[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->released[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->joined, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "uploading tables");
         fdf_destroy(c);
@@ -653,19 +792,21 @@ int fdf_sample(fdf_ctx* c)
                              c->st.pmag, c->st.id, c->dflag);
     });
     if (rc) return rc;
-    c->cur = 0;
-    c->gk[0] = c->gk[1] = -1;
+    for (int i = 0; i < kMaxBuf; ++i) c->gk[i] = -1;
     rc = draw_noise(c);
     if (rc) return rc;
-    if (!c->frozen) {
-        rc = build_fields(c, c->lna(0), c->G[0]);
-        if (rc) return rc;
-        c->gk[0] = 0;
-    }
+    const void* G0 = nullptr;
+    int b0 = -1;
+    rc = ensure_grid(c, 0, 0u, &G0, &b0);
+    if (rc) return rc;
+    rc = acquire_grid(c, b0);
+    if (rc) return rc;
     rc = timed(c, FDF_K_OTHER, "initial transform", [&] {
         return launch_initial(c->stream, c->p.precision, c->st, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
-                              c->p.m_ev, c->a0, c->tau0, c->p.n_grid, c->p.box_mpc, grid_for_step(c, 0));
+                              c->p.m_ev, c->a0, c->tau0, c->p.n_grid, c->p.box_mpc, G0);
     });
+    if (rc) return rc;
+    rc = release_grid(c, b0);
     if (rc) return rc;
     if (c->p.sort_every >= 0 && c->n > 0) {
         rc = sort_particles(c);
@@ -691,37 +832,83 @@ int fdf_step(fdf_ctx* c, int32_t n)
     c->stepped = true;
     const int dir = n > 0 ? 1 : -1;
     const int steps = n > 0 ? n : -n;
-    int rc;
-    if (!c->frozen && c->gk[c->cur] != c->k) {
-        rc = build_fields(c, c->lna(c->k), c->G[c->cur]);
-        if (rc) return rc;
-        c->gk[c->cur] = c->k;
-    }
-    PushArgs a;
-    fill_push(c, false, 0, 0, true, c->lna(c->k), c->lna(c->k + 0.5 * dir), a);
-    rc = push(c, a, grid_for_step(c, c->cur));
+    const int k_start = c->k;
+    // Passes of up to spp leapfrog steps; pass j covers steps [first_j, first_j + len_j).
+    // The grids of pass j+1 are built on the fields stream while pass j runs.
+    auto pass_first = [&](int j) { return j * c->spp; };
+    auto pass_len = [&](int j) { return std::min(c->spp, steps - j * c->spp); };
+    const int passes = (steps + c->spp - 1) / c->spp;
+    std::vector<int> bufs_cur, bufs_next;
+    std::vector<const void*> grids_cur, grids_next;
+    auto prepare = [&](int j, std::vector<int>& bufs, std::vector<const void*>& grids, unsigned busy) -> int {
+        bufs.clear();
+        grids.clear();
+        std::vector<int> ks;
+        if (j == 0) ks.push_back(k_start);                       // the opening half kick
+        for (int i = 0; i < pass_len(j); ++i) ks.push_back(k_start + dir * (pass_first(j) + i + 1));
+        for (int kk : ks) {
+            const void* G = nullptr;
+            int b = -1;
+            int rc = ensure_grid(c, kk, busy, &G, &b);
+            if (rc) return rc;
+            if (b >= 0) busy |= 1u << b;
+            bufs.push_back(b);
+            grids.push_back(G);
+        }
+        return FDF_OK;
+    };
+    auto mask_of = [](const std::vector<int>& bufs) {
+        unsigned m = 0;
+        for (int b : bufs)
+            if (b >= 0) m |= 1u << b;
+        return m;
+    };
+    int rc = prepare(0, bufs_cur, grids_cur, 0u);
     if (rc) return rc;
-    for (int i = 0; i < steps; ++i) {
-        const int k1 = c->k + dir;
-        const int nxt = c->cur ^ 1;
-        if (!c->frozen) {
-            rc = build_fields(c, c->lna(k1), c->G[nxt]);
+    for (int j = 0; j < passes; ++j) {
+        if (j + 1 < passes) {
+            rc = prepare(j + 1, bufs_next, grids_next, mask_of(bufs_cur));
             if (rc) return rc;
-            c->gk[nxt] = k1;
         }
-        const bool last = i == steps - 1;
-        fill_push(c, true, c->lna(c->k), c->lna(k1), true, c->lna(c->k + 0.5 * dir),
-                  last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a);
-        rc = push(c, a, grid_for_step(c, nxt));
+        PushArgs a;
+        fill_pass(c, a);
+        a.nsub = 0;
+        size_t gi = 0;
+        if (j == 0) {
+            fill_substep(c, false, 0, 0, true, c->lna(c->k), c->lna(c->k + 0.5 * dir), a.sub[0]);
+            a.G[0] = grids_cur[gi++];
+            a.nsub = 1;
+        }
+        for (int i = 0; i < pass_len(j); ++i) {
+            const int k0 = c->k, k1 = k0 + dir;
+            const bool last = (j == passes - 1) && (i == pass_len(j) - 1);
+            // drift over the step; merged kick (closing half of this step, opening half
+            // of the next) at x_{k+1} with the fields of step k+1, or only the closing half
+            fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir),
+                         last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
+            a.G[a.nsub] = grids_cur[gi++];
+            ++a.nsub;
+            c->k = k1;
+            c->disp += typical_displacement(c, c->lna(k0), c->lna(k1));
+        }
+        for (int b : bufs_cur) {
+            rc = acquire_grid(c, b);
+            if (rc) return rc;
+        }
+        rc = push(c, a);
         if (rc) return rc;
-        if (!last) {
-            rc = maybe_sort(c, k1, c->lna(c->k), c->lna(k1));
+        for (int b : bufs_cur) {
+            rc = release_grid(c, b);
             if (rc) return rc;
         }
-        c->cur = nxt;
-        c->k = k1;
+        if (j + 1 < passes) {
+            rc = maybe_sort(c, c->k - k_start);
+            if (rc) return rc;
+        }
+        std::swap(bufs_cur, bufs_next);
+        std::swap(grids_cur, grids_next);
     }
-    return FDF_OK;
+    return join_fields(c);
 }
 
 int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_t out_on_device)
@@ -806,10 +993,14 @@ int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device)
     if (!out || !std::isfinite(lna)) return fail(FDF_EINVAL, "bad arguments");
     const int N = c->p.n_grid;
     const size_t N3 = (size_t)N * N * N;
-    const int buf = c->cur ^ 1;
-    int rc = build_fields(c, lna, c->G[buf]);
-    if (rc) return rc;
+    FDF_CUDA(cudaStreamSynchronize(c->sf), "fdf_build_fields");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_build_fields");
+    int buf = 0;
+    for (int i = 0; i < c->nbuf; ++i)
+        if (c->gk[i] != c->k) buf = i;
     c->gk[buf] = -1;
+    int rc = build_fields(c, lna, c->G[buf], c->stream);
+    if (rc) return rc;
     double* dst = out;
     if (!out_on_device) FDF_CUDA(cudaMalloc(&dst, 8 * N3 * 8), "allocating the field copy");
     rc = timed(c, FDF_K_OTHER, "field export",
@@ -828,9 +1019,10 @@ int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device)
 int fdf_set_fields(fdf_ctx* c, const double* fields, int32_t on_device)
 {
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    FDF_CUDA(cudaStreamSynchronize(c->sf), "fdf_set_fields");
     if (!fields) {
         c->frozen = false;
-        c->gk[0] = c->gk[1] = -1;
+        for (int i = 0; i < kMaxBuf; ++i) c->gk[i] = -1;
         return FDF_OK;
     }
     const int N = c->p.n_grid;
@@ -870,6 +1062,7 @@ int fdf_timing(fdf_ctx* c, int32_t enable)
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
     if (enable) {
         FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_timing");
+        FDF_CUDA(cudaStreamSynchronize(c->sf), "fdf_timing");
         c->marks.clear();
         c->pool_used = 0;
     }
@@ -882,6 +1075,7 @@ int fdf_kernel_time(fdf_ctx* c, int32_t which, double* ms, int64_t* launches)
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
     if (which < 0 || which >= FDF_K_COUNT) return fail(FDF_EINVAL, "unknown kernel class");
     FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_kernel_time");
+    FDF_CUDA(cudaStreamSynchronize(c->sf), "fdf_kernel_time");
     double total = 0;
     int64_t cnt = 0;
     for (auto& m : c->marks) {
@@ -920,6 +1114,15 @@ void fdf_destroy(fdf_ctx* c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    if (c->sf) {
+        cudaStreamSynchronize(c->sf);
+        cudaStreamDestroy(c->sf);
+    }
+    for (int i = 0; i < kMaxBuf; ++i) {
+        if (c->built[i]) cudaEventDestroy(c->built[i]);
+        if (c->released[i]) cudaEventDestroy(c->released[i]);
+    }
+    if (c->joined) cudaEventDestroy(c->joined);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->Gfrozen) cudaFree(c->Gfrozen);
     if (c->own_block && c->block) cudaFree(c->block);

@@ -24,9 +24,9 @@ struct SpeciesCoef {
     // drift over [ln a_k, ln a_k+1]: D(q) = sum_j Wd_j / sqrt(q^2 + mud_j)
     double Wd[kMaxGL];
     double mud[kMaxGL];
-    FF Wd_sum;                  // sum_j Wd_j
+    FF Wd_sum;                  // sum_j Wd_j, times 2^32/L (position quanta)
     FF mud_c;                   // mud at the centre node jc
-    float Wd_f[kMaxGL];
+    float Wd_f[kMaxGL];         // Wd_j times 2^32/L
     float dmud_f[kMaxGL];       // mud_j - mud_c
     // kick over [lo, hi]: K_psi = sum Wk sqrt(q0^2 + muk), K_phi = sum Wk / sqrt(..)
     double Wk[kMaxGL];
@@ -37,17 +37,29 @@ struct SpeciesCoef {
     float dtau_k_f;
 };
 
+// One sub-step of a particle pass: an optional drift over [ln a_k, ln a_k+1] and an
+// optional kick with the grid of the sub-step's end point.
+struct SubStep {
+    int do_drift;
+    int do_kick;
+    SpeciesCoef sp[kMaxSpecies];
+};
+
+constexpr int kMaxSub = 5;      // sub-steps per particle pass (an open kick and 4 steps)
+
 struct PushArgs {
     int64_t n;                  // particles in all species
     int64_t n_part;             // particles per species
     int64_t sp_begin[kMaxSpecies];  // first particle of species 1, 2, 3 (n beyond the last species)
-    int n_gl;
-    int do_drift;
-    int do_kick;
+    int n_gl;                   // Gauss-Legendre nodes of the drift integral
+    int n_kick;                 // nodes of the kick integrals
+    int uniform_species;        // every species has the same mass: use sp[0]
     int N;                      // grid side
+    int nsub;                   // sub-steps in this pass, 1..kMaxSub
     double L, invL, invh;
     FF fx_scale;                // 2^32 / L
-    SpeciesCoef sp[kMaxSpecies];
+    SubStep sub[kMaxSub];
+    const void* G[kMaxSub];     // the grid each sub-step's kick reads
 };
 
 // Field-build arguments for one scale factor.
@@ -120,15 +132,17 @@ struct ParticleState {
 
 cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t n_part,
                            const double* m_ev, double a0, double tau0, int N, double L, const void* G);
-cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a, const void* G);
+cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a);
 
 // Counting sort of the particle state a into b by (species, Morton index of
 // the particle's tile of 2^tile_shift cells per axis).  key: n words; hist:
-// n_species * tiles words; bsum: 1024 words.
+// n_species * tiles words; bsum: scan_scratch_words(bins) words; recs: n records
+// of sort_record_bytes(precision).
 int sort_tile_shift(int N);
+size_t sort_record_bytes(int precision);
 cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, const ParticleState& b, int64_t n,
                         int64_t n_part, int n_species, int N, double L, uint32_t* key, uint32_t* hist,
-                        uint32_t* bsum);
+                        uint32_t* bsum, void* recs);
 // Particles [begin, begin + count) of an array of n; outputs in id order
 // (out index = id - begin).
 cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,

@@ -65,7 +65,6 @@ template <> __device__ __forceinline__ double2 tw32<double2>(int j) { return kTw
 // Compile-time loops: f(Idx<I>) for I = 0..N-1, so that every register-array index
 // below is a constant expression.
 template <int I> struct Idx {
-    static constexpr int value = I;
     __host__ __device__ constexpr operator int() const { return I; }
 };
 template <typename F, int... Is>

@@ -192,6 +192,10 @@ __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t 
 }
 
 // ---- the fused leapfrog pass, split form -------------------------------------
+// A pass advances every particle through a.nsub sub-steps (temporal blocking): the
+// particle's state is read once, carried through the sub-steps in registers and
+// written once; each sub-step's kick reads its own grid.  The arithmetic of a
+// sub-step does not depend on how the steps are grouped into passes.
 __device__ __forceinline__ int species_of(const PushArgs& a, int64_t i)
 {
     return (int)(i >= a.sp_begin[0]) + (int)(i >= a.sp_begin[1]) + (int)(i >= a.sp_begin[2]);
@@ -218,74 +222,101 @@ __device__ __forceinline__ SplitState load_split(const uint32_t* __restrict__ X,
     return s;
 }
 
-template <typename Gt>
+// D (q0 + dq) in position quanta, as a normalised float-float: D q0 with an exact
+// product, D dq (|dq| << |q0|) folded into the low part.
+__device__ __forceinline__ FF scale_q(FF D, float q0, float dq)
+{
+    const float p = __fmul_rn(D.hi, q0);
+    float e = __fmaf_rn(D.hi, q0, -p);
+    e = __fmaf_rn(D.lo, q0, e);
+    e = __fmaf_rn(D.hi, dq, e);
+    FF r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+// NGL drift nodes and NK kick nodes are compile-time, so the quadrature loops
+// unroll into constant-bank operands; UNI: every species has the same mass.
+template <typename Gt, int NGL, int NK, bool UNI>
 __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constant__ PushArgs a,
                                                             uint32_t* __restrict__ X, const float* __restrict__ q0f,
-                                                            float* __restrict__ dqf, const Gt* __restrict__ G)
+                                                            float* __restrict__ dqf)
 {
     const int64_t n = a.n;
     const uint32_t N = (uint32_t)a.N;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    SplitState nx{};
-    if (i < n) nx = load_split(X, q0f, dqf, n, i);
-    for (; i < n; i += stride) {
-        const SplitState cur = nx;
-        if (i + stride < n) nx = load_split(X, q0f, dqf, n, i + stride);  // next particle's state in flight
-        const SpeciesCoef& c = a.sp[species_of(a, i)];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const SplitState cur = load_split(X, q0f, dqf, n, i);
+        const int s = UNI ? 0 : species_of(a, i);
         uint32_t X0 = cur.X0, X1 = cur.X1, X2 = cur.X2;
         const float qa = cur.qa, qb = cur.qb, qc = cur.qc;
         float da = cur.da, db = cur.db, dc = cur.dc;
-        if (a.do_drift) {
-            // q = q_0 + dq exactly, as float-float per component
-            FF t0, t1, t2;
-            two_sum(qa, da, t0.hi, t0.lo);
-            two_sum(qb, db, t1.hi, t1.lo);
-            two_sum(qc, dc, t2.hi, t2.lo);
-            // |q|^2 in float-float
-            const FF S = ff_add(ff_add(ff_mul(t0, t0), ff_mul(t1, t1)), ff_mul(t2, t2));
-            // D = sum_j Wd_j (S + mu_j)^-1/2 = r_c [sum_j Wd_j + sum_j Wd_j g(delta_j)],
-            // r_c = (S + mu_c)^-1/2, delta_j = (mu_j - mu_c) r_c^2, g(d) = (1+d)^-1/2 - 1
-            // = -d y / (1 + (1+d) y) with y = (1+d)^-1/2.  The corrections are small
-            // next to sum_j Wd_j, so hardware rsqrt and reciprocal (2^-22) suffice.
-            const FF r = ff_rsqrt(ff_add(S, c.mud_c));
-            const float r2 = r.hi * r.hi;
-            float corr = 0.f;
-            for (int j = 0; j < a.n_gl; ++j) {
-                const float d = c.dmud_f[j] * r2;
-                const float t = 1.f + d;
-                const float y = rsqrtf(t);
-                corr = fmaf(c.Wd_f[j], -d * y * __frcp_rn(fmaf(t, y, 1.f)), corr);
+        // |q0|^2 in float-float (exact squares), and |q0|^2 in FP32 for the kick
+        const float pa = __fmul_rn(qa, qa), pb = __fmul_rn(qb, qb), pc = __fmul_rn(qc, qc);
+        const float ea = __fmaf_rn(qa, qa, -pa), eb = __fmaf_rn(qb, qb, -pb), ec = __fmaf_rn(qc, qc, -pc);
+        float s1, e1, s2, e2;
+        two_sum(pa, pb, s1, e1);
+        two_sum(s1, pc, s2, e2);
+        const float elo = (e1 + e2) + (ea + eb + ec);
+        const float q02 = s2;
+        bool moved = false, kicked = false;
+        for (int u = 0; u < a.nsub; ++u) {
+            const SubStep& st = a.sub[u];
+            const SpeciesCoef& c = st.sp[s];
+            if (st.do_drift) {
+                // |q|^2 = |q0|^2 + (2 q0 + dq).dq; the second term is at most a few per
+                // cent of the first and carries FP32 rounding only.
+                const float small = fmaf(2.f * qa + da, da, fmaf(2.f * qb + db, db, (2.f * qc + dc) * dc));
+                FF S;
+                fast_two_sum(s2, elo + small, S.hi, S.lo);
+                // D = sum_j Wd_j (S + mu_j)^-1/2 = r_c [sum_j Wd_j + sum_j Wd_j g(delta_j)],
+                // r_c = (S + mu_c)^-1/2, delta_j = (mu_j - mu_c) r_c^2, g(d) = (1+d)^-1/2 - 1
+                // = -d y / (1 + (1+d) y), y = (1+d)^-1/2.  The corrections are small next to
+                // sum_j Wd_j, so hardware rsqrt and reciprocal (2^-22) suffice.  The weights
+                // carry the factor 2^32/L, so D is in position quanta per eV.
+                const FF r = ff_rsqrt(ff_add(S, c.mud_c));
+                const float r2 = r.hi * r.hi;
+                float corr = 0.f;
+#pragma unroll
+                for (int j = 0; j < NGL; ++j) {
+                    const float d = c.dmud_f[j] * r2;
+                    const float t = 1.f + d;
+                    const float y = rsqrtf(t);
+                    corr = fmaf(c.Wd_f[j], -d * y * __frcp_rn(fmaf(t, y, 1.f)), corr);
+                }
+                FF A;
+                fast_two_sum(c.Wd_sum.hi, __fadd_rn(c.Wd_sum.lo, corr), A.hi, A.lo);
+                const FF D = ff_mul(r, A);
+                X0 += round_mod32(scale_q(D, qa, da));
+                X1 += round_mod32(scale_q(D, qb, db));
+                X2 += round_mod32(scale_q(D, qc, dc));
+                moved = true;
             }
-            FF A;
-            fast_two_sum(c.Wd_sum.hi, __fadd_rn(c.Wd_sum.lo, corr), A.hi, A.lo);
-            const FF D = ff_mul(ff_mul(r, A), a.fx_scale);  // position quanta per eV of momentum
-            X0 += round_mod32(ff_mul(D, t0));
-            X1 += round_mod32(ff_mul(D, t1));
-            X2 += round_mod32(ff_mul(D, t2));
+            if (st.do_kick) {
+                float g[8];
+                gather_fixed<Gt>(reinterpret_cast<const Gt*>(a.G[u]), N, X0, X1, X2, g);
+                float Kpsi = 0.f, Kphi = 0.f;
+#pragma unroll
+                for (int j = 0; j < NK; ++j) {
+                    const float e2k = q02 + c.muk_f[j];
+                    const float ie = rsqrtf(e2k);
+                    Kpsi = fmaf(c.Wk_f[j], e2k * ie, Kpsi);
+                    Kphi = fmaf(c.Wk_f[j], ie, Kphi);
+                }
+                const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
+                const float b = qdphi * Kphi + g[6] * c.dtau_k_f;
+                const float a2 = q02 * Kphi;
+                da += -g[0] * Kpsi - g[3] * a2 + qa * b;
+                db += -g[1] * Kpsi - g[4] * a2 + qb * b;
+                dc += -g[2] * Kpsi - g[5] * a2 + qc * b;
+                kicked = true;
+            }
         }
-        if (a.do_kick) {
-            float g[8];
-            gather_fixed<Gt>(G, N, X0, X1, X2, g);
-            const float q02 = qa * qa + qb * qb + qc * qc;
-            float Kpsi = 0.f, Kphi = 0.f;
-            for (int j = 0; j < a.n_gl; ++j) {
-                const float e2 = q02 + c.muk_f[j];
-                const float ie = rsqrtf(e2);
-                Kpsi = fmaf(c.Wk_f[j], e2 * ie, Kpsi);
-                Kphi = fmaf(c.Wk_f[j], ie, Kphi);
-            }
-            const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
-            const float b = qdphi * Kphi + g[6] * c.dtau_k_f;
-            const float a2 = q02 * Kphi;
-            da += -g[0] * Kpsi - g[3] * a2 + qa * b;
-            db += -g[1] * Kpsi - g[4] * a2 + qb * b;
-            dc += -g[2] * Kpsi - g[5] * a2 + qc * b;
+        if (kicked) {
             __stcs(dqf + i, da);
             __stcs(dqf + n + i, db);
             __stcs(dqf + 2 * n + i, dc);
         }
-        if (a.do_drift) {
+        if (moved) {
             __stcs(X + i, X0);
             __stcs(X + n + i, X1);
             __stcs(X + 2 * n + i, X2);
@@ -293,40 +324,69 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
     }
 }
 
+template <typename Gt, int NGL, bool UNI>
+void push_split_ngl(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
+{
+    k_push_split<Gt, NGL, (NGL + 1) / 2, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf);
+}
+
+template <typename Gt, bool UNI>
+void push_split(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
+{
+    switch (a.n_gl) {
+        case 3: push_split_ngl<Gt, 3, UNI>(s, b, a, st); break;
+        case 4: push_split_ngl<Gt, 4, UNI>(s, b, a, st); break;
+        case 5: push_split_ngl<Gt, 5, UNI>(s, b, a, st); break;
+        case 6: push_split_ngl<Gt, 6, UNI>(s, b, a, st); break;
+        default: push_split_ngl<Gt, 8, UNI>(s, b, a, st); break;
+    }
+}
+
 // ---- the fused leapfrog pass, plain FP64 form --------------------------------
-__global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ PushArgs a, double* __restrict__ xd, double* __restrict__ qd,
-                                                       const double* __restrict__ q0d, const double* __restrict__ G)
+__global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ PushArgs a, double* __restrict__ xd,
+                                                       double* __restrict__ qd, const double* __restrict__ q0d)
 {
     const int64_t n = a.n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const SpeciesCoef& c = a.sp[(int)(i >= a.sp_begin[0]) + (int)(i >= a.sp_begin[1]) + (int)(i >= a.sp_begin[2])];
+        const int s = (int)(i >= a.sp_begin[0]) + (int)(i >= a.sp_begin[1]) + (int)(i >= a.sp_begin[2]);
         double x[3] = {xd[i], xd[n + i], xd[2 * n + i]};
         double q[3] = {qd[i], qd[n + i], qd[2 * n + i]};
         const double q0[3] = {q0d[i], q0d[n + i], q0d[2 * n + i]};
-        if (a.do_drift) {
-            const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
-            double D = 0.0;
-            for (int j = 0; j < a.n_gl; ++j) D += c.Wd[j] / sqrt(qq + c.mud[j]);
+        const double q02 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+        bool moved = false, kicked = false;
+        for (int u = 0; u < a.nsub; ++u) {
+            const SubStep& st = a.sub[u];
+            const SpeciesCoef& c = st.sp[s];
+            if (st.do_drift) {
+                const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+                double D = 0.0;
+                for (int j = 0; j < a.n_gl; ++j) D += c.Wd[j] / sqrt(qq + c.mud[j]);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) x[d] = wrap_f64(x[d] + D * q[d], a.L, a.invL);
+                for (int d = 0; d < 3; ++d) x[d] = wrap_f64(x[d] + D * q[d], a.L, a.invL);
+                moved = true;
+            }
+            if (st.do_kick) {
+                double g[8];
+                gather_f64(reinterpret_cast<const double*>(a.G[u]), a.N, a.invh, x, g);
+                double Kpsi = 0.0, Kphi = 0.0;
+                for (int j = 0; j < a.n_kick; ++j) {
+                    const double e = sqrt(q02 + c.muk[j]);
+                    Kpsi += c.Wk[j] * e;
+                    Kphi += c.Wk[j] / e;
+                }
+                const double qdphi = q0[0] * g[3] + q0[1] * g[4] + q0[2] * g[5];
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    q[d] += -g[d] * Kpsi - g[3 + d] * (q02 * Kphi) + q0[d] * (qdphi * Kphi) + q0[d] * (g[6] * c.dtau_k);
+                kicked = true;
+            }
+        }
+        if (moved) {
             xd[i] = x[0];
             xd[n + i] = x[1];
             xd[2 * n + i] = x[2];
         }
-        if (a.do_kick) {
-            double g[8];
-            gather_f64(G, a.N, a.invh, x, g);
-            const double q02 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
-            double Kpsi = 0.0, Kphi = 0.0;
-            for (int j = 0; j < a.n_gl; ++j) {
-                const double e = sqrt(q02 + c.muk[j]);
-                Kpsi += c.Wk[j] * e;
-                Kphi += c.Wk[j] / e;
-            }
-            const double qdphi = q0[0] * g[3] + q0[1] * g[4] + q0[2] * g[5];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                q[d] += -g[d] * Kpsi - g[3 + d] * (q02 * Kphi) + q0[d] * (qdphi * Kphi) + q0[d] * (g[6] * c.dtau_k);
+        if (kicked) {
             qd[i] = q[0];
             qd[n + i] = q[1];
             qd[2 * n + i] = q[2];
@@ -479,16 +539,18 @@ cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& s
     return cudaGetLastError();
 }
 
-cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a, const void* G)
+cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a)
 {
     if (a.n <= 0) return cudaSuccess;
     const unsigned b = grid_for(a.n);
-    if (precision == FDF_PREC_F64)
-        k_push_f64<<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d, (const double*)G);
-    else if (precision == FDF_PREC_F32)
-        k_push_split<float><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf, (const float*)G);
-    else
-        k_push_split<__nv_bfloat16><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf, (const __nv_bfloat16*)G);
+    if (precision == FDF_PREC_F64) k_push_f64<<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d);
+    else if (precision == FDF_PREC_F32) {
+        if (a.uniform_species) push_split<float, true>(s, b, a, st);
+        else push_split<float, false>(s, b, a, st);
+    } else {
+        if (a.uniform_species) push_split<__nv_bfloat16, true>(s, b, a, st);
+        else push_split<__nv_bfloat16, false>(s, b, a, st);
+    }
     return cudaGetLastError();
 }
 

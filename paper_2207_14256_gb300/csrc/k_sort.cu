@@ -33,7 +33,12 @@ __global__ void __launch_bounds__(kThreads) k_sort_keys(ParticleState st, int64_
                                                         int tile_shift, uint32_t tiles_per_species, double invh,
                                                         uint32_t* __restrict__ key, uint32_t* __restrict__ hist)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool live = i < n;
+        const unsigned active = __ballot_sync(0xffffffffu, live);
+        if (!live) continue;
         uint32_t c[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -49,23 +54,24 @@ __global__ void __launch_bounds__(kThreads) k_sort_keys(ParticleState st, int64_
         const uint32_t s = (uint32_t)(i / n_part);
         const uint32_t k = s * tiles_per_species + (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
         key[i] = k;
-        atomicAdd(hist + k, 1u);
+        // lanes with the same key (neighbours in a sorted state) add once through a leader
+        const unsigned peers = __match_any_sync(active, k);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + k, (uint32_t)__popc(peers));
     }
 }
 
-// Exclusive scan, phase 1: each block scans 4 * kThreads elements.
-__global__ void __launch_bounds__(kThreads) k_scan_local(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                                         uint32_t* __restrict__ bsum, int n)
+// Exclusive scan, phase 1: each block scans 4 * kThreads elements and writes its total.
+__global__ void __launch_bounds__(kThreads) k_scan_local(uint32_t* __restrict__ v, uint32_t* __restrict__ bsum,
+                                                         int64_t n)
 {
     __shared__ uint32_t warp_tot[kThreads / 32];
-    const int base = blockIdx.x * 4 * kThreads + 4 * threadIdx.x;
-    uint32_t v[4], t = 0;
+    const int64_t base = (int64_t)blockIdx.x * 4 * kThreads + 4 * threadIdx.x;
+    uint32_t x4[4], t = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        v[j] = base + j < n ? in[base + j] : 0u;
-        t += v[j];
+        x4[j] = base + j < n ? v[base + j] : 0u;
+        t += x4[j];
     }
-    // inclusive scan of the thread totals within the block
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t x = t;
 #pragma unroll
@@ -85,47 +91,57 @@ __global__ void __launch_bounds__(kThreads) k_scan_local(const uint32_t* __restr
         if (lane < kThreads / 32) warp_tot[lane] = w;
     }
     __syncthreads();
-    uint32_t run = x - t + (wid ? warp_tot[wid - 1] : 0u);  // exclusive prefix of this thread
+    uint32_t run = x - t + (wid ? warp_tot[wid - 1] : 0u);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (base + j < n) out[base + j] = run;
-        run += v[j];
+        if (base + j < n) v[base + j] = run;
+        run += x4[j];
     }
     if (threadIdx.x == kThreads - 1) bsum[blockIdx.x] = run;
 }
 
-// Phase 2: one block scans the block totals (at most 4 * kThreads of them).
-__global__ void __launch_bounds__(kThreads) k_scan_totals(uint32_t* __restrict__ bsum, int nb)
+// Phase 3: add the scanned block totals.
+__global__ void __launch_bounds__(kThreads) k_scan_add(uint32_t* __restrict__ v, const uint32_t* __restrict__ bsum,
+                                                       int64_t n)
 {
-    __shared__ uint32_t s[4 * kThreads];
-    for (int i = threadIdx.x; i < 4 * kThreads; i += kThreads) s[i] = i < nb ? bsum[i] : 0u;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int i = 0; i < nb; ++i) {
-            const uint32_t v = s[i];
-            s[i] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += kThreads) bsum[i] = s[i];
-}
-
-// Phase 3: add the block offsets.
-__global__ void __launch_bounds__(kThreads) k_scan_add(uint32_t* __restrict__ out, const uint32_t* __restrict__ bsum,
-                                                       int n)
-{
-    const int base = blockIdx.x * 4 * kThreads;
+    const int64_t base = (int64_t)blockIdx.x * 4 * kThreads;
     const uint32_t add = bsum[blockIdx.x];
     for (int j = threadIdx.x; j < 4 * kThreads; j += kThreads)
-        if (base + j < n) out[base + j] += add;
+        if (base + j < n) v[base + j] += add;
 }
 
+// Exclusive scan of v[0..n) in place; the totals of each level go to tmp.
+cudaError_t scan_exclusive(cudaStream_t s, uint32_t* v, int64_t n, uint32_t* tmp)
+{
+    const int64_t per = 4 * kThreads;
+    const int64_t nb = (n + per - 1) / per;
+    k_scan_local<<<(unsigned)nb, kThreads, 0, s>>>(v, tmp, n);
+    if (nb > 1) {
+        cudaError_t e = scan_exclusive(s, tmp, nb, tmp + nb);
+        if (e != cudaSuccess) return e;
+        k_scan_add<<<(unsigned)nb, kThreads, 0, s>>>(v, tmp, n);
+    }
+    return cudaGetLastError();
+}
+
+// Scatter: every particle's state, packed into one record, goes to offset[key]++.
+// Records keep the scattered writes whole (48 bytes instead of nine 4-byte fields).
+struct alignas(64) SplitRec {   // 64 bytes: a scattered record covers two whole sectors
+    uint32_t X[3];
+    float q0[3];
+    float dq[3];
+    uint32_t id;
+    double pmag;
+    uint32_t pad[4];
+};
+struct alignas(32) PlainRec {   // 96 bytes: three whole sectors
+    double x[3], q[3], q0[3], pmag;
+    uint32_t id, pad[7];
+};
+
 template <int Prec>
-__global__ void __launch_bounds__(kThreads) k_sort_scatter(ParticleState a, ParticleState b, int64_t n,
-                                                           const uint32_t* __restrict__ key,
-                                                           uint32_t* __restrict__ offset)
+__global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t n, const uint32_t* __restrict__ key,
+                                                        uint32_t* __restrict__ offset, void* __restrict__ recs)
 {
     // Grid-stride loop with a warp-uniform trip count, so that every lane can take
     // part in the warp-aggregated atomic: lanes sharing a key (the common case once
@@ -145,20 +161,55 @@ __global__ void __launch_bounds__(kThreads) k_sort_scatter(ParticleState a, Part
         if (lane == leader) base = atomicAdd(offset + k, (uint32_t)__popc(peers));
         base = __shfl_sync(peers, base, leader);
         const int64_t j = (int64_t)base + rank;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if constexpr (Prec == FDF_PREC_F64) {
-                b.xd[d * n + j] = a.xd[d * n + i];
-                b.qd[d * n + j] = a.qd[d * n + i];
-                b.q0d[d * n + j] = a.q0d[d * n + i];
-            } else {
-                b.X[d * n + j] = a.X[d * n + i];
-                b.q0f[d * n + j] = a.q0f[d * n + i];
-                b.dqf[d * n + j] = a.dqf[d * n + i];
+        if constexpr (Prec == FDF_PREC_F64) {
+            PlainRec r;
+            for (int d = 0; d < 3; ++d) {
+                r.x[d] = a.xd[d * n + i];
+                r.q[d] = a.qd[d * n + i];
+                r.q0[d] = a.q0d[d * n + i];
             }
+            r.pmag = a.pmag[i];
+            r.id = a.id[i];
+            for (int q = 0; q < 7; ++q) r.pad[q] = 0;
+            reinterpret_cast<PlainRec*>(recs)[j] = r;
+        } else {
+            SplitRec r;
+            for (int d = 0; d < 3; ++d) {
+                r.X[d] = a.X[d * n + i];
+                r.q0[d] = a.q0f[d * n + i];
+                r.dq[d] = a.dqf[d * n + i];
+            }
+            r.id = a.id[i];
+            r.pmag = a.pmag[i];
+            r.pad[0] = r.pad[1] = r.pad[2] = r.pad[3] = 0;
+            reinterpret_cast<SplitRec*>(recs)[j] = r;
         }
-        b.pmag[j] = a.pmag[i];
-        b.id[j] = a.id[i];
+    }
+}
+
+template <int Prec>
+__global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64_t n, const void* __restrict__ recs)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (Prec == FDF_PREC_F64) {
+            const PlainRec r = reinterpret_cast<const PlainRec*>(recs)[j];
+            for (int d = 0; d < 3; ++d) {
+                b.xd[d * n + j] = r.x[d];
+                b.qd[d * n + j] = r.q[d];
+                b.q0d[d * n + j] = r.q0[d];
+            }
+            b.pmag[j] = r.pmag;
+            b.id[j] = r.id;
+        } else {
+            const SplitRec r = reinterpret_cast<const SplitRec*>(recs)[j];
+            for (int d = 0; d < 3; ++d) {
+                b.X[d * n + j] = r.X[d];
+                b.q0f[d * n + j] = r.q0[d];
+                b.dqf[d * n + j] = r.dq[d];
+            }
+            b.id[j] = r.id;
+            b.pmag[j] = r.pmag;
+        }
     }
 }
 
@@ -171,17 +222,21 @@ unsigned grid_for(int64_t n)
 
 }  // namespace
 
-int sort_tile_shift(int N) { return N > 64 ? ilog2_host(N / 64) : 0; }
+// Sort tiles of single cells: consecutive particles then share grid cells, which
+// the gather's loads serve once per warp.
+int sort_tile_shift(int N) { return 0; }
+
+size_t sort_record_bytes(int precision) { return precision == FDF_PREC_F64 ? sizeof(PlainRec) : sizeof(SplitRec); }
 
 cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, const ParticleState& b, int64_t n,
                         int64_t n_part, int n_species, int N, double L, uint32_t* key, uint32_t* hist,
-                        uint32_t* bsum)
+                        uint32_t* bsum, void* recs)
 {
     if (n <= 0) return cudaSuccess;
     const int shift = sort_tile_shift(N);
     const uint32_t tpa = (uint32_t)(N >> shift);
     const uint32_t tiles = tpa * tpa * tpa;
-    const int bins = (int)(tiles * (uint32_t)n_species);
+    const int64_t bins = (int64_t)tiles * n_species;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)bins * 4, s);
     if (e != cudaSuccess) return e;
     const unsigned g = grid_for(n);
@@ -189,12 +244,15 @@ cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, c
         k_sort_keys<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, key, hist);
     else
         k_sort_keys<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, key, hist);
-    const int nb = (bins + 4 * kThreads - 1) / (4 * kThreads);
-    k_scan_local<<<nb, kThreads, 0, s>>>(hist, hist, bsum, bins);
-    k_scan_totals<<<1, kThreads, 0, s>>>(bsum, nb);
-    k_scan_add<<<nb, kThreads, 0, s>>>(hist, bsum, bins);
-    if (precision == FDF_PREC_F64) k_sort_scatter<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, b, n, key, hist);
-    else k_sort_scatter<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, b, n, key, hist);
+    e = scan_exclusive(s, hist, bins, bsum);
+    if (e != cudaSuccess) return e;
+    if (precision == FDF_PREC_F64) {
+        k_sort_pack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, key, hist, recs);
+        k_sort_unpack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(b, n, recs);
+    } else {
+        k_sort_pack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, key, hist, recs);
+        k_sort_unpack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(b, n, recs);
+    }
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ class fdf_params(C.Structure):
         ("flags", C.c_int32),
         ("n_gl", C.c_int32),
         ("sort_every", C.c_int32),
-        ("reserved", C.c_int32),
+        ("steps_per_pass", C.c_int32),
     ]
 
 
@@ -157,6 +157,7 @@ def make_params(d):
     p.flags = int(d.get("flags", 0))
     p.n_gl = int(d.get("n_gl", 0))
     p.sort_every = int(d.get("sort_every", 0))
+    p.steps_per_pass = int(d.get("steps_per_pass", 0))
     return p
 
 
