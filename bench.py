@@ -32,8 +32,26 @@ from paper_2207_14256_gb300 import inputs as I  # noqa: E402
 METRIC = "neutrino particle-steps/s at 256^3 vs plain FP64 GPU form; served p99 latency"
 UNIT = "particle-steps/s"
 WORKLOAD = "c3_3x256"
-PUSH_BYTES_PER_PARTICLE = {1: 60, 2: 60, 0: 120}   # algorithmic bytes per particle-step (see DESIGN)
-GRID_BYTES_PER_CELL = {1: 28, 2: 14, 0: 56}        # the 7 gradient fields read once per step
+# Algorithmic bytes of the method per unit of work, by precision form (0 FP64, 1 FP32,
+# 2 BF16 grids): a particle-step reads and writes x and q at FP64 and reads q0 at FP32
+# (108 B; 120 B with q0 at FP64), and a kick reads the seven gradient fields of every
+# cell once (28 B per cell at FP32, 14 B at BF16, 56 B at FP64).
+PARTICLE_STEP_BYTES = {1: 108, 2: 108, 0: 120}
+GRID_READ_BYTES_PER_CELL = {1: 28, 2: 14, 0: 56}
+
+# DRAM bytes per particle pass of the FP32 split form, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean over the 50 passes of a one-species 256^3 run, profiles/
+# k_push_split_1x256.md), per particle of the launch.  Valid only for the kernel sources
+# it was measured on: their hash is checked and the figure dropped if they changed.
+PUSH_TRAFFIC = {"bytes_per_particle": 4.447e9 / 256 ** 3, "sources_sha256": "8decf3be1c918365:bb45ba9f916a8aff:e8b1efa1a66072ac"}
+PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
+
+
+def push_sources_hash():
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_2207_14256_gb300", "csrc")
+    return ":".join(hashlib.sha256(open(os.path.join(d, f), "rb").read()).hexdigest()[:16] for f in PUSH_SOURCES)
 
 
 def describe(p):
@@ -104,6 +122,31 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------------------------
+def rank_params(workload, rank, n_species=0):
+    """The workload of one replica: every rank runs the same shapes with its own seed."""
+    p = I.config(workload, seed=I.config(workload)["seed"] + 1000 * rank)
+    if n_species:
+        p["n_species"] = n_species
+        p["m_ev"] = (p["m_ev"] * 4)[:n_species]
+    return p
+
+
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of a list of floats over all ranks (the slowest rank's times)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def whole_job_value(world, units_per_rank, seconds):
+    """Units all ranks processed divided by the (max-over-ranks) time."""
+    return world * units_per_rank / seconds
+
+
 def run_once(fdf, ctx, p, out_dev):
     fdf.fdf_sample(ctx)
     fdf.fdf_step(ctx, p["n_steps"])
@@ -117,10 +160,7 @@ def bench_ours(args, rank, world, dist):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    p = I.config(args.workload, seed=I.config(args.workload)["seed"] + 1000 * rank)
-    if args.n_species:
-        p["n_species"] = args.n_species
-        p["m_ev"] = (p["m_ev"] * 4)[:args.n_species]
+    p = rank_params(args.workload, rank, args.n_species)
     tables = I.transfer_tables(p)
     stream = torch.cuda.Stream(device=dev)
     P = fdf.make_params(p)
@@ -209,6 +249,81 @@ def bench_ours(args, rank, world, dist):
 
 
 # ----------------------------------------------------------------------------------------------
+SERVED_BUDGET = 180 * 10 ** 9     # bytes of HBM the served stream may hold
+SERVED_ARRIVAL_SEED = 5
+
+
+def served_requests(n_req):
+    """The served stream's requests: request i draws its shapes from seed 1000 + i."""
+    reqs = []
+    for i in range(n_req):
+        r = np.random.default_rng(1000 + i)
+        N = int(r.choice([64, 128, 256]))
+        side = int(r.choice([64, 128, 256, 512]))
+        ns = int(r.integers(1, 4))
+        masses = [float(m) for m in r.uniform(0.02, 0.3, size=ns)]
+        steps = int(r.integers(100, 301))
+        reqs.append(I.config("c2_128", box=1000.0, n_part=side ** 3, n_grid=N, n_species=ns, m_ev=masses,
+                             n_steps=steps, seed=1000 + i, precision=I.PREC_F32))
+    return reqs
+
+
+def serve(fdf, reqs, tables, arrivals, max_active, slice_steps):
+    """Submit request i at arrivals[i] seconds (server clock), release each as it
+    finishes; returns per-request latencies and the span from first submit to last done."""
+    srv = fdf.Server(SERVED_BUDGET, max_active=max_active, slice_steps=slice_steps)
+    try:
+        t_start = srv.clock()
+        ids, infos = [], {}
+        i = 0
+        while len(infos) < len(reqs):
+            now = srv.clock() - t_start
+            while i < len(reqs) and arrivals[i] <= now:
+                ids.append(srv.submit(reqs[i], tables))
+                i += 1
+            wait_ms = 50 if i >= len(reqs) else max(0, min(50, int((arrivals[i] - now) * 1e3)))
+            rid = srv.wait(wait_ms)
+            while rid is not None:
+                info = srv.info(rid)
+                if info.status != fdf.FDF_REQ_DONE:
+                    raise RuntimeError("request %d failed: %s" % (rid, info.message.decode()))
+                infos[rid] = (info.t_submit, info.t_admit, info.t_done, info.particle_steps)
+                srv.release(rid)
+                rid = srv.wait(0)
+    finally:
+        srv.close()
+    lat = np.array([infos[r][2] - infos[r][0] for r in ids])
+    span = max(v[2] for v in infos.values()) - min(v[0] for v in infos.values())
+    work = sum(v[3] for v in infos.values())
+    return lat, span, work
+
+
+def bench_served(n_req=64, load=0.8, max_active=8, slice_steps=8):
+    """The served stream: first all requests at once (the batched capacity), then
+    Poisson arrivals at `load` times that capacity; p50/p99 latency of the second."""
+    from paper_2207_14256_gb300 import fdf
+
+    reqs = served_requests(n_req)
+    tables = I.transfer_tables(reqs[0])
+    lat0, span0, work = serve(fdf, reqs, tables, [0.0] * n_req, max_active, slice_steps)
+    capacity = work / span0
+    mean_service = work / n_req / capacity
+    rate = load / mean_service
+    gaps = np.random.default_rng(SERVED_ARRIVAL_SEED).exponential(1.0 / rate, size=n_req)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    lat, span, work = serve(fdf, reqs, tables, arrivals, max_active, slice_steps)
+    return {"requests": n_req, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "max_s": float(lat.max()), "value": work / span, "unit": UNIT,
+            "capacity": capacity, "offered_load": load, "arrival_rate_per_s": rate,
+            "saturated_p50_s": float(np.percentile(lat0, 50)), "saturated_p99_s": float(np.percentile(lat0, 99)),
+            "budget_bytes": SERVED_BUDGET, "max_active": max_active, "slice_steps": slice_steps,
+            "note": "requests: grid 64/128/256, 64^3..512^3 particles per species, 1-3 species, m U(0.02, 0.3) eV, "
+                    "100-300 steps, box 1000 Mpc, FP32 grids (request i from seed 1000 + i); Poisson arrivals "
+                    "(seed 5) at %.0f%% of the capacity measured with every request queued at once; latency = "
+                    "submit to results resident on the device" % (100 * load)}
+
+
+# ----------------------------------------------------------------------------------------------
 def cpu_baseline(workload, budget_s=25.0):
     """The oracle as it stands, on the host cores, on a bounded sample of the workload:
     one field build at full grid size plus one leapfrog step of a particle subset,
@@ -257,6 +372,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-served", action="store_true", help="skip the served stream")
+    ap.add_argument("--served-requests", type=int, default=64)
     ap.add_argument("--n-species", type=int, default=0,
                     help="override the species count (smaller device footprint for profiler captures)")
     args = ap.parse_args()
@@ -297,14 +414,9 @@ def main():
     r = bench_ours(args, rank, world, dist)
     ms = r["ms"]
     e2e_s = r["e2e_s"] / r["e2e_steps"]
-    if dist is not None:
-        import torch
-
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], "cuda")
     ms_per_step = ms / args.steps
-    value = world * r["units"] / (ms_per_step / 1e3)
+    value = whole_job_value(world, r["units"], ms_per_step / 1e3)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -317,19 +429,24 @@ def main():
     push_avg = push_ms / max(push_n, 1)
     n_total = r["p"]["n_species"] * r["p"]["n_part"]
     N3 = r["p"]["n_grid"] ** 3
-    # a particle pass reads and writes every particle's state once, however many
-    # leapfrog steps it covers; every kick sub-step (n_steps + 1 per run: the opening
-    # half kick and one merged kick per step) reads its grid once
+    # every run takes n_steps particle-steps per particle and n_steps + 1 grid reads
+    # (the opening half kick and one merged kick per step), spread over push_n launches
+    steps = args.steps * r["p"]["n_steps"]
     kicks = args.steps * (r["p"]["n_steps"] + 1)
-    alg_total = push_n * n_total * PUSH_BYTES_PER_PARTICLE[prec] + kicks * N3 * GRID_BYTES_PER_CELL[prec]
+    alg_total = steps * n_total * PARTICLE_STEP_BYTES[prec] + kicks * N3 * GRID_READ_BYTES_PER_CELL[prec]
     alg = alg_total / max(push_n, 1)
     achieved = alg / (push_avg / 1e3) / 1e9
     roof = {"kernel": "k_push_split (fused drift + wrap + gather + kick over a pass of leapfrog steps)",
             "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm if hbm else None, "traffic": None,
+            "frac": achieved / hbm if hbm else None,
+            "traffic": (PUSH_TRAFFIC["bytes_per_particle"] * n_total
+                        if prec == 1 and push_sources_hash() == PUSH_TRAFFIC["sources_sha256"] else None),
+            "traffic_note": "ncu DRAM bytes per pass, mean over a run, one species scaled to all by particles",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800",
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": push_avg,
-            "steps_per_launch": (kicks - args.steps) / max(push_n, 1)}
+            "steps_per_launch": steps / max(push_n, 1),
+            "per_unit": "%d B per particle-step + %d B per cell per kick" % (PARTICLE_STEP_BYTES[prec],
+                                                                           GRID_READ_BYTES_PER_CELL[prec])}
     per_run = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                for k, v in r["ktimes"].items()}
     out = line_base(args, world)
@@ -339,7 +456,7 @@ def main():
                    "l2": "inputs larger than L2 (%.1f GB particle state)" % (n_total * 48 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
-        "e2e": {"value": world * r["units"] / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["tab_bytes"],
+        "e2e": {"value": whole_job_value(world, r["units"], e2e_s), "unit": UNIT, "h2d_bytes_per_step": r["tab_bytes"],
                 "d2h_bytes_per_step": r["d2h"],
                 "note": "fdf_create (table upload) + sample + steps + fdf_get of every species into pinned host "
                         "memory + fdf_destroy, per step"},
@@ -351,6 +468,8 @@ def main():
         out["plain_f64"] = dict(r["plain"], value=world * r["plain"]["value"],
                                 note="the plain FP64 form (FP64 grids, FFT, state and arithmetic), same workload")
         out["speedup_vs_plain_f64"] = value / out["plain_f64"]["value"]
+    if not args.no_served and world == 1:
+        out["served"] = bench_served(args.served_requests)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(out))

@@ -235,6 +235,93 @@ FDF_API const char* fdf_last_error(void);
 /* Free everything the context allocated.  NULL is allowed. */
 FDF_API void fdf_destroy(fdf_ctx* c);
 
+/* ---- request server (continuous batching) --------------------------------
+ * Runs many independent runs ("requests": one fdf_params + fdf_tables each,
+ * of any grid size, particle count, species count, masses and step count) on
+ * one GPU at once.  The paper has no counterpart: each of its runs is one job
+ * (Sec. 2.1 notes that every neutrino is independent once the metric is known,
+ * so independent runs can share a GPU without interacting).
+ *
+ * The server allocates one device arena of hbm_budget bytes at creation and
+ * never calls cudaMalloc or cudaFree afterwards.  A worker thread:
+ *  - admits queued requests first-come-first-served while a slot is free
+ *    (at most max_active running) and the arena has a free range of the
+ *    request's fdf_footprint; a request that would never fit is refused at
+ *    submission (FDF_ENOMEM);
+ *  - runs every admitted request on its own CUDA streams (fdf_create on the
+ *    arena range, fdf_sample, then fdf_step in slices of slice_steps steps,
+ *    at most two slices in flight per request), so the kernels of different
+ *    requests overlap on the device;
+ *  - after the last step, deposits the weighted density of all species
+ *    (FDF_Q_W_EPS) on the device and marks the request done.
+ * A done request keeps its state (particles, deposit) resident until
+ * fdf_server_release returns its arena range; only then can a waiting request
+ * use that memory.  Each request's results do not depend on what else runs:
+ * positions, momenta and weights are bitwise those of the same request run
+ * alone; the deposit differs by the order of its FP64 atomic additions only.
+ *
+ * Times are seconds on the server's steady clock (fdf_server_clock).
+ * t_done is taken on the GPU timeline (a host function enqueued after the
+ * deposit), so a request's latency is t_done - t_submit. */
+typedef struct fdf_server fdf_server;
+
+#define FDF_REQ_QUEUED  0
+#define FDF_REQ_RUNNING 1
+#define FDF_REQ_DONE    2
+#define FDF_REQ_FAILED  3
+
+typedef struct fdf_request_info {
+    int64_t id;
+    int32_t status;            /* FDF_REQ_* */
+    int32_t error;             /* FDF_E* code when FAILED, else 0 */
+    double  t_submit, t_admit, t_done;
+    size_t  footprint;         /* device bytes held while admitted */
+    int64_t particle_steps;    /* n_species * n_part * n_steps */
+    char    message[160];      /* error detail when FAILED */
+} fdf_request_info;
+
+/* hbm_budget: bytes of the device arena (allocated on the current device);
+ * max_active: running requests at most (>= 1); slice_steps: steps per
+ * fdf_step call of the worker (>= 1).  FDF_ENOMEM if the arena cannot be
+ * allocated. */
+FDF_API int fdf_server_create(size_t hbm_budget, int32_t max_active, int32_t slice_steps, fdf_server** out);
+
+/* Queue a run.  p and t are copied (host memory; the caller may free them on
+ * return).  *id receives the request's id.  FDF_EINVAL for invalid
+ * parameters; FDF_ENOMEM if fdf_footprint exceeds the whole budget. */
+FDF_API int fdf_server_submit(fdf_server* s, const fdf_params* p, const fdf_tables* t, int64_t* id);
+
+/* Wait up to timeout_ms (< 0: forever) for the next request to finish (done or
+ * failed) and return its id; each finished request is reported once.
+ * FDF_ETIMEOUT if none finished in time. */
+FDF_API int fdf_server_wait(fdf_server* s, int32_t timeout_ms, int64_t* id);
+
+/* Status and timestamps of a request that has not been released. */
+FDF_API int fdf_server_info(fdf_server* s, int64_t id, fdf_request_info* info);
+
+/* Results of a done request: as fdf_get for one species, and the all-species
+ * FDF_Q_W_EPS deposit at z_end (N^3 doubles).  Host or device memory per
+ * on_device; both synchronise the request's stream only.  FDF_ESTATE if the
+ * request is not done. */
+FDF_API int fdf_server_get(fdf_server* s, int64_t id, int32_t species, double* x, double* q, double* w,
+                           int32_t on_device);
+FDF_API int fdf_server_deposit(fdf_server* s, int64_t id, double* out, int32_t on_device);
+
+/* Drop a finished request and return its memory to the arena.  FDF_ESTATE
+ * if it is still queued or running. */
+FDF_API int fdf_server_release(fdf_server* s, int64_t id);
+
+/* Seconds since fdf_server_create on the server's steady clock. */
+FDF_API double fdf_server_clock(const fdf_server* s);
+
+/* Queued and running request counts and arena bytes in use. */
+FDF_API int fdf_server_load(fdf_server* s, int32_t* queued, int32_t* running, size_t* bytes_in_use);
+
+/* Stop the worker, wait for the work already enqueued for running requests,
+ * drop every request (queued, running or finished) and free the arena.  NULL
+ * is allowed. */
+FDF_API void fdf_server_destroy(fdf_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -419,9 +419,22 @@ void fill_substep(const fdf_ctx* c, bool drift, double d1, double d2, bool kick,
             }
             sc.Wd_sum = split_ff(sum * q32);
             sc.mud_c = split_ff(sc.mud[jc]);
+            sc.mud_c_f = (float)sc.mud[jc];
+            double e[kMaxGL];
             for (int j = 0; j < c->ngl; ++j) {
                 sc.Wd_f[j] = (float)(Wd[j] * q32);
                 sc.dmud_f[j] = (float)(sc.mud[j] - sc.mud[jc]);
+                e[j] = sc.mud[jc] > 0 ? (sc.mud[j] - sc.mud[jc]) / sc.mud[jc] : 0.0;
+                u.emax = std::max(u.emax, std::fabs(e[j]));
+            }
+            // Cd_k = c_k sum_j Wd_j e_j^k with c_k the binomial coefficients of
+            // (1 + d)^(-1/2) - 1 = sum_k c_k d^k: c_1 = -1/2, c_k = c_(k-1) (1 - 2k)/(2k)
+            double ck = 1.0;
+            for (int k = 1; k <= kTaylor; ++k) {
+                ck *= (1.0 - 2.0 * k) / (2.0 * k);
+                double m = 0;
+                for (int j = 0; j < c->ngl; ++j) m += Wd[j] * std::pow(e[j], k);
+                sc.Cd[k - 1] = (float)(ck * m * q32);
             }
         }
         if (kick) {
@@ -666,12 +679,10 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     if (c->p.n_gl == 0) c->p.n_gl = auto_nodes(c->dlna);
     c->ngl = c->p.n_gl;
     if (c->p.precision != FDF_PREC_F64) {
-        // the split form's pass is compiled for 3, 4, 5, 6 or 8 drift nodes, and its
-        // kick (needed to ~1e-7) takes half as many: the error of an n-point rule falls
-        // like rho^(-2n), so ceil(n/2) nodes give about the square root of the drift's
-        static const int supported[] = {3, 3, 3, 4, 5, 6, 8, 8, 8};
-        c->ngl = supported[c->ngl];
-        c->nkick = (c->ngl + 1) / 2;
+        // the split form's kick (needed to ~1e-7) takes half the drift's nodes (2 to 4):
+        // the error of an n-point rule falls like rho^(-2n), so ceil(n/2) nodes give
+        // about the square root of the drift's
+        c->nkick = std::min(4, std::max(2, (c->ngl + 1) / 2));
     } else {
         c->nkick = c->ngl;
     }
@@ -755,19 +766,24 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
         twd[2 * j] = std::cos(2.0 * kPi * j / N);
         twd[2 * j + 1] = std::sin(2.0 * kPi * j / N);
     }
-    cudaError_t e = cudaMemcpy(c->tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice);
+    // uploads on the context's stream (not the legacy default stream, which would wait
+    // for every other blocking stream of the device), then waited for, since the host
+    // buffers belong to the caller
+    const std::vector<float> twf(twd.begin(), twd.end());
+    cudaStream_t s0 = c->stream;
+    cudaError_t e = cudaMemcpyAsync(c->tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s0);
     if (e == cudaSuccess) {
-        if (p->precision == FDF_PREC_F64) {
-            e = cudaMemcpy(c->tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice);
-        } else {
-            std::vector<float> twf(twd.begin(), twd.end());
-            e = cudaMemcpy(c->tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice);
-        }
+        if (p->precision == FDF_PREC_F64) e = cudaMemcpyAsync(c->tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, s0);
+        else e = cudaMemcpyAsync(c->tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, s0);
     }
-    if (e == cudaSuccess) e = cudaMemcpy(c->cdf_t, t->cdf_t, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->cdf_F, t->cdf_F, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(c->dflag, 0, 64);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->sf, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->cdf_t, t->cdf_t, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice, s0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->cdf_F, t->cdf_F, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice, s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dflag, 0, 64, s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
+    // the fields stream takes the priority of the caller's stream
+    int prio = 0;
+    if (e == cudaSuccess && c->stream) e = cudaStreamGetPriority(c->stream, &prio);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->sf, cudaStreamNonBlocking, prio);
     for (int i = 0; i < c->nbuf && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&c->built[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->released[i], cudaEventDisableTiming);
@@ -782,7 +798,14 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     return FDF_OK;
 }
 
-int fdf_sample(fdf_ctx* c)
+}  // extern "C"
+
+namespace fdf {
+
+// fdf_sample without its final host synchronisation: everything is enqueued on
+// the context's streams, and a failed direction draw shows in the device flag
+// word only (ctx_error_flag).  The request server uses it to overlap requests.
+int sample_enqueue(fdf_ctx* c)
 {
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
     FDF_CUDA(cudaMemsetAsync(c->dflag, 0, 64, c->stream), "clearing flags");
@@ -812,13 +835,31 @@ int fdf_sample(fdf_ctx* c)
         rc = sort_particles(c);
         if (rc) return rc;
     }
-    int flag = 0;
-    FDF_CUDA(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "reading flags");
-    FDF_CUDA(cudaStreamSynchronize(c->stream), "sampling");
-    if (flag) return fail(FDF_EINVAL, "a direction could not be drawn in 64 attempts");
     c->sampled = true;
     c->stepped = false;
     c->k = 0;
+    return FDF_OK;
+}
+
+int* ctx_error_flag(fdf_ctx* c) { return c->dflag; }
+
+cudaStream_t ctx_stream(fdf_ctx* c) { return c->stream; }
+
+}  // namespace fdf
+
+extern "C" {
+
+int fdf_sample(fdf_ctx* c)
+{
+    int rc = sample_enqueue(c);
+    if (rc) return rc;
+    int flag = 0;
+    FDF_CUDA(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "reading flags");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "sampling");
+    if (flag) {
+        c->sampled = false;
+        return fail(FDF_EINVAL, "a direction could not be drawn in 64 attempts");
+    }
     return FDF_OK;
 }
 
@@ -891,6 +932,9 @@ int fdf_step(fdf_ctx* c, int32_t n)
             c->k = k1;
             c->disp += typical_displacement(c, c->lna(k0), c->lna(k1));
         }
+        a.drift_series = 1;
+        for (int u = 0; u < a.nsub; ++u)
+            if (a.sub[u].emax > kSeriesMaxE) a.drift_series = 0;
         for (int b : bufs_cur) {
             rc = acquire_grid(c, b);
             if (rc) return rc;
@@ -962,6 +1006,37 @@ int fdf_get_initial(fdf_ctx* c, int32_t species, uint32_t* X, double* q_sampled,
     return FDF_OK;
 }
 
+}  // extern "C"
+
+namespace fdf {
+
+// The deposit into device memory, enqueued on the context's stream without
+// waiting for it (fdf_deposit with out_on_device, minus its synchronisation).
+int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, double* out_dev)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!c->sampled) return fail(FDF_ESTATE, "fdf_deposit before fdf_sample");
+    if (species < -1 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
+    if (quantity < FDF_Q_W_EPS || quantity > FDF_Q_COUNT) return fail(FDF_EINVAL, "unknown quantity");
+    if (!out_dev) return fail(FDF_EINVAL, "out is NULL");
+    const size_t N3 = (size_t)c->p.n_grid * c->p.n_grid * c->p.n_grid;
+    FDF_CUDA(cudaMemsetAsync(out_dev, 0, N3 * 8, c->stream), "clearing the deposit grid");
+    const int64_t np = c->p.n_part;
+    const int64_t begin = species < 0 ? 0 : species * np;
+    const int64_t count = species < 0 ? c->n : np;
+    const double a = std::exp(c->lna(c->k));
+    return timed(c, FDF_K_OTHER, "deposit", [&] {
+        return launch_deposit(c->stream, c->p.precision, c->st, c->n, begin, count, np > 0 ? np : 1, c->p.m_ev, a,
+                              c->T_ev, quantity, c->p.n_grid, c->p.box_mpc, out_dev);
+    });
+}
+
+double* ctx_deposit_grid(fdf_ctx* c) { return c->dep; }
+
+}  // namespace fdf
+
+extern "C" {
+
 int fdf_deposit(fdf_ctx* c, int32_t species, int32_t quantity, double* out, int32_t out_on_device)
 {
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
@@ -971,15 +1046,7 @@ int fdf_deposit(fdf_ctx* c, int32_t species, int32_t quantity, double* out, int3
     if (!out) return fail(FDF_EINVAL, "out is NULL");
     const size_t N3 = (size_t)c->p.n_grid * c->p.n_grid * c->p.n_grid;
     double* grid = out_on_device ? out : c->dep;
-    FDF_CUDA(cudaMemsetAsync(grid, 0, N3 * 8, c->stream), "clearing the deposit grid");
-    const int64_t np = c->p.n_part;
-    const int64_t begin = species < 0 ? 0 : species * np;
-    const int64_t count = species < 0 ? c->n : np;
-    const double a = std::exp(c->lna(c->k));
-    int rc = timed(c, FDF_K_OTHER, "deposit", [&] {
-        return launch_deposit(c->stream, c->p.precision, c->st, c->n, begin, count, np > 0 ? np : 1, c->p.m_ev, a,
-                              c->T_ev, quantity, c->p.n_grid, c->p.box_mpc, grid);
-    });
+    int rc = deposit_enqueue(c, species, quantity, grid);
     if (rc) return rc;
     if (!out_on_device)
         FDF_CUDA(cudaMemcpyAsync(out, grid, N3 * 8, cudaMemcpyDeviceToHost, c->stream), "copy deposit");

@@ -20,6 +20,8 @@ struct FF {                     // float-float: value = hi + lo, |lo| <= ulp(hi)
 // Coefficients of one particle pass for one species.  Every integral is a sum
 // over Gauss-Legendre nodes a_j of the pass's interval in ln a:
 //   int g(a) dtau = sum_j W_j g(a_j),  W_j = w_j (dlna/2) / (a_j H(a_j)).
+constexpr int kTaylor = 12;     // terms of the drift correction series
+
 struct SpeciesCoef {
     // drift over [ln a_k, ln a_k+1]: D(q) = sum_j Wd_j / sqrt(q^2 + mud_j)
     double Wd[kMaxGL];
@@ -28,6 +30,10 @@ struct SpeciesCoef {
     FF mud_c;                   // mud at the centre node jc
     float Wd_f[kMaxGL];         // Wd_j times 2^32/L
     float dmud_f[kMaxGL];       // mud_j - mud_c
+    // the same correction as a series: sum_j Wd_j g(delta_j) = sum_k Cd_k t^k with
+    // t = mud_c / (q^2 + mud_c) (see k_push_split)
+    float Cd[kTaylor];          // c_k sum_j Wd_j e_j^k, e_j = (mud_j - mud_c) / mud_c, times 2^32/L
+    float mud_c_f;
     // kick over [lo, hi]: K_psi = sum Wk sqrt(q0^2 + muk), K_phi = sum Wk / sqrt(..)
     double Wk[kMaxGL];
     double muk[kMaxGL];
@@ -42,8 +48,11 @@ struct SpeciesCoef {
 struct SubStep {
     int do_drift;
     int do_kick;
+    double emax;                // largest |e_j| of any species (the series converges for <= 1/4)
     SpeciesCoef sp[kMaxSpecies];
 };
+
+constexpr double kSeriesMaxE = 0.25;
 
 constexpr int kMaxSub = 5;      // sub-steps per particle pass (an open kick and 4 steps)
 
@@ -54,6 +63,7 @@ struct PushArgs {
     int n_gl;                   // Gauss-Legendre nodes of the drift integral
     int n_kick;                 // nodes of the kick integrals
     int uniform_species;        // every species has the same mass: use sp[0]
+    int drift_series;           // the drift corrections of this pass converge as a series
     int N;                      // grid side
     int nsub;                   // sub-steps in this pass, 1..kMaxSub
     double L, invL, invh;
@@ -152,5 +162,16 @@ cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleS
 cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                            int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
                            int N, double L, double* grid);
+
+// Asynchronous forms of two entry points, for the request server: the work is
+// enqueued on the context's streams and nothing waits for it.
+//   sample_enqueue: fdf_sample minus its final check; a failed direction draw
+//     leaves a nonzero word at ctx_error_flag(c) (device memory).
+//   deposit_enqueue: fdf_deposit into device memory out_dev (N^3 doubles).
+int sample_enqueue(fdf_ctx* c);
+int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, double* out_dev);
+int* ctx_error_flag(fdf_ctx* c);
+cudaStream_t ctx_stream(fdf_ctx* c);
+double* ctx_deposit_grid(fdf_ctx* c);
 
 }  // namespace fdf

@@ -235,9 +235,10 @@ __device__ __forceinline__ FF scale_q(FF D, float q0, float dq)
     return r;
 }
 
-// NGL drift nodes and NK kick nodes are compile-time, so the quadrature loops
-// unroll into constant-bank operands; UNI: every species has the same mass.
-template <typename Gt, int NGL, int NK, bool UNI>
+// SERIES: the drift correction as a power series (else a loop over the drift
+// nodes); NK kick nodes are compile-time, so the loops unroll into constant-bank
+// operands; UNI: every species has the same mass.
+template <typename Gt, bool SERIES, int NK, bool UNI>
 __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constant__ PushArgs a,
                                                             uint32_t* __restrict__ X, const float* __restrict__ q0f,
                                                             float* __restrict__ dqf)
@@ -276,12 +277,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
                 const FF r = ff_rsqrt(ff_add(S, c.mud_c));
                 const float r2 = r.hi * r.hi;
                 float corr = 0.f;
+                if constexpr (SERIES) {
+                    // g(delta_j) = sum_k c_k delta_j^k with delta_j = e_j t, so
+                    // sum_j Wd_j g(delta_j) = sum_k Cd_k t^k (|e_j| <= 1/4, 0 <= t <= 1)
+                    const float t = c.mud_c_f * r2;
+                    corr = c.Cd[kTaylor - 1];
 #pragma unroll
-                for (int j = 0; j < NGL; ++j) {
-                    const float d = c.dmud_f[j] * r2;
-                    const float t = 1.f + d;
-                    const float y = rsqrtf(t);
-                    corr = fmaf(c.Wd_f[j], -d * y * __frcp_rn(fmaf(t, y, 1.f)), corr);
+                    for (int k = kTaylor - 2; k >= 0; --k) corr = fmaf(corr, t, c.Cd[k]);
+                    corr *= t;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kMaxGL; ++j) {
+                        if (j < a.n_gl) {
+                            const float d = c.dmud_f[j] * r2;
+                            const float t = 1.f + d;
+                            const float y = rsqrtf(t);
+                            corr = fmaf(c.Wd_f[j], -d * y * __frcp_rn(fmaf(t, y, 1.f)), corr);
+                        }
+                    }
                 }
                 FF A;
                 fast_two_sum(c.Wd_sum.hi, __fadd_rn(c.Wd_sum.lo, corr), A.hi, A.lo);
@@ -324,22 +337,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
     }
 }
 
-template <typename Gt, int NGL, bool UNI>
-void push_split_ngl(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
+template <typename Gt, bool SERIES, bool UNI>
+void push_split_nk(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
 {
-    k_push_split<Gt, NGL, (NGL + 1) / 2, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf);
+    switch (a.n_kick) {
+        case 2: k_push_split<Gt, SERIES, 2, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
+        case 3: k_push_split<Gt, SERIES, 3, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
+        default: k_push_split<Gt, SERIES, 4, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
+    }
 }
 
 template <typename Gt, bool UNI>
 void push_split(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
 {
-    switch (a.n_gl) {
-        case 3: push_split_ngl<Gt, 3, UNI>(s, b, a, st); break;
-        case 4: push_split_ngl<Gt, 4, UNI>(s, b, a, st); break;
-        case 5: push_split_ngl<Gt, 5, UNI>(s, b, a, st); break;
-        case 6: push_split_ngl<Gt, 6, UNI>(s, b, a, st); break;
-        default: push_split_ngl<Gt, 8, UNI>(s, b, a, st); break;
-    }
+    if (a.drift_series) push_split_nk<Gt, true, UNI>(s, b, a, st);
+    else push_split_nk<Gt, false, UNI>(s, b, a, st);
 }
 
 // ---- the fused leapfrog pass, plain FP64 form --------------------------------

@@ -69,6 +69,23 @@ class fdf_tables(C.Structure):
     ]
 
 
+FDF_REQ_QUEUED, FDF_REQ_RUNNING, FDF_REQ_DONE, FDF_REQ_FAILED = 0, 1, 2, 3
+
+
+class fdf_request_info(C.Structure):
+    _fields_ = [
+        ("id", C.c_int64),
+        ("status", C.c_int32),
+        ("error", C.c_int32),
+        ("t_submit", C.c_double),
+        ("t_admit", C.c_double),
+        ("t_done", C.c_double),
+        ("footprint", C.c_size_t),
+        ("particle_steps", C.c_int64),
+        ("message", C.c_char * 160),
+    ]
+
+
 _lib = None
 _V = C.c_void_p
 _D = C.POINTER(C.c_double)
@@ -101,6 +118,16 @@ def lib():
             "fdf_error_string": (C.c_char_p, [C.c_int]),
             "fdf_last_error": (C.c_char_p, []),
             "fdf_destroy": (None, [_V]),
+            "fdf_server_create": (C.c_int, [C.c_size_t, C.c_int32, C.c_int32, C.POINTER(_V)]),
+            "fdf_server_submit": (C.c_int, [_V, P, T, C.POINTER(C.c_int64)]),
+            "fdf_server_wait": (C.c_int, [_V, C.c_int32, C.POINTER(C.c_int64)]),
+            "fdf_server_info": (C.c_int, [_V, C.c_int64, C.POINTER(fdf_request_info)]),
+            "fdf_server_get": (C.c_int, [_V, C.c_int64, C.c_int32, _V, _V, _V, C.c_int32]),
+            "fdf_server_deposit": (C.c_int, [_V, C.c_int64, _V, C.c_int32]),
+            "fdf_server_release": (C.c_int, [_V, C.c_int64]),
+            "fdf_server_clock": (C.c_double, [_V]),
+            "fdf_server_load": (C.c_int, [_V, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
+            "fdf_server_destroy": (None, [_V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -283,6 +310,67 @@ def fdf_destroy(ctx):
         lib().fdf_destroy(ctx)
 
 
+def fdf_server_create(hbm_budget, max_active, slice_steps):
+    srv = _V()
+    _check(lib().fdf_server_create(int(hbm_budget), int(max_active), int(slice_steps), C.byref(srv)),
+           "fdf_server_create")
+    return srv
+
+
+def fdf_server_submit(srv, params, tables):
+    rid = C.c_int64(0)
+    _check(lib().fdf_server_submit(srv, C.byref(params), C.byref(tables), C.byref(rid)), "fdf_server_submit")
+    return rid.value
+
+
+def fdf_server_wait(srv, timeout_ms=-1):
+    """Id of the next finished request, or None on timeout."""
+    rid = C.c_int64(0)
+    rc = lib().fdf_server_wait(srv, int(timeout_ms), C.byref(rid))
+    if rc == FDF_ETIMEOUT:
+        return None
+    _check(rc, "fdf_server_wait")
+    return rid.value
+
+
+def fdf_server_info(srv, rid):
+    info = fdf_request_info()
+    _check(lib().fdf_server_info(srv, int(rid), C.byref(info)), "fdf_server_info")
+    return info
+
+
+def fdf_server_get(srv, rid, species, x=None, q=None, w=None):
+    ptrs = [_ptr(a) for a in (x, q, w)]
+    dev = _same_side(ptrs)
+    _check(lib().fdf_server_get(srv, int(rid), species, ptrs[0][0], ptrs[1][0], ptrs[2][0], dev), "fdf_server_get")
+    return x, q, w
+
+
+def fdf_server_deposit(srv, rid, out):
+    p, dev = _ptr(out)
+    _check(lib().fdf_server_deposit(srv, int(rid), p, dev), "fdf_server_deposit")
+    return out
+
+
+def fdf_server_release(srv, rid):
+    _check(lib().fdf_server_release(srv, int(rid)), "fdf_server_release")
+
+
+def fdf_server_clock(srv):
+    return lib().fdf_server_clock(srv)
+
+
+def fdf_server_load(srv):
+    q, r, b = C.c_int32(0), C.c_int32(0), C.c_size_t(0)
+    _check(lib().fdf_server_load(srv, C.byref(q), C.byref(r), C.byref(b)), "fdf_server_load")
+    return q.value, r.value, b.value
+
+
+def fdf_server_destroy(srv):
+    if srv:
+        lib().fdf_server_destroy(srv)
+
+
 class Run:
     """One context: ``with Run(params_dict, tables_dict) as r: r.sample(); r.step(n); x, q, w = r.get(0)``."""
 
@@ -348,3 +436,59 @@ class Run:
 
     def state(self):
         return fdf_state(self.ctx)
+
+
+class Server:
+    """The request server: ``with Server(budget_bytes) as s: rid = s.submit(p, t); s.wait(); s.get(rid)``."""
+
+    def __init__(self, hbm_budget, max_active=8, slice_steps=8):
+        self.srv = fdf_server_create(hbm_budget, max_active, slice_steps)
+        self.params = {}
+
+    def close(self):
+        if self.srv:
+            fdf_server_destroy(self.srv)
+            self.srv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, params, tables):
+        P = make_params(params)
+        T, keep = make_tables(tables)
+        rid = fdf_server_submit(self.srv, P, T)
+        self.params[rid] = dict(params)
+        return rid
+
+    def wait(self, timeout_ms=-1):
+        return fdf_server_wait(self.srv, timeout_ms)
+
+    def info(self, rid):
+        return fdf_server_info(self.srv, rid)
+
+    def clock(self):
+        return fdf_server_clock(self.srv)
+
+    def load(self):
+        return fdf_server_load(self.srv)
+
+    def get(self, rid, species=0):
+        n = int(self.params[rid]["n_part"])
+        x = np.zeros((3, n))
+        q = np.zeros((3, n))
+        w = np.zeros(n)
+        fdf_server_get(self.srv, rid, species, x, q, w)
+        return x, q, w
+
+    def deposit(self, rid):
+        N = int(self.params[rid]["n_grid"])
+        out = np.zeros((N, N, N))
+        fdf_server_deposit(self.srv, rid, out)
+        return out
+
+    def release(self, rid):
+        fdf_server_release(self.srv, rid)
+        self.params.pop(rid, None)

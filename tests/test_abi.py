@@ -56,6 +56,10 @@ int main(void) {
   O(fdf_tables, nk); O(fdf_tables, na); O(fdf_tables, lnk); O(fdf_tables, lna); O(fdf_tables, T_psi);
   O(fdf_tables, T_phi); O(fdf_tables, dTphi_dlna); O(fdf_tables, ncdf); O(fdf_tables, cdf_t);
   O(fdf_tables, cdf_F);
+  printf("fdf_request_info %zu\n", sizeof(fdf_request_info));
+  O(fdf_request_info, id); O(fdf_request_info, status); O(fdf_request_info, error); O(fdf_request_info, t_submit);
+  O(fdf_request_info, t_admit); O(fdf_request_info, t_done); O(fdf_request_info, footprint);
+  O(fdf_request_info, particle_steps); O(fdf_request_info, message);
   return 0;
 }
 '''
@@ -73,7 +77,9 @@ def test_struct_layout_matches_c(fdf):
     c = _c_offsets()
     assert c["fdf_params"] == C.sizeof(fdf.fdf_params)
     assert c["fdf_tables"] == C.sizeof(fdf.fdf_tables)
-    for name, cls in (("fdf_params", fdf.fdf_params), ("fdf_tables", fdf.fdf_tables)):
+    assert c["fdf_request_info"] == C.sizeof(fdf.fdf_request_info)
+    for name, cls in (("fdf_params", fdf.fdf_params), ("fdf_tables", fdf.fdf_tables),
+                      ("fdf_request_info", fdf.fdf_request_info)):
         for f in cls._fields_:
             key = "%s.%s" % (name, f[0])
             if key in c:
