@@ -558,11 +558,27 @@ int join_fields(fdf_ctx* c)
     return FDF_OK;
 }
 
-int sort_particles(fdf_ctx* c)
+// Sort by the positions the particles will have halfway through the next pass,
+// which runs in direction dir from the current step.
+int sort_particles(fdf_ctx* c, int dir)
 {
+    SortLead lead{};
+    if (c->p.precision != FDF_PREC_F64) {
+        const double l1 = c->lna(c->k), l2 = c->lna(c->k + 0.5 * c->spp * dir);
+        double W[kMaxGL], a2[kMaxGL];
+        nodes(c, std::min(l1, l2), std::max(l1, l2), W, a2);
+        double dt = 0;
+        for (int j = 0; j < c->ngl; ++j) dt += W[j];
+        const double am = std::exp(0.5 * (l1 + l2));
+        lead.on = 1;
+        for (int s = 0; s < c->p.n_species; ++s) {
+            lead.dtau_q32[s] = (float)(dir * dt * 4294967296.0 / c->p.box_mpc);
+            lead.m2a2[s] = (float)(c->p.m_ev[s] * c->p.m_ev[s] * am * am);
+        }
+    }
     int rc = timed(c, FDF_K_SORT, "sort", [&] {
         return launch_sort(c->stream, c->p.precision, c->st, c->st_alt, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
-                           c->p.n_species, c->p.n_grid, c->p.box_mpc, c->key, c->hist, c->bsum, c->recs);
+                           c->p.n_species, c->p.n_grid, c->p.box_mpc, lead, c->key, c->hist, c->bsum, c->recs);
     });
     if (rc) return rc;
     std::swap(c->st, c->st_alt);
@@ -587,7 +603,7 @@ double typical_displacement(const fdf_ctx* c, double l1, double l2)
 }
 
 // Sort between passes if the schedule says so (c->disp accumulates per step).
-int maybe_sort(fdf_ctx* c, int steps_done)
+int maybe_sort(fdf_ctx* c, int steps_done, int dir)
 {
     const int every = c->p.sort_every;
     if (every < 0 || c->n == 0) return FDF_OK;
@@ -601,7 +617,7 @@ int maybe_sort(fdf_ctx* c, int steps_done)
         const double tile = (double)(1 << sort_tile_shift(c->p.n_grid)) * c->p.box_mpc / c->p.n_grid;
         go = c->disp > 4.0 * tile;
     }
-    return go ? sort_particles(c) : FDF_OK;
+    return go ? sort_particles(c, dir) : FDF_OK;
 }
 
 }  // namespace
@@ -831,13 +847,13 @@ int sample_enqueue(fdf_ctx* c)
     if (rc) return rc;
     rc = release_grid(c, b0);
     if (rc) return rc;
+    c->k = 0;
     if (c->p.sort_every >= 0 && c->n > 0) {
-        rc = sort_particles(c);
+        rc = sort_particles(c, 1);
         if (rc) return rc;
     }
     c->sampled = true;
     c->stepped = false;
-    c->k = 0;
     return FDF_OK;
 }
 
@@ -946,7 +962,7 @@ int fdf_step(fdf_ctx* c, int32_t n)
             if (rc) return rc;
         }
         if (j + 1 < passes) {
-            rc = maybe_sort(c, c->k - k_start);
+            rc = maybe_sort(c, (c->k - k_start) * dir, dir);
             if (rc) return rc;
         }
         std::swap(bufs_cur, bufs_next);

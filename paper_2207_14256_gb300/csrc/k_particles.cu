@@ -35,11 +35,12 @@ unsigned grid_for(int64_t n, int per_sm = 16)
 // ---- grid reads ------------------------------------------------------------
 template <typename Gt> struct Cell;
 template <> struct Cell<float> {
-    // one 256-bit load per cell (a cell's 8 slots are 32 contiguous, 32-byte aligned bytes)
+    // one 256-bit load per cell (a cell's 8 slots are 32 contiguous, 32-byte aligned bytes);
+    // not allocated in L1: the loads that would hit are too few to pay for the fills
     __device__ static void load(const float* G, uint32_t c, float v[8])
     {
         const float* g = G + 8 * (size_t)c;
-        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        asm("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
             : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
             : "l"(g));
     }
@@ -47,7 +48,10 @@ template <> struct Cell<float> {
 template <> struct Cell<__nv_bfloat16> {
     __device__ static void load(const __nv_bfloat16* G, uint32_t c, float v[8])
     {
-        const uint4 u = __ldg(reinterpret_cast<const uint4*>(G) + c);
+        uint4 u;
+        asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+            : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w)
+            : "l"(reinterpret_cast<const uint4*>(G) + c));
         const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -245,9 +249,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
 {
     const int64_t n = a.n;
     const uint32_t N = (uint32_t)a.N;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const SplitState cur = load_split(X, q0f, dqf, n, i);
-        const int s = UNI ? 0 : species_of(a, i);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // block-uniform trip count (i0 is the same for every thread of a block)
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool live = i < n;
+        SplitState cur{};
+        if (live) cur = load_split(X, q0f, dqf, n, i);
+        const int s = UNI || !live ? 0 : species_of(a, i);
         uint32_t X0 = cur.X0, X1 = cur.X1, X2 = cur.X2;
         const float qa = cur.qa, qb = cur.qb, qc = cur.qc;
         float da = cur.da, db = cur.db, dc = cur.dc;
@@ -261,6 +270,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
         const float q02 = s2;
         bool moved = false, kicked = false;
         for (int u = 0; u < a.nsub; ++u) {
+            if (!live) continue;
             const SubStep& st = a.sub[u];
             const SpeciesCoef& c = st.sp[s];
             if (st.do_drift) {
@@ -324,12 +334,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
                 kicked = true;
             }
         }
-        if (kicked) {
+        if (live && kicked) {
             __stcs(dqf + i, da);
             __stcs(dqf + n + i, db);
             __stcs(dqf + 2 * n + i, dc);
         }
-        if (moved) {
+        if (live && moved) {
             __stcs(X + i, X0);
             __stcs(X + n + i, X1);
             __stcs(X + 2 * n + i, X2);

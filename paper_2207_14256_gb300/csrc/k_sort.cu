@@ -31,7 +31,8 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v)  // 10 bits -> every thi
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_sort_keys(ParticleState st, int64_t n, int64_t n_part, uint32_t N,
                                                         int tile_shift, uint32_t tiles_per_species, double invh,
-                                                        uint32_t* __restrict__ key, uint32_t* __restrict__ hist)
+                                                        SortLead lead, uint32_t* __restrict__ key,
+                                                        uint32_t* __restrict__ hist)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += stride) {
@@ -39,19 +40,32 @@ __global__ void __launch_bounds__(kThreads) k_sort_keys(ParticleState st, int64_
         const bool live = i < n;
         const unsigned active = __ballot_sync(0xffffffffu, live);
         if (!live) continue;
+        const uint32_t s = (uint32_t)(i / n_part);
         uint32_t c[3];
+        if constexpr (Prec == FDF_PREC_F64) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if constexpr (Prec == FDF_PREC_F64) {
+            for (int d = 0; d < 3; ++d) {
                 int ci = (int)floor(st.xd[d * n + i] * invh);
                 ci = ci < 0 ? 0 : (ci >= (int)N ? (int)N - 1 : ci);
-                c[d] = (uint32_t)ci;
-            } else {
-                c[d] = __umulhi(st.X[d * n + i], N);
+                c[d] = (uint32_t)ci >> tile_shift;
             }
-            c[d] >>= tile_shift;
+        } else {
+            float q[3];
+            float q2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                q[d] = st.q0f[d * n + i] + st.dqf[d * n + i];
+                q2 = fmaf(q[d], q[d], q2);
+            }
+            const float k = lead.on ? lead.dtau_q32[s] * rsqrtf(q2 + lead.m2a2[s]) : 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                // a saturated shift only makes the bucket a poor guess, never wrong
+                const float shift = fminf(fmaxf(q[d] * k, -2.0e9f), 2.0e9f);
+                const uint32_t Xp = st.X[d * n + i] + (uint32_t)__float2int_rn(shift);
+                c[d] = __umulhi(Xp, N) >> tile_shift;
+            }
         }
-        const uint32_t s = (uint32_t)(i / n_part);
         const uint32_t k = s * tiles_per_species + (spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
         key[i] = k;
         // lanes with the same key (neighbours in a sorted state) add once through a leader
@@ -229,8 +243,8 @@ int sort_tile_shift(int N) { return 0; }
 size_t sort_record_bytes(int precision) { return precision == FDF_PREC_F64 ? sizeof(PlainRec) : sizeof(SplitRec); }
 
 cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, const ParticleState& b, int64_t n,
-                        int64_t n_part, int n_species, int N, double L, uint32_t* key, uint32_t* hist,
-                        uint32_t* bsum, void* recs)
+                        int64_t n_part, int n_species, int N, double L, const SortLead& lead, uint32_t* key,
+                        uint32_t* hist, uint32_t* bsum, void* recs)
 {
     if (n <= 0) return cudaSuccess;
     const int shift = sort_tile_shift(N);
@@ -241,9 +255,11 @@ cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, c
     if (e != cudaSuccess) return e;
     const unsigned g = grid_for(n);
     if (precision == FDF_PREC_F64)
-        k_sort_keys<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, key, hist);
+        k_sort_keys<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, lead, key,
+                                                         hist);
     else
-        k_sort_keys<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, key, hist);
+        k_sort_keys<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, lead, key,
+                                                         hist);
     e = scan_exclusive(s, hist, bins, bsum);
     if (e != cudaSuccess) return e;
     if (precision == FDF_PREC_F64) {
