@@ -165,6 +165,11 @@ def bench_ours(args, rank, world, dist):
     stream = torch.cuda.Stream(device=dev)
     P = fdf.make_params(p)
     T, keep = fdf.make_tables(tables)
+    # the schedule knobs (re-sort distance, bucket size, steps per pass) from the autotuner
+    tune = None
+    if not args.no_tune:
+        P, tune_ms, tune_trials = fdf.fdf_tune(P, T, stream)
+        tune = {"knobs": fdf.knobs(P), "best_run_ms": tune_ms, "timed_runs": tune_trials}
     N = p["n_grid"]
     dep = torch.zeros((N, N, N), dtype=torch.float64, device=dev)
     units = p["n_species"] * p["n_part"] * p["n_steps"]
@@ -244,7 +249,7 @@ def bench_ours(args, rank, world, dist):
             fdf.fdf_destroy(c3)
         plain = {"value": units / (pms / 1e3), "ms_per_step": pms, "push_ms_per_launch": push64[0] / push64[1]}
 
-    return dict(p=p, ms=ms, units=units, launches=launches, ktimes=ktimes, clocks=clk, e2e_s=e2e_s,
+    return dict(p=p, ms=ms, units=units, launches=launches, ktimes=ktimes, clocks=clk, e2e_s=e2e_s, tune=tune,
                 e2e_steps=e2e_steps, tab_bytes=tab_bytes, d2h=p["n_species"] * np_ * 7 * 8, plain=plain)
 
 
@@ -373,6 +378,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-served", action="store_true", help="skip the served stream")
+    ap.add_argument("--no-tune", action="store_true", help="use the automatic schedule knobs")
     ap.add_argument("--served-requests", type=int, default=64)
     ap.add_argument("--n-species", type=int, default=0,
                     help="override the species count (smaller device footprint for profiler captures)")
@@ -454,7 +460,8 @@ def main():
         "value": value, "ms_per_step": ms_per_step, "dtype": "f32",
         "config": {"workload": args.workload, "description": describe(r["p"]),
                    "l2": "inputs larger than L2 (%.1f GB particle state)" % (n_total * 48 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "schedule": r["tune"] or "automatic"},
         "roofline": roof,
         "e2e": {"value": whole_job_value(world, r["units"], e2e_s), "unit": UNIT, "h2d_bytes_per_step": r["tab_bytes"],
                 "d2h_bytes_per_step": r["d2h"],

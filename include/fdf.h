@@ -116,6 +116,10 @@ typedef struct fdf_params {
     int32_t  steps_per_pass;   /* leapfrog steps per particle pass, 1..4: the particle state is
                                   read and written once per pass (0 = 4 for the split forms,
                                   1 for the plain FP64 form) */
+    int32_t  sort_tile;        /* sort buckets are cubes of 2^sort_tile cells per axis, 0..3
+                                  (0 = single cells) */
+    int32_t  sort_cells;       /* with sort_every = 0: re-bucket when the typical particle has
+                                  moved this many cells since the last sort (0 = 4) */
 } fdf_params;
 
 /* Input tables, host memory, copied by fdf_create.
@@ -234,6 +238,19 @@ FDF_API const char* fdf_last_error(void);
 
 /* Free everything the context allocated.  NULL is allowed. */
 FDF_API void fdf_destroy(fdf_ctx* c);
+
+/* Autotuner of the schedule knobs that change speed only (no result beyond the
+ * stated tolerances): sort_cells, sort_tile and steps_per_pass.  It times whole
+ * runs (fdf_sample + fdf_step(n_steps)) of p on the device, one knob at a time
+ * (coordinate descent over sort_cells in {2, 4, 8}, sort_tile in {0, 1, 2},
+ * steps_per_pass in {2, 3, 4}), starting from the automatic choices, and writes
+ * the fastest parameter set to *out (p with the three knobs set).  The paper
+ * has no counterpart.  stream: a cudaStream_t or NULL; every trial allocates
+ * and frees its own context.  ms (may be NULL) receives the best run time;
+ * trials (may be NULL) the number of timed runs.  Only split forms are tuned;
+ * for FDF_PREC_F64 *out = *p. */
+FDF_API int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, fdf_params* out, double* ms,
+                     int32_t* trials);
 
 /* ---- request server (continuous batching) --------------------------------
  * Runs many independent runs ("requests": one fdf_params + fdf_tables each,

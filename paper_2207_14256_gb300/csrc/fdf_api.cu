@@ -127,7 +127,7 @@ struct Layout {
 
 int64_t sort_bins(const fdf_params& p)
 {
-    const int64_t tpa = p.n_grid >> sort_tile_shift(p.n_grid);
+    const int64_t tpa = p.n_grid >> sort_tile_shift(p);
     return tpa * tpa * tpa * p.n_species;
 }
 
@@ -217,6 +217,9 @@ int fdf::validate_params(const fdf_params* p)
     if (p->sort_every < -1) return fail(FDF_EINVAL, "sort_every must be -1, 0 or a step count");
     if (p->steps_per_pass < 0 || p->steps_per_pass > kMaxSub - 1)
         return fail(FDF_EINVAL, "steps_per_pass must be 0 (automatic) or 1..4");
+    if (p->sort_tile < 0 || p->sort_tile > 3 || (p->n_grid >> p->sort_tile) < 1)
+        return fail(FDF_EINVAL, "sort_tile must be 0..3 and at most log2(n_grid)");
+    if (p->sort_cells < 0) return fail(FDF_EINVAL, "sort_cells must be >= 0");
     return FDF_OK;
 }
 
@@ -578,7 +581,8 @@ int sort_particles(fdf_ctx* c, int dir)
     }
     int rc = timed(c, FDF_K_SORT, "sort", [&] {
         return launch_sort(c->stream, c->p.precision, c->st, c->st_alt, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
-                           c->p.n_species, c->p.n_grid, c->p.box_mpc, lead, c->key, c->hist, c->bsum, c->recs);
+                           c->p.n_species, c->p.n_grid, sort_tile_shift(c->p), c->p.box_mpc, lead, c->key, c->hist,
+                           c->bsum, c->recs);
     });
     if (rc) return rc;
     std::swap(c->st, c->st_alt);
@@ -613,9 +617,9 @@ int maybe_sort(fdf_ctx* c, int steps_done, int dir)
     } else {
         // The gather's working set stays in L2 long after a sort (the touched
         // region grows with the displacement but stays far below L2), so sort
-        // when the typical particle has crossed four tiles.
-        const double tile = (double)(1 << sort_tile_shift(c->p.n_grid)) * c->p.box_mpc / c->p.n_grid;
-        go = c->disp > 4.0 * tile;
+        // when the typical particle has crossed sort_cells cells (4 by default).
+        const double cell = c->p.box_mpc / c->p.n_grid;
+        go = c->disp > (c->p.sort_cells > 0 ? c->p.sort_cells : 4) * cell;
     }
     return go ? sort_particles(c, dir) : FDF_OK;
 }

@@ -145,7 +145,7 @@ cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& s
 cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a);
 
 // Counting sort of the particle state a into b by (species, Morton index of
-// the particle's tile of 2^tile_shift cells per axis).  key: n words; hist:
+// the particle's tile of 2^tile_shift cells per axis, tile_shift = sort_tile).  key: n words; hist:
 // n_species * tiles words; bsum: scan_scratch_words(bins) words; recs: n records
 // of sort_record_bytes(precision).
 // The split form buckets particles by where they will be halfway through the
@@ -156,11 +156,11 @@ struct SortLead {
     float dtau_q32[kMaxSpecies];  // conformal time of the lead, times 2^32 / L
     float m2a2[kMaxSpecies];      // m^2 a^2 at the middle of the lead
 };
-int sort_tile_shift(int N);
+inline int sort_tile_shift(const fdf_params& p) { return p.sort_tile; }
 size_t sort_record_bytes(int precision);
 cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, const ParticleState& b, int64_t n,
-                        int64_t n_part, int n_species, int N, double L, const SortLead& lead, uint32_t* key,
-                        uint32_t* hist, uint32_t* bsum, void* recs);
+                        int64_t n_part, int n_species, int N, int tile_shift, double L, const SortLead& lead,
+                        uint32_t* key, uint32_t* hist, uint32_t* bsum, void* recs);
 // Particles [begin, begin + count) of an array of n; outputs in id order
 // (out index = id - begin).
 cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,

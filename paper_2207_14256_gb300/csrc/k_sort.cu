@@ -236,18 +236,14 @@ unsigned grid_for(int64_t n)
 
 }  // namespace
 
-// Sort tiles of single cells: consecutive particles then share grid cells, which
-// the gather's loads serve once per warp.
-int sort_tile_shift(int N) { return 0; }
-
 size_t sort_record_bytes(int precision) { return precision == FDF_PREC_F64 ? sizeof(PlainRec) : sizeof(SplitRec); }
 
 cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, const ParticleState& b, int64_t n,
-                        int64_t n_part, int n_species, int N, double L, const SortLead& lead, uint32_t* key,
-                        uint32_t* hist, uint32_t* bsum, void* recs)
+                        int64_t n_part, int n_species, int N, int tile_shift, double L, const SortLead& lead,
+                        uint32_t* key, uint32_t* hist, uint32_t* bsum, void* recs)
 {
     if (n <= 0) return cudaSuccess;
-    const int shift = sort_tile_shift(N);
+    const int shift = tile_shift;
     const uint32_t tpa = (uint32_t)(N >> shift);
     const uint32_t tiles = tpa * tpa * tpa;
     const int64_t bins = (int64_t)tiles * n_species;

@@ -51,6 +51,8 @@ class fdf_params(C.Structure):
         ("n_gl", C.c_int32),
         ("sort_every", C.c_int32),
         ("steps_per_pass", C.c_int32),
+        ("sort_tile", C.c_int32),
+        ("sort_cells", C.c_int32),
     ]
 
 
@@ -118,6 +120,7 @@ def lib():
             "fdf_error_string": (C.c_char_p, [C.c_int]),
             "fdf_last_error": (C.c_char_p, []),
             "fdf_destroy": (None, [_V]),
+            "fdf_tune": (C.c_int, [P, T, _V, P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
             "fdf_server_create": (C.c_int, [C.c_size_t, C.c_int32, C.c_int32, C.POINTER(_V)]),
             "fdf_server_submit": (C.c_int, [_V, P, T, C.POINTER(C.c_int64)]),
             "fdf_server_wait": (C.c_int, [_V, C.c_int32, C.POINTER(C.c_int64)]),
@@ -185,7 +188,14 @@ def make_params(d):
     p.n_gl = int(d.get("n_gl", 0))
     p.sort_every = int(d.get("sort_every", 0))
     p.steps_per_pass = int(d.get("steps_per_pass", 0))
+    p.sort_tile = int(d.get("sort_tile", 0))
+    p.sort_cells = int(d.get("sort_cells", 0))
     return p
+
+
+def knobs(p):
+    """The schedule knobs of an fdf_params as a dict (for reports)."""
+    return {k: int(getattr(p, k)) for k in ("sort_every", "sort_cells", "sort_tile", "steps_per_pass", "n_gl")}
 
 
 def make_tables(d):
@@ -308,6 +318,16 @@ def fdf_last_error():
 def fdf_destroy(ctx):
     if ctx:
         lib().fdf_destroy(ctx)
+
+
+def fdf_tune(params, tables, stream=None):
+    """Returns (tuned fdf_params, best run ms, timed runs)."""
+    s = getattr(stream, "cuda_stream", stream)
+    out = fdf_params()
+    ms = C.c_double(0)
+    n = C.c_int32(0)
+    _check(lib().fdf_tune(C.byref(params), C.byref(tables), s, C.byref(out), C.byref(ms), C.byref(n)), "fdf_tune")
+    return out, ms.value, n.value
 
 
 def fdf_server_create(hbm_budget, max_active, slice_steps):

@@ -53,6 +53,7 @@ int main(void) {
   O(fdf_params, n_steps); O(fdf_params, precision); O(fdf_params, seed); O(fdf_params, h);
   O(fdf_params, omega_m); O(fdf_params, omega_r); O(fdf_params, A_s); O(fdf_params, n_s);
   O(fdf_params, k_pivot); O(fdf_params, flags); O(fdf_params, n_gl); O(fdf_params, sort_every); O(fdf_params, steps_per_pass);
+  O(fdf_params, sort_tile); O(fdf_params, sort_cells);
   O(fdf_tables, nk); O(fdf_tables, na); O(fdf_tables, lnk); O(fdf_tables, lna); O(fdf_tables, T_psi);
   O(fdf_tables, T_phi); O(fdf_tables, dTphi_dlna); O(fdf_tables, ncdf); O(fdf_tables, cdf_t);
   O(fdf_tables, cdf_F);

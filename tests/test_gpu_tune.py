@@ -1,0 +1,73 @@
+"""fdf_tune: the autotuner of the schedule knobs (sort_cells, sort_tile,
+steps_per_pass).
+
+The knobs change how the work is scheduled, not what is computed, so a run
+with the tuned parameters must give the same particles as a run with the
+automatic ones: positions to 1e-8 L and momenta to 1e-7 relative (merging two
+half kicks into one, or not, changes the rounding only), weights to 1e-8, and
+the sampled state bitwise.  The tuner must also return valid knob values and a
+best time no worse than the automatic choice it timed first.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2207_14256_gb300 import build
+    from paper_2207_14256_gb300 import fdf
+
+    build.build()
+    fdf.lib()
+    return fdf
+
+
+def _run(F, P, T, n_part, n_species):
+    ctx = F.fdf_create(P, T)
+    try:
+        F.fdf_sample(ctx)
+        F.fdf_step(ctx, P.n_steps)
+        out = []
+        for s in range(n_species):
+            x, q, w = np.zeros((3, n_part)), np.zeros((3, n_part)), np.zeros(n_part)
+            F.fdf_get(ctx, s, x, q, w)
+            out.append((x, q, w))
+    finally:
+        F.fdf_destroy(ctx)
+    return out
+
+
+def test_tuned_knobs_are_valid_and_change_no_result(F, inputs):
+    p = inputs.config("c2_128", n_part=48 ** 3, n_grid=64, n_species=2, m_ev=[0.1, 0.1], n_steps=40, seed=91)
+    tables = inputs.transfer_tables(p)
+    P = F.make_params(p)
+    T, keep = F.make_tables(tables)
+    tuned, ms, trials = F.fdf_tune(P, T)
+    k = F.knobs(tuned)
+    print("tuned knobs", k, "best run %.2f ms over %d timed runs" % (ms, trials))
+    assert trials >= 6 and ms > 0
+    assert k["sort_cells"] in (2, 4, 8) and k["sort_tile"] in (0, 1, 2) and k["steps_per_pass"] in (2, 3, 4)
+    # every other field is the caller's
+    for f, _ in F.fdf_params._fields_:
+        if f not in ("sort_every", "sort_cells", "sort_tile", "steps_per_pass"):
+            a, b = getattr(P, f), getattr(tuned, f)
+            assert (list(a) == list(b)) if f == "m_ev" else a == b, f
+    ref = _run(F, P, T, p["n_part"], 2)
+    got = _run(F, tuned, T, p["n_part"], 2)
+    L = p["box"]
+    for (x, q, w), (x0, q0, w0) in zip(got, ref):
+        dx = np.abs((x - x0 + L / 2) % L - L / 2)
+        assert dx.max() <= 1e-8 * L
+        assert (np.linalg.norm(q - q0, axis=0) / np.linalg.norm(q0, axis=0)).max() <= 1e-7
+        assert np.abs(w - w0).max() <= 1e-8
+
+
+def test_plain_form_is_returned_unchanged(F, inputs, c1_tables):
+    p = inputs.config("c1_32", n_part=4096, n_steps=8)
+    P = F.make_params(p)
+    T, keep = F.make_tables(c1_tables)
+    tuned, ms, trials = F.fdf_tune(P, T)
+    assert trials == 0
+    assert F.knobs(tuned) == F.knobs(P)
