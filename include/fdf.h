@@ -76,6 +76,9 @@ extern "C" {
 #define FDF_Q_W     1  /* w_k */
 #define FDF_Q_EPS   2  /* eps_k (no delta-f weight) */
 #define FDF_Q_COUNT 3  /* 1 */
+#define FDF_Q_W_QX  4  /* w_k q_k,x: the delta-f momentum density, whose divergence */
+#define FDF_Q_W_QY  5  /*   gives the (1 + delta) theta spectrum of Sec. 4 */
+#define FDF_Q_W_QZ  6
 
 /* ---- timed kernel classes (fdf_kernel_time) ------------------------------ */
 #define FDF_K_PUSH     0  /* fused drift + wrap + gather + kick */
@@ -120,6 +123,16 @@ typedef struct fdf_params {
                                   (0 = single cells) */
     int32_t  sort_cells;       /* with sort_every = 0: re-bucket when the typical particle has
                                   moved this many cells since the last sort (0 = 4) */
+    int32_t  interp_order;     /* interpolation order r of the force read and the deposit
+                                  (Sec. 4): 1 (or 0) cloud-in-cell, 2 triangular-shaped cloud */
+    double   superstep_tol;    /* super-steps (Sec. 2.1): > 0 builds the fields by transform only
+                                  at steps where the transfer functions of phi and psi changed
+                                  by more than this fraction (the paper uses 0.01) since the last
+                                  built step, and interpolates them linearly in ln a in between;
+                                  0 builds every step.  The change between steps j0 and j1 is,
+                                  for T = T_psi and T_phi, max |T(k, a_j1) - T(k, a_j0)| over 64
+                                  ln k points from 2 pi/L to sqrt(3) pi N/L, relative to
+                                  max |T(k, a_j0)| there; the larger of the two. */
 } fdf_params;
 
 /* Input tables, host memory, copied by fdf_create.
@@ -170,11 +183,18 @@ FDF_API int fdf_step(fdf_ctx* c, int32_t n);
 
 /* Weighted CIC density estimate of eq:empirical_rho at the current scale
  * factor: out[n] = sum_k v_k W(x_n - x_k) over the grid nodes n, with v_k
- * chosen by quantity (FDF_Q_*), over one species (0..n_species-1) or all (-1).
+ * chosen by quantity (FDF_Q_*), over one species (0..n_species-1) or all (-1);
+ * W is the kernel of order interp_order.
  * w_k = 1 - fbar(|q_k|)/fbar(p_k) (Sec. 2.2).  The raw sum is returned; the
  * M/N normalisation is the caller's.  out is N^3 doubles, device memory if
  * out_on_device else host memory. */
 FDF_API int fdf_deposit(fdf_ctx* c, int32_t species, int32_t quantity, double* out, int32_t out_on_device);
+
+/* fdf_deposit over one half of the ensemble: parity 0 deposits the particles
+ * with even ids, 1 those with odd ids, -1 all.  The cross-spectrum of the two
+ * halves removes the shot-noise plateau (Sec. 4 computes power spectra so). */
+FDF_API int fdf_deposit_subset(fdf_ctx* c, int32_t species, int32_t quantity, int32_t parity, double* out,
+                               int32_t out_on_device);
 
 /* Current state of one species in particle-index order: x[3][n_part] (Mpc,
  * in [0, L)), q[3][n_part] (eV), w[n_part] (delta-f weight, Sec. 2.2).  Any
@@ -219,6 +239,11 @@ FDF_API int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t, d
  * fdf_build_fields) replace the per-step grid build for every later call;
  * fields = NULL returns to building them. */
 FDF_API int fdf_set_fields(fdf_ctx* c, const double* fields, int32_t on_device);
+
+/* The super-step schedule: is_super[j] = 1 where the fields of step j are built
+ * by transform (every step when superstep_tol = 0), for j = 0..min(len, n_steps+1)-1;
+ * *count = the number of such steps.  Either pointer may be NULL. */
+FDF_API int fdf_supersteps(fdf_ctx* c, int32_t* is_super, int32_t len, int32_t* count);
 
 /* Current step index (0..n_steps) and its ln a. */
 FDF_API int fdf_state(fdf_ctx* c, int32_t* step, double* lna);

@@ -34,6 +34,8 @@ class OrParams(C.Structure):
         ("A_s", C.c_double),
         ("n_s", C.c_double),
         ("k_pivot", C.c_double),
+        ("interp_order", C.c_int32),
+        ("superstep_tol", C.c_double),
     ]
 
 
@@ -84,6 +86,9 @@ def lib():
         L.or_noise.argtypes = [C.POINTER(OrParams), _D]
         L.or_interp_table.argtypes = [C.POINTER(OrTables), _D, C.c_double, C.c_double]
         L.or_interp_table.restype = C.c_double
+        L.or_supersteps.argtypes = [C.POINTER(OrParams), C.POINTER(OrTables), C.POINTER(C.c_int32)]
+        L.or_tf_change.argtypes = [C.POINTER(OrParams), C.POINTER(OrTables), C.c_int, C.c_int]
+        L.or_tf_change.restype = C.c_double
         L.or_fft3d_inverse.argtypes = [C.c_int, _D]
         L.or_dft3d_inverse_naive.argtypes = [C.c_int, _D, _D]
         L.or_fields.argtypes = [C.POINTER(OrParams), C.POINTER(OrTables), _D, C.c_double, C.c_uint, _D, _D]
@@ -194,8 +199,17 @@ class Oracle:
     def interp_table(self, which, lnk, lna):
         return lib().or_interp_table(C.byref(self._T), _p(self._keep[which], C.c_double), lnk, lna)
 
+    def supersteps(self):
+        """The super-step schedule (Sec. 2.1): 1 where the fields are computed."""
+        out = np.zeros(self.params["n_steps"] + 1, np.int32)
+        lib().or_supersteps(C.byref(self._P), C.byref(self._T), _p(out, C.c_int32))
+        return out
+
+    def tf_change(self, j0, j1):
+        return lib().or_tf_change(C.byref(self._P), C.byref(self._T), int(j0), int(j1))
+
     def gather(self, F, x):
-        """Trilinear read of fields F [8][N][N][N] at one position x (3,)."""
+        """Read of fields F [8][N][N][N] at one position x (3,), order r = interp_order."""
         Fa = np.ascontiguousarray(F, dtype=np.float64).ravel()
         xa = np.ascontiguousarray(x, dtype=np.float64)
         out = np.zeros(8)

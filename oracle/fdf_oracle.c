@@ -484,29 +484,55 @@ void or_fields(const or_params* p, const or_tables* t, const double complex* R, 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Interpolation from the node grid (order r = 1, Sec. 4): trilinear.        */
+/* Interpolation from the node grid x_n = n L/N with the kernel of order r    */
+/* (Sec. 4 offers r = 1 and r = 2): the B-spline of degree r, a product of    */
+/* one-dimensional weights.                                                   */
+/*   r = 1 (cloud-in-cell): nodes i, i+1 around u = x/h, weights 1-f, f.      */
+/*   r = 2 (triangular-shaped cloud): the nearest node c and its neighbours,  */
+/*        d = u - c in [-1/2, 1/2): (1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2.  */
 /* ------------------------------------------------------------------------ */
-static void gather(int N, double L, const double* F, unsigned mask, const double x[3], double out[8])
+static int order_of(const or_params* p) { return p->interp_order == 2 ? 2 : 1; }
+
+static int kernel1d(int order, int N, double u, int idx[3], double w[3])
+{
+    if (order == 2) {
+        double c = floor(u + 0.5);
+        double d = u - c;
+        int i = (int)c % N;
+        if (i < 0) i += N;
+        idx[0] = (i + N - 1) % N;
+        idx[1] = i;
+        idx[2] = (i + 1) % N;
+        w[0] = 0.5 * (0.5 - d) * (0.5 - d);
+        w[1] = 0.75 - d * d;
+        w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+        return 3;
+    }
+    double fl = floor(u);
+    double f = u - fl;
+    int i = (int)fl % N;
+    if (i < 0) i += N;
+    idx[0] = i;
+    idx[1] = (i + 1) % N;
+    w[0] = 1.0 - f;
+    w[1] = f;
+    return 2;
+}
+
+static void gather(int N, double L, int order, const double* F, unsigned mask, const double x[3], double out[8])
 {
     const size_t N3 = (size_t)N * N * N;
     const double h = L / N;
-    int i0[3], i1[3];
-    double f[3];
-    for (int d = 0; d < 3; ++d) {
-        double u = x[d] / h;
-        double fl = floor(u);
-        f[d] = u - fl;
-        int i = (int)fl % N;
-        if (i < 0) i += N;
-        i0[d] = i;
-        i1[d] = (i + 1) % N;
-    }
+    int idx[3][3];
+    double w[3][3];
+    int m = 0;
+    for (int d = 0; d < 3; ++d) m = kernel1d(order, N, x[d] / h, idx[d], w[d]);
     for (int s = 0; s < 8; ++s) out[s] = 0.0;
-    for (int cz = 0; cz < 2; ++cz)
-        for (int cy = 0; cy < 2; ++cy)
-            for (int cx = 0; cx < 2; ++cx) {
-                double wgt = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) * (cz ? f[2] : 1.0 - f[2]);
-                size_t c = ((size_t)(cz ? i1[2] : i0[2]) * N + (cy ? i1[1] : i0[1])) * N + (cx ? i1[0] : i0[0]);
+    for (int cz = 0; cz < m; ++cz)
+        for (int cy = 0; cy < m; ++cy)
+            for (int cx = 0; cx < m; ++cx) {
+                double wgt = w[0][cx] * w[1][cy] * w[2][cz];
+                size_t c = ((size_t)idx[2][cz] * N + idx[1][cy]) * N + idx[0][cx];
                 for (int s = 0; s < 8; ++s)
                     if (mask & (1u << s)) out[s] += wgt * F[(size_t)s * N3 + c];
             }
@@ -514,7 +540,7 @@ static void gather(int N, double L, const double* F, unsigned mask, const double
 
 void or_gather(const or_params* p, const double* F, const double* x, double* out)
 {
-    gather(p->n_grid, p->box, F, 0xFFu, x, out);
+    gather(p->n_grid, p->box, order_of(p), F, 0xFFu, x, out);
 }
 
 /* Periodic wrap into [0, L). */
@@ -556,19 +582,88 @@ static void kick(const double g[8], const double q0[3], double m, const or_quad*
 }
 
 /* The fields used at step index k: the frozen set if given, else built. */
+/* ------------------------------------------------------------------------ */
+/* Super-steps (Sec. 2.1): the potential fields are computed only when the    */
+/* transfer functions have changed by more than a fraction tol (the paper     */
+/* uses 1%) since the last computed ones, and interpolated linearly between   */
+/* these super-steps.  Reading: the change between steps j0 and j1 is, for    */
+/* Q = T_psi and T_phi, the largest |Q(k, a_j1) - Q(k, a_j0)| over 64 ln k    */
+/* points spanning the mesh's modes (2 pi/L to sqrt(3) pi N/L), relative to  */
+/* the largest |Q(k, a_j0)| there; the larger of the two.  A step becomes a   */
+/* super-step when its change from the last super-step exceeds tol; steps 0   */
+/* and n_steps always are; interpolation is linear in ln a.                   */
+/* ------------------------------------------------------------------------ */
+double or_tf_change(const or_params* p, const or_tables* t, int j0, int j1)
+{
+    const double lk0 = log(2.0 * OR_PI / p->box), lk1 = log(sqrt(3.0) * OR_PI * p->n_grid / p->box);
+    const double la0 = or_lna(p, j0), la1 = or_lna(p, j1);
+    double worst = 0.0;
+    for (int which = 0; which < 2; ++which) {
+        const double* T = which ? t->T_phi : t->T_psi;
+        double dmax = 0.0, qmax = 0.0;
+        for (int i = 0; i < 64; ++i) {
+            double lk = lk0 + (lk1 - lk0) * i / 63.0;
+            double q0 = or_interp_table(t, T, lk, la0), q1 = or_interp_table(t, T, lk, la1);
+            if (fabs(q1 - q0) > dmax) dmax = fabs(q1 - q0);
+            if (fabs(q0) > qmax) qmax = fabs(q0);
+        }
+        if (qmax > 0.0 && dmax / qmax > worst) worst = dmax / qmax;
+    }
+    return worst;
+}
+
+void or_supersteps(const or_params* p, const or_tables* t, int* is_super)
+{
+    const int n = p->n_steps;
+    for (int j = 0; j <= n; ++j) is_super[j] = !(p->superstep_tol > 0.0);
+    is_super[0] = is_super[n] = 1;
+    if (!(p->superstep_tol > 0.0)) return;
+    int s = 0;
+    for (int j = 1; j < n; ++j)
+        if (or_tf_change(p, t, s, j) > p->superstep_tol) {
+            is_super[j] = 1;
+            s = j;
+        }
+}
+
 typedef struct {
     const or_params* p;
     const or_tables* t;
     const double* frozen;
     double complex* R;
+    int* is_super;          /* the super-step schedule, or NULL (every step computed) */
 } field_src;
+
+static void field_src_schedule(field_src* fs)
+{
+    fs->is_super = NULL;
+    if (fs->frozen || !(fs->p->superstep_tol > 0.0)) return;
+    fs->is_super = (int*)malloc(sizeof(int) * (fs->p->n_steps + 1));
+    or_supersteps(fs->p, fs->t, fs->is_super);
+}
 
 static const double* fields_at(field_src* fs, double k, unsigned mask)
 {
     if (fs->frozen) return fs->frozen;
     size_t N3 = (size_t)fs->p->n_grid * fs->p->n_grid * fs->p->n_grid;
     double* F = (double*)calloc(8 * N3, sizeof(double));
-    or_fields(fs->p, fs->t, fs->R, or_lna(fs->p, k), mask, F, NULL);
+    const int kk = (int)k;
+    if (!fs->is_super || fs->is_super[kk]) {
+        or_fields(fs->p, fs->t, fs->R, or_lna(fs->p, k), mask, F, NULL);
+        return F;
+    }
+    /* between the super-steps s < k < e: linear in ln a */
+    int s = kk, e = kk;
+    while (!fs->is_super[s]) --s;
+    while (!fs->is_super[e]) ++e;
+    double* Fs = (double*)calloc(8 * N3, sizeof(double));
+    double* Fe = (double*)calloc(8 * N3, sizeof(double));
+    or_fields(fs->p, fs->t, fs->R, or_lna(fs->p, s), mask, Fs, NULL);
+    or_fields(fs->p, fs->t, fs->R, or_lna(fs->p, e), mask, Fe, NULL);
+    const double w = (or_lna(fs->p, k) - or_lna(fs->p, s)) / (or_lna(fs->p, e) - or_lna(fs->p, s));
+    for (size_t i = 0; i < 8 * N3; ++i) F[i] = (1.0 - w) * Fs[i] + w * Fe[i];
+    free(Fs);
+    free(Fe);
     return F;
 }
 
@@ -588,11 +683,12 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
     if (or_sample(p, t, gidx, n, X, qs, pmag) != 0) return -1;
     const int N = p->n_grid;
     const size_t N3 = (size_t)N * N * N;
-    field_src fs = {p, t, frozen, NULL};
+    field_src fs = {p, t, frozen, NULL, NULL};
     if (!frozen) {
         fs.R = (double complex*)malloc(sizeof(double complex) * N3);
         or_noise(p, fs.R);
     }
+    field_src_schedule(&fs);
     const double* F = fields_at(&fs, 0.0, 0xFFu);
     const double a0 = exp(or_lna(p, 0.0));
     const double tau0 = or_tau(p, a0);
@@ -601,7 +697,7 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
     for (int64_t i = 0; i < n; ++i) {
         double xi[3], g[8];
         for (int d = 0; d < 3; ++d) xi[d] = L * ((double)X[d * n + i] * (1.0 / 4294967296.0));
-        gather(N, L, F, 0xFFu, xi, g);
+        gather(N, L, order_of(p), F, 0xFFu, xi, g);
         double m = mass_of(p, gidx[i]);
         double eps = sqrt(pmag[i] * pmag[i] + m * m * a0 * a0);
         for (int d = 0; d < 3; ++d) {
@@ -613,6 +709,7 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
     }
     fields_done(&fs, F);
     free(fs.R);
+    free(fs.is_super);
     return 0;
 }
 
@@ -630,11 +727,12 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
     const size_t N3 = (size_t)N * N * N;
     const int dir = k_to > k_from ? 1 : -1;
     const double L = p->box;
-    field_src fs = {p, t, frozen, NULL};
+    field_src fs = {p, t, frozen, NULL, NULL};
     if (!frozen) {
         fs.R = (double complex*)malloc(sizeof(double complex) * N3);
         or_noise(p, fs.R);
     }
+    field_src_schedule(&fs);
     const double* Fk = fields_at(&fs, (double)k_from, 0x7Fu);
     for (int k = k_from; k != k_to; k += dir) {
         const double* Fn = fields_at(&fs, (double)(k + dir), 0x7Fu);
@@ -652,13 +750,13 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
                 qi[d] = q[d * n + i];
                 q0i[d] = q0[d * n + i];
             }
-            gather(N, L, Fk, 0x7Fu, xi, g);
+            gather(N, L, order_of(p), Fk, 0x7Fu, xi, g);
             kick(g, q0i, m, &Qopen, qi);
             double qq = qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2];
             double D = 0.0;
             for (int j = 0; j < OR_NGL; ++j) D += Qdrift.wdt[j] / sqrt(qq + m * m * Qdrift.a2[j]);
             for (int d = 0; d < 3; ++d) xi[d] = wrap(xi[d] + D * qi[d], L);
-            gather(N, L, Fn, 0x7Fu, xi, g);
+            gather(N, L, order_of(p), Fn, 0x7Fu, xi, g);
             kick(g, q0i, m, &Qclose, qi);
             for (int d = 0; d < 3; ++d) {
                 x[d * n + i] = xi[d];
@@ -670,6 +768,7 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
     }
     fields_done(&fs, Fk);
     free(fs.R);
+    free(fs.is_super);
     return 0;
 }
 
@@ -696,29 +795,31 @@ void or_weights(const or_params* p, int64_t n, const double* q, const double* pm
 void or_deposit(const or_params* p, const int64_t* gidx, int64_t n, const double* x, const double* q,
                 const double* w, double a, int quantity, double* grid)
 {
-    const int N = p->n_grid;
+    const int N = p->n_grid, order = order_of(p);
     const double L = p->box, h = L / N;
     for (int64_t i = 0; i < n; ++i) {
         double m = mass_of(p, gidx[i]);
         double qq = q[i] * q[i] + q[n + i] * q[n + i] + q[2 * n + i] * q[2 * n + i];
         double eps = sqrt(qq + m * m * a * a);
-        double v = quantity == 0 ? w[i] * eps : quantity == 1 ? w[i] : quantity == 2 ? eps : 1.0;
-        int i0[3], i1[3];
-        double f[3];
+        /* 0: w eps (eq:empirical_rho), 1: w, 2: eps, 3: 1, 4-6: w q_x, w q_y, w q_z
+         * (the delta-f momentum density, whose divergence gives (1 + delta) theta) */
+        double v = quantity == 0 ? w[i] * eps
+                 : quantity == 1 ? w[i]
+                 : quantity == 2 ? eps
+                 : quantity == 3 ? 1.0
+                 : w[i] * q[(size_t)(quantity - 4) * n + i];
+        int idx[3][3];
+        double wt[3][3];
+        int mm = 0;
         for (int d = 0; d < 3; ++d) {
-            double u = x[d * n + i] / h;
-            double fl = floor(u);
-            f[d] = u - fl;
-            int ii = (int)fl % N;
-            if (ii < 0) ii += N;
-            i0[d] = ii;
-            i1[d] = (ii + 1) % N;
+            double xd = x[d * n + i];
+            mm = kernel1d(order, N, xd / h, idx[d], wt[d]);
         }
-        for (int cz = 0; cz < 2; ++cz)
-            for (int cy = 0; cy < 2; ++cy)
-                for (int cx = 0; cx < 2; ++cx) {
-                    double wgt = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) * (cz ? f[2] : 1.0 - f[2]);
-                    size_t c = ((size_t)(cz ? i1[2] : i0[2]) * N + (cy ? i1[1] : i0[1])) * N + (cx ? i1[0] : i0[0]);
+        for (int cz = 0; cz < mm; ++cz)
+            for (int cy = 0; cy < mm; ++cy)
+                for (int cx = 0; cx < mm; ++cx) {
+                    double wgt = wt[0][cx] * wt[1][cy] * wt[2][cz];
+                    size_t c = ((size_t)idx[2][cz] * N + idx[1][cy]) * N + idx[0][cx];
                     grid[c] += wgt * v;
                 }
     }

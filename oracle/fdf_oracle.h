@@ -30,6 +30,10 @@ typedef struct {
     uint64_t seed;
     double   h, omega_m, omega_r;   /* Omega_Lambda = 1 - omega_m - omega_r */
     double   A_s, n_s, k_pivot;
+    int32_t  interp_order; /* interpolation order r of Sec. 4: 1 (or 0) cloud-in-cell, 2 TSC */
+    double   superstep_tol; /* super-steps of Sec. 2.1: > 0 builds the fields only where the
+                               transfer functions changed by more than this fraction (paper:
+                               0.01) and interpolates linearly in ln a in between; 0 = off */
 } or_params;
 
 typedef struct {

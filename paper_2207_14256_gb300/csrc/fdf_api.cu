@@ -119,8 +119,8 @@ constexpr int kMaxBuf = 2 * (kMaxSub - 1) + 1;
 int grid_buffers(const fdf_params& p) { return std::min(kMaxBuf, 2 * steps_per_pass(p) + 1); }
 
 struct Layout {
-    size_t tabs, modeA, noise, cdf_t, cdf_F, tw, W0, W1, G[kMaxBuf], qs, stage, dep, flag, key, hist, bsum, recs,
-        total;
+    size_t tabs, modeA, noise, cdf_t, cdf_F, tw, W0, W1, G[kMaxBuf], Gss[2], qs, stage, dep, flag, key, hist, bsum,
+        recs, total;
     int nbuf;
     StateLayout s[2];
 };
@@ -153,6 +153,8 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     L.W1 = take(4 * N3 * complex_bytes(prec));
     L.nbuf = grid_buffers(p);
     for (int b = 0; b < L.nbuf; ++b) L.G[b] = take(N3 * grid_bytes_per_cell(prec));
+    // the two super-step grids an interpolated step reads (super-steps only)
+    for (int b = 0; b < 2; ++b) L.Gss[b] = take(p.superstep_tol > 0 ? N3 * grid_bytes_per_cell(prec) : 0);
     const bool split = prec != FDF_PREC_F64;
     const bool sorts = p.sort_every >= 0;
     for (int h = 0; h < (sorts ? 2 : 1); ++h) {
@@ -220,6 +222,9 @@ int fdf::validate_params(const fdf_params* p)
     if (p->sort_tile < 0 || p->sort_tile > 3 || (p->n_grid >> p->sort_tile) < 1)
         return fail(FDF_EINVAL, "sort_tile must be 0..3 and at most log2(n_grid)");
     if (p->sort_cells < 0) return fail(FDF_EINVAL, "sort_cells must be >= 0");
+    if (p->interp_order < 0 || p->interp_order > 2) return fail(FDF_EINVAL, "interp_order must be 0, 1 or 2");
+    if (!(p->superstep_tol >= 0.0) || !std::isfinite(p->superstep_tol))
+        return fail(FDF_EINVAL, "superstep_tol must be finite and >= 0");
     return FDF_OK;
 }
 
@@ -249,6 +254,11 @@ struct fdf_ctx {
     int uniform = 0;                        // all species share one mass
     double T_ev = 0, H0 = 0, ol = 0, lna0 = 0, lnaN = 0, dlna = 0, a0 = 0, tau0 = 0;
     int nk = 0, na = 0, ncdf = 0;
+    std::vector<double> tab_host;     // T_psi, T_phi, dT_phi/dln a on the host (super-step schedule)
+    std::vector<int> is_super;        // super-step schedule, n_steps + 1 entries
+    bool supersteps = false;
+    void* Gss[2] = {nullptr, nullptr};
+    int ssk[2] = {-1, -1};            // the step each super-step grid holds
     double lnk0 = 0, dlnk = 0, lnat0 = 0, dlnat = 0;
     Layout lay{};
     char* block = nullptr;
@@ -391,6 +401,7 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.n_gl = c->ngl;
     a.n_kick = c->nkick;
     a.uniform_species = c->uniform;
+    a.order = c->p.interp_order == 2 ? 2 : 1;
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
     a.invL = 1.0 / c->p.box_mpc;
@@ -495,6 +506,110 @@ int push(fdf_ctx* c, const PushArgs& a)
     return timed(c, FDF_K_PUSH, "particle pass", [&] { return launch_push(c->stream, c->p.precision, c->st, a); });
 }
 
+// ---- super-steps (Sec. 2.1) --------------------------------------------------------
+// The fields are built by transform only at super-steps: steps 0 and n_steps, and
+// every step whose transfer functions of phi and psi changed by more than
+// superstep_tol since the last super-step.  Between super-steps s < k < e they are
+// interpolated linearly in ln a.  The change between steps j0 and j1 is, for
+// T = T_psi and T_phi, the largest |T(k, a_j1) - T(k, a_j0)| over 64 ln k points
+// spanning the mesh's modes (2 pi/L to sqrt(3) pi N/L), relative to the largest
+// |T(k, a_j0)| there; the larger of the two.
+
+// Bilinear read of table `which` (0 T_psi, 1 T_phi), clamped at the edges.
+double table_at(const fdf_ctx* c, int which, double lnk, double lna)
+{
+    auto locate = [](double v, double v0, double dv, int n, int* i, double* f) {
+        const double pos = (v - v0) / dv;
+        if (pos <= 0.0) {
+            *i = 0;
+            *f = 0.0;
+        } else if (pos >= n - 1) {
+            *i = n - 2;
+            *f = 1.0;
+        } else {
+            *i = (int)pos;
+            *f = pos - *i;
+        }
+    };
+    int ik, ia;
+    double fk, fa;
+    locate(lnk, c->lnk0, c->dlnk, c->nk, &ik, &fk);
+    locate(lna, c->lnat0, c->dlnat, c->na, &ia, &fa);
+    const double* T = c->tab_host.data() + (size_t)which * c->na * c->nk;
+    const double* r0 = T + (size_t)ia * c->nk;
+    const double* r1 = r0 + c->nk;
+    const double v0 = (1.0 - fk) * r0[ik] + fk * r0[ik + 1];
+    const double v1 = (1.0 - fk) * r1[ik] + fk * r1[ik + 1];
+    return (1.0 - fa) * v0 + fa * v1;
+}
+
+double tf_change(const fdf_ctx* c, int j0, int j1)
+{
+    const double lk0 = std::log(2.0 * kPi / c->p.box_mpc);
+    const double lk1 = std::log(std::sqrt(3.0) * kPi * c->p.n_grid / c->p.box_mpc);
+    const double la0 = c->lna(j0), la1 = c->lna(j1);
+    double worst = 0.0;
+    for (int which = 0; which < 2; ++which) {
+        double dmax = 0.0, tmax = 0.0;
+        for (int i = 0; i < 64; ++i) {
+            const double lk = lk0 + (lk1 - lk0) * i / 63.0;
+            const double t0 = table_at(c, which, lk, la0), t1 = table_at(c, which, lk, la1);
+            dmax = std::max(dmax, std::fabs(t1 - t0));
+            tmax = std::max(tmax, std::fabs(t0));
+        }
+        if (tmax > 0.0) worst = std::max(worst, dmax / tmax);
+    }
+    return worst;
+}
+
+void superstep_schedule(fdf_ctx* c)
+{
+    const int n = c->p.n_steps;
+    c->supersteps = c->p.superstep_tol > 0.0;
+    c->is_super.assign(n + 1, c->supersteps ? 0 : 1);
+    c->is_super[0] = c->is_super[n] = 1;
+    if (!c->supersteps) return;
+    int s = 0;
+    for (int j = 1; j < n; ++j)
+        if (tf_change(c, s, j) > c->p.superstep_tol) {
+            c->is_super[j] = 1;
+            s = j;
+        }
+}
+
+// The fields of step k into G on the fields stream: a transform, or with super-steps
+// the interpolation between the two bracketing super-steps, which are built into the
+// two super-step grids as needed (a step that is itself a super-step is the copy w = 0).
+int produce_grid(fdf_ctx* c, int k, void* G)
+{
+    if (!c->supersteps) return build_fields(c, c->lna(k), G, c->sf);
+    int s = k, e = k;
+    while (!c->is_super[s]) --s;
+    while (!c->is_super[e]) ++e;
+    int slot[2] = {-1, -1};
+    const int need[2] = {s, e};
+    for (int n = 0; n < 2; ++n)
+        for (int i = 0; i < 2; ++i)
+            if (c->ssk[i] == need[n]) slot[n] = i;
+    for (int n = 0; n < 2; ++n) {
+        if (slot[n] >= 0) continue;
+        if (n == 1 && s == e) {
+            slot[1] = slot[0];
+            break;
+        }
+        const int i = slot[1 - n] == 0 ? 1 : 0;   // the grid the other end does not use
+        c->ssk[i] = -1;
+        int rc = build_fields(c, c->lna(need[n]), c->Gss[i], c->sf);
+        if (rc) return rc;
+        c->ssk[i] = need[n];
+        slot[n] = i;
+    }
+    const double w = s == e ? 0.0 : (c->lna(k) - c->lna(s)) / (c->lna(e) - c->lna(s));
+    return timed_on(c, c->sf, FDF_K_FIELDS_X, "super-step interpolation", [&] {
+        return launch_interp_grid(c->sf, c->p.precision, c->p.n_grid, c->Gss[slot[0]], c->Gss[slot[1]], w, G);
+    });
+}
+
 // The buffer holding the fields of step k, or -1.
 int find_grid(const fdf_ctx* c, int k)
 {
@@ -526,7 +641,7 @@ int ensure_grid(fdf_ctx* c, int k, unsigned busy, const void** G, int* buf)
         if (b < 0) return fail(FDF_EINVAL, "no free grid buffer");
         c->gk[b] = -1;
         if (c->has_release[b]) FDF_CUDA(cudaStreamWaitEvent(c->sf, c->released[b], 0), "wait release");
-        int rc = build_fields(c, c->lna(k), c->G[b], c->sf);
+        int rc = produce_grid(c, k, c->G[b]);
         if (rc) return rc;
         FDF_CUDA(cudaEventRecord(c->built[b], c->sf), "record build");
         c->gk[b] = k;
@@ -781,6 +896,10 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     std::memcpy(tab.data(), t->T_psi, ntab * 8);
     std::memcpy(tab.data() + ntab, t->T_phi, ntab * 8);
     std::memcpy(tab.data() + 2 * ntab, t->dTphi_dlna, ntab * 8);
+    c->tab_host = tab;
+    c->Gss[0] = b + L.Gss[0];
+    c->Gss[1] = b + L.Gss[1];
+    superstep_schedule(c);
     std::vector<double> twd(2 * (size_t)N);
     for (int j = 0; j < N; ++j) {
         twd[2 * j] = std::cos(2.0 * kPi * j / N);
@@ -836,6 +955,7 @@ int sample_enqueue(fdf_ctx* c)
     });
     if (rc) return rc;
     for (int i = 0; i < kMaxBuf; ++i) c->gk[i] = -1;
+    c->ssk[0] = c->ssk[1] = -1;
     rc = draw_noise(c);
     if (rc) return rc;
     const void* G0 = nullptr;
@@ -846,7 +966,8 @@ int sample_enqueue(fdf_ctx* c)
     if (rc) return rc;
     rc = timed(c, FDF_K_OTHER, "initial transform", [&] {
         return launch_initial(c->stream, c->p.precision, c->st, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
-                              c->p.m_ev, c->a0, c->tau0, c->p.n_grid, c->p.box_mpc, G0);
+                              c->p.m_ev, c->a0, c->tau0, c->p.interp_order == 2 ? 2 : 1, c->p.n_grid,
+                              c->p.box_mpc, G0);
     });
     if (rc) return rc;
     rc = release_grid(c, b0);
@@ -1032,12 +1153,13 @@ namespace fdf {
 
 // The deposit into device memory, enqueued on the context's stream without
 // waiting for it (fdf_deposit with out_on_device, minus its synchronisation).
-int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, double* out_dev)
+int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, int32_t parity, double* out_dev)
 {
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
     if (!c->sampled) return fail(FDF_ESTATE, "fdf_deposit before fdf_sample");
     if (species < -1 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
-    if (quantity < FDF_Q_W_EPS || quantity > FDF_Q_COUNT) return fail(FDF_EINVAL, "unknown quantity");
+    if (quantity < FDF_Q_W_EPS || quantity > FDF_Q_W_QZ) return fail(FDF_EINVAL, "unknown quantity");
+    if (parity < -1 || parity > 1) return fail(FDF_EINVAL, "parity must be -1, 0 or 1");
     if (!out_dev) return fail(FDF_EINVAL, "out is NULL");
     const size_t N3 = (size_t)c->p.n_grid * c->p.n_grid * c->p.n_grid;
     FDF_CUDA(cudaMemsetAsync(out_dev, 0, N3 * 8, c->stream), "clearing the deposit grid");
@@ -1047,7 +1169,8 @@ int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, double* out_d
     const double a = std::exp(c->lna(c->k));
     return timed(c, FDF_K_OTHER, "deposit", [&] {
         return launch_deposit(c->stream, c->p.precision, c->st, c->n, begin, count, np > 0 ? np : 1, c->p.m_ev, a,
-                              c->T_ev, quantity, c->p.n_grid, c->p.box_mpc, out_dev);
+                              c->T_ev, quantity, parity, c->p.interp_order == 2 ? 2 : 1, c->p.n_grid,
+                              c->p.box_mpc, out_dev);
     });
 }
 
@@ -1059,14 +1182,18 @@ extern "C" {
 
 int fdf_deposit(fdf_ctx* c, int32_t species, int32_t quantity, double* out, int32_t out_on_device)
 {
+    return fdf_deposit_subset(c, species, quantity, -1, out, out_on_device);
+}
+
+int fdf_deposit_subset(fdf_ctx* c, int32_t species, int32_t quantity, int32_t parity, double* out,
+                       int32_t out_on_device)
+{
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
     if (!c->sampled) return fail(FDF_ESTATE, "fdf_deposit before fdf_sample");
-    if (species < -1 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
-    if (quantity < FDF_Q_W_EPS || quantity > FDF_Q_COUNT) return fail(FDF_EINVAL, "unknown quantity");
     if (!out) return fail(FDF_EINVAL, "out is NULL");
     const size_t N3 = (size_t)c->p.n_grid * c->p.n_grid * c->p.n_grid;
     double* grid = out_on_device ? out : c->dep;
-    int rc = deposit_enqueue(c, species, quantity, grid);
+    int rc = deposit_enqueue(c, species, quantity, parity, grid);
     if (rc) return rc;
     if (!out_on_device)
         FDF_CUDA(cudaMemcpyAsync(out, grid, N3 * 8, cudaMemcpyDeviceToHost, c->stream), "copy deposit");
@@ -1133,6 +1260,18 @@ int fdf_set_fields(fdf_ctx* c, const double* fields, int32_t on_device)
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "fdf_set_fields");
     c->frozen = true;
+    return FDF_OK;
+}
+
+int fdf_supersteps(fdf_ctx* c, int32_t* is_super, int32_t len, int32_t* count)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    int n = 0;
+    for (size_t j = 0; j < c->is_super.size(); ++j) {
+        n += c->is_super[j];
+        if (is_super && (int64_t)j < len) is_super[j] = c->is_super[j];
+    }
+    if (count) *count = n;
     return FDF_OK;
 }
 

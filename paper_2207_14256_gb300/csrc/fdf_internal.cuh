@@ -64,6 +64,7 @@ struct PushArgs {
     int n_kick;                 // nodes of the kick integrals
     int uniform_species;        // every species has the same mass: use sp[0]
     int drift_series;           // the drift corrections of this pass converge as a series
+    int order;                  // interpolation order r: 1 cloud-in-cell, 2 TSC
     int N;                      // grid side
     int nsub;                   // sub-steps in this pass, 1..kMaxSub
     double L, invL, invh;
@@ -125,6 +126,9 @@ cudaError_t launch_fields_x(cudaStream_t s, int precision, const FieldArgs& a, c
                             void* G);
 // G (any precision) <-> [8][N^3] FP64.
 cudaError_t launch_fields_to_f64(cudaStream_t s, int precision, int N, const void* G, double* out);
+// G = (1 - w) A + w B over whole gather grids (super-steps, Sec. 2.1)
+cudaError_t launch_interp_grid(cudaStream_t s, int precision, int N, const void* A, const void* B, double w,
+                               void* G);
 cudaError_t launch_fields_from_f64(cudaStream_t s, int precision, int N, const double* in, void* G);
 
 // Particle passes.
@@ -141,7 +145,7 @@ struct ParticleState {
 };
 
 cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t n_part,
-                           const double* m_ev, double a0, double tau0, int N, double L, const void* G);
+                           const double* m_ev, double a0, double tau0, int order, int N, double L, const void* G);
 cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a);
 
 // Counting sort of the particle state a into b by (species, Morton index of
@@ -167,9 +171,11 @@ cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st
                           int64_t count, double L, double T_ev, double* x, double* q, double* w);
 cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                                   int64_t count, uint32_t* X, double* p);
+// parity: -1 every particle, 0 or 1 the particles whose id has that parity (the
+// two halves of the ensemble); order: the kernel order r (1 or 2).
 cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                            int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
-                           int N, double L, double* grid);
+                           int parity, int order, int N, double L, double* grid);
 
 // Asynchronous forms of two entry points, for the request server: the work is
 // enqueued on the context's streams and nothing waits for it.
@@ -177,7 +183,7 @@ cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& s
 //     leaves a nonzero word at ctx_error_flag(c) (device memory).
 //   deposit_enqueue: fdf_deposit into device memory out_dev (N^3 doubles).
 int sample_enqueue(fdf_ctx* c);
-int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, double* out_dev);
+int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, int32_t parity, double* out_dev);
 int* ctx_error_flag(fdf_ctx* c);
 cudaStream_t ctx_stream(fdf_ctx* c);
 double* ctx_deposit_grid(fdf_ctx* c);

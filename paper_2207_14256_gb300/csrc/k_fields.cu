@@ -445,11 +445,17 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_X) k_fields_x(FieldArgs a, c
     const int t = threadIdx.x % T, lo = threadIdx.x / T;
     const size_t N3 = (size_t)N * N * N;
     const size_t line = (size_t)blockIdx.x * TL + lo;
+    // the next packed grid's line is loaded while this one is transformed
+    V nxt[N1];
+    sfor<N1>([&](auto N1i) { nxt[N1i] = W1[line * N + N2 * N1i + t]; });
 #pragma unroll 1
     for (int p = 0; p < 4; ++p) {
-        const V* src = W1 + p * N3 + line * N;
         V v[N1];
-        sfor<N1>([&](auto N1i) { v[N1i] = src[N2 * N1i + t]; });
+        sfor<N1>([&](auto N1i) { v[N1i] = nxt[N1i]; });
+        if (p < 3) {
+            const V* src = W1 + (p + 1) * N3 + line * N;
+            sfor<N1>([&](auto N1i) { nxt[N1i] = src[N2 * N1i + t]; });
+        }
         __syncthreads();
         line_first<V, N>(v, t, s_tw, tr + lo * S::TSX);
         __syncthreads();
@@ -547,7 +553,66 @@ cudaError_t run_x(cudaStream_t s, const FieldArgs& a, const void* tw, const void
 
 }  // namespace
 
+// ---- super-steps: G = (1 - w) A + w B, element by element -------------------
+__global__ void __launch_bounds__(256) k_interp_f32(size_t n4, const float4* __restrict__ A,
+                                                    const float4* __restrict__ B, float w, float4* __restrict__ G)
+{
+    const float u = 1.f - w;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldcs(A + i), b = __ldcs(B + i);
+        G[i] = make_float4(u * a.x + w * b.x, u * a.y + w * b.y, u * a.z + w * b.z, u * a.w + w * b.w);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_interp_f64(size_t n2, const double2* __restrict__ A,
+                                                    const double2* __restrict__ B, double w,
+                                                    double2* __restrict__ G)
+{
+    const double u = 1.0 - w;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 a = A[i], b = B[i];
+        G[i] = make_double2(u * a.x + w * b.x, u * a.y + w * b.y);
+    }
+}
+
+// BF16 cells (8 values, 16 bytes): interpolated in FP32, rounded to nearest
+__global__ void __launch_bounds__(256) k_interp_bf16(size_t n, const uint4* __restrict__ A,
+                                                     const uint4* __restrict__ B, float w, uint4* __restrict__ G)
+{
+    const float u = 1.f - w;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 a = A[i], b = B[i];
+        const uint32_t ai[4] = {a.x, a.y, a.z, a.w}, bi[4] = {b.x, b.y, b.z, b.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float lo = u * __uint_as_float(ai[k] << 16) + w * __uint_as_float(bi[k] << 16);
+            const float hi = u * __uint_as_float(ai[k] & 0xFFFF0000u) + w * __uint_as_float(bi[k] & 0xFFFF0000u);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+            o[k] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        G[i] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
 int mode_table_size(int N) { return 3 * (N / 2 - 1) * (N / 2 - 1) + 1; }
+
+cudaError_t launch_interp_grid(cudaStream_t s, int precision, int N, const void* A, const void* B, double w,
+                               void* G)
+{
+    const size_t N3 = (size_t)N * N * N;
+    const size_t items = precision == FDF_PREC_F64 ? 4 * N3 : (precision == FDF_PREC_F32 ? 2 * N3 : N3);
+    size_t blocks = (items + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (precision == FDF_PREC_F64)
+        k_interp_f64<<<(unsigned)blocks, 256, 0, s>>>(items, (const double2*)A, (const double2*)B, w, (double2*)G);
+    else if (precision == FDF_PREC_F32)
+        k_interp_f32<<<(unsigned)blocks, 256, 0, s>>>(items, (const float4*)A, (const float4*)B, (float)w,
+                                                       (float4*)G);
+    else
+        k_interp_bf16<<<(unsigned)blocks, 256, 0, s>>>(items, (const uint4*)A, (const uint4*)B, (float)w, (uint4*)G);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mode_table(cudaStream_t s, int precision, const FieldArgs& a, const double* tabs64, void* A)
 {

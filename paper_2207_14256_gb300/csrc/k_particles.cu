@@ -84,6 +84,65 @@ __device__ __forceinline__ void gather_fixed(const Gt* __restrict__ G, uint32_t 
     }
 }
 
+// One axis of the order-2 kernel (Sec. 4, r = 2: the quadratic B-spline, or
+// triangular-shaped cloud) at a fixed-point coordinate: the nearest node c and
+// its neighbours, with d = u - c in [-1/2, 1/2) and weights (1/2 - d)^2/2,
+// 3/4 - d^2, (1/2 + d)^2/2.
+__device__ __forceinline__ void tsc_axis(uint32_t X, uint32_t N, uint32_t idx[3], float w[3])
+{
+    uint32_t i0, i1;
+    float f;
+    fixed_cell(X, N, i0, i1, f);
+    const bool up = f >= 0.5f;
+    const uint32_t c = up ? i1 : i0;
+    const float d = up ? f - 1.f : f;
+    idx[0] = c == 0u ? N - 1u : c - 1u;
+    idx[1] = c;
+    idx[2] = c + 1u == N ? 0u : c + 1u;
+    const float l = 0.5f - d, r = 0.5f + d;
+    w[0] = 0.5f * l * l;
+    w[1] = 0.75f - d * d;
+    w[2] = 0.5f * r * r;
+}
+
+template <typename Gt>
+__device__ __forceinline__ void gather_fixed_tsc(const Gt* __restrict__ G, uint32_t N, uint32_t X0, uint32_t X1,
+                                                 uint32_t X2, float g[8])
+{
+    uint32_t ix[3], iy[3], iz[3];
+    float wx[3], wy[3], wz[3];
+    tsc_axis(X0, N, ix, wx);
+    tsc_axis(X1, N, iy, wy);
+    tsc_axis(X2, N, iz, wz);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) g[s] = 0.f;
+#pragma unroll 1
+    for (int cz = 0; cz < 3; ++cz) {
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy) {
+            const uint32_t row = (iz[cz] * N + iy[cy]) * N;
+            const float wzy = wz[cz] * wy[cy];
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+                const float w = wx[cx] * wzy;
+                float v[8];
+                Cell<Gt>::load(G, row + ix[cx], v);
+#pragma unroll
+                for (int s = 0; s < 8; ++s) g[s] = fmaf(w, v[s], g[s]);
+            }
+        }
+    }
+}
+
+// The kernel of order r (1 or 2) at a fixed-point position.
+template <typename Gt>
+__device__ __forceinline__ void gather_order(int order, const Gt* __restrict__ G, uint32_t N, uint32_t X0,
+                                             uint32_t X1, uint32_t X2, float g[8])
+{
+    if (order == 2) gather_fixed_tsc<Gt>(G, N, X0, X1, X2, g);
+    else gather_fixed<Gt>(G, N, X0, X1, X2, g);
+}
+
 // FP64 read at an FP64 position in [0, L).
 __device__ __forceinline__ void gather_f64(const double* __restrict__ G, int N, double invh, const double x[3],
                                            double g[8])
@@ -116,6 +175,51 @@ __device__ __forceinline__ void gather_f64(const double* __restrict__ G, int N, 
             g[2 * k + 1] += w * v.y;
         }
     }
+}
+
+// FP64 order-2 read at an FP64 position in [0, L).
+__device__ __forceinline__ void gather_f64_tsc(const double* __restrict__ G, int N, double invh, const double x[3],
+                                               double g[8])
+{
+    int idx[3][3];
+    double w[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double u = x[d] * invh;
+        const double c = floor(u + 0.5);
+        const double e = u - c;
+        int i = (int)c;
+        if (i >= N) i -= N;
+        if (i < 0) i += N;
+        idx[d][0] = i == 0 ? N - 1 : i - 1;
+        idx[d][1] = i;
+        idx[d][2] = i + 1 == N ? 0 : i + 1;
+        w[d][0] = 0.5 * (0.5 - e) * (0.5 - e);
+        w[d][1] = 0.75 - e * e;
+        w[d][2] = 0.5 * (0.5 + e) * (0.5 + e);
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) g[s] = 0.0;
+    for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+            for (int cx = 0; cx < 3; ++cx) {
+                const double wt = w[0][cx] * w[1][cy] * w[2][cz];
+                const size_t cell = ((size_t)idx[2][cz] * N + idx[1][cy]) * N + idx[0][cx];
+                const double2* p = reinterpret_cast<const double2*>(G) + 4 * cell;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const double2 v = __ldg(p + k);
+                    g[2 * k] += wt * v.x;
+                    g[2 * k + 1] += wt * v.y;
+                }
+            }
+}
+
+__device__ __forceinline__ void gather_f64_order(int order, const double* __restrict__ G, int N, double invh,
+                                                 const double x[3], double g[8])
+{
+    if (order == 2) gather_f64_tsc(G, N, invh, x, g);
+    else gather_f64(G, N, invh, x, g);
 }
 
 __device__ __forceinline__ double wrap_f64(double x, double L, double invL)
@@ -156,7 +260,7 @@ struct Masses {
 // theta = k^2 tau psi / 2, nu = 4, omega = 4/3), eps = sqrt(p^2 + m^2 a_0^2).
 template <int Prec, typename Gt>
 __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t n, int64_t n_part, Masses ms,
-                                                      double a0, double tau0, int N, double L,
+                                                      double a0, double tau0, int order, int N, double L,
                                                       const Gt* __restrict__ G)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -168,10 +272,10 @@ __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t 
         x[1] = L * ((double)X1 * 2.3283064365386963e-10);
         x[2] = L * ((double)X2 * 2.3283064365386963e-10);
         if constexpr (Prec == FDF_PREC_F64) {
-            gather_f64(reinterpret_cast<const double*>(G), N, (double)N / L, x, g);
+            gather_f64_order(order, reinterpret_cast<const double*>(G), N, (double)N / L, x, g);
         } else {
             float gf[8];
-            gather_fixed<Gt>(G, (uint32_t)N, X0, X1, X2, gf);
+            gather_order<Gt>(order, G, (uint32_t)N, X0, X1, X2, gf);
 #pragma unroll
             for (int s = 0; s < 8; ++s) g[s] = (double)gf[s];
         }
@@ -316,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
             }
             if (st.do_kick) {
                 float g[8];
-                gather_fixed<Gt>(reinterpret_cast<const Gt*>(a.G[u]), N, X0, X1, X2, g);
+                gather_order<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, X0, X1, X2, g);
                 float Kpsi = 0.f, Kphi = 0.f;
 #pragma unroll
                 for (int j = 0; j < NK; ++j) {
@@ -389,7 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ P
             }
             if (st.do_kick) {
                 double g[8];
-                gather_f64(reinterpret_cast<const double*>(a.G[u]), a.N, a.invh, x, g);
+                gather_f64_order(a.order, reinterpret_cast<const double*>(a.G[u]), a.N, a.invh, x, g);
                 double Kpsi = 0.0, Kphi = 0.0;
                 for (int j = 0; j < a.n_kick; ++j) {
                     const double e = sqrt(q02 + c.muk[j]);
@@ -491,12 +595,14 @@ __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, i
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                       int64_t n_part, Masses ms, double a, double T, int quantity,
-                                                      int N, double L, double* __restrict__ grid)
+                                                      int parity, int order, int N, double L,
+                                                      double* __restrict__ grid)
 {
     const double invh = (double)N / L;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = begin + j;
+        if (parity >= 0 && (int)(st.id[i] & 1u) != parity) continue;
         const double m = ms.m[i / n_part];
         double x[3], q[3];
         load_state<Prec>(st, n, i, L, x, q);
@@ -506,33 +612,48 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
         if (quantity == FDF_Q_W_EPS) v = dfweight(qm, st.pmag[i], T) * eps;
         else if (quantity == FDF_Q_W) v = dfweight(qm, st.pmag[i], T);
         else if (quantity == FDF_Q_EPS) v = eps;
-        int i0[3], i1[3];
-        double f[3];
+        else if (quantity >= FDF_Q_W_QX) v = dfweight(qm, st.pmag[i], T) * q[quantity - FDF_Q_W_QX];
+        // per axis: the kernel's nodes and weights (order 1: 2 nodes, order 2: 3)
+        int idx[3][3];
+        double w[3][3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
+            double u;
             if constexpr (Prec == FDF_PREC_F64) {
-                const double u = x[d] * invh;
-                const double fl = floor(u);
-                f[d] = u - fl;
-                int ii = (int)fl;
-                if (ii >= N) ii -= N;
-                if (ii < 0) ii += N;
-                i0[d] = ii;
+                u = x[d] * invh;
             } else {
                 const uint32_t Xd = st.X[d * n + i];
-                i0[d] = (int)__umulhi(Xd, (uint32_t)N);
-                f[d] = (double)(Xd * (uint32_t)N) * 2.3283064365386963e-10;
+                u = (double)__umulhi(Xd, (uint32_t)N) + (double)(Xd * (uint32_t)N) * 2.3283064365386963e-10;
             }
-            i1[d] = i0[d] + 1 == N ? 0 : i0[d] + 1;
+            const double c = order == 2 ? floor(u + 0.5) : floor(u);
+            const double e = u - c;
+            int ii = (int)c;
+            if (ii >= N) ii -= N;
+            if (ii < 0) ii += N;
+            if (order == 2) {
+                idx[d][0] = ii == 0 ? N - 1 : ii - 1;
+                idx[d][1] = ii;
+                idx[d][2] = ii + 1 == N ? 0 : ii + 1;
+                w[d][0] = 0.5 * (0.5 - e) * (0.5 - e);
+                w[d][1] = 0.75 - e * e;
+                w[d][2] = 0.5 * (0.5 + e) * (0.5 + e);
+            } else {
+                idx[d][0] = ii;
+                idx[d][1] = ii + 1 == N ? 0 : ii + 1;
+                idx[d][2] = ii;
+                w[d][0] = 1.0 - e;
+                w[d][1] = e;
+                w[d][2] = 0.0;
+            }
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-            const double w = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) * (cz ? f[2] : 1.0 - f[2]);
-            const size_t cell =
-                ((size_t)(cz ? i1[2] : i0[2]) * N + (cy ? i1[1] : i0[1])) * N + (cx ? i1[0] : i0[0]);
-            atomicAdd(grid + cell, w * v);
-        }
+        const int m3 = order == 2 ? 3 : 2;
+        for (int cz = 0; cz < m3; ++cz)
+            for (int cy = 0; cy < m3; ++cy)
+                for (int cx = 0; cx < m3; ++cx) {
+                    const double wt = w[0][cx] * w[1][cy] * w[2][cz];
+                    const size_t cell = ((size_t)idx[2][cz] * N + idx[1][cy]) * N + idx[0][cx];
+                    atomicAdd(grid + cell, wt * v);
+                }
     }
 }
 
@@ -546,18 +667,20 @@ Masses masses_of(const double* m_ev)
 }  // namespace
 
 cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t n_part,
-                           const double* m_ev, double a0, double tau0, int N, double L, const void* G)
+                           const double* m_ev, double a0, double tau0, int order, int N, double L, const void* G)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned b = grid_for(n);
     const Masses ms = masses_of(m_ev);
     if (precision == FDF_PREC_F64)
-        k_initial<FDF_PREC_F64, double><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, N, L, (const double*)G);
+        k_initial<FDF_PREC_F64, double><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, order, N, L,
+                                                                   (const double*)G);
     else if (precision == FDF_PREC_F32)
-        k_initial<FDF_PREC_F32, float><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, N, L, (const float*)G);
+        k_initial<FDF_PREC_F32, float><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, order, N, L,
+                                                                 (const float*)G);
     else
         k_initial<FDF_PREC_BF16, __nv_bfloat16>
-            <<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, N, L, (const __nv_bfloat16*)G);
+            <<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, order, N, L, (const __nv_bfloat16*)G);
     return cudaGetLastError();
 }
 
@@ -602,17 +725,17 @@ cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleS
 
 cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                            int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
-                           int N, double L, double* grid)
+                           int parity, int order, int N, double L, double* grid)
 {
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
     const Masses ms = masses_of(m_ev);
     if (precision == FDF_PREC_F64)
-        k_deposit<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, N, L,
-                                                        grid);
+        k_deposit<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, parity,
+                                                        order, N, L, grid);
     else
-        k_deposit<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, N, L,
-                                                        grid);
+        k_deposit<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, parity,
+                                                        order, N, L, grid);
     return cudaGetLastError();
 }
 

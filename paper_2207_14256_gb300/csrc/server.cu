@@ -227,7 +227,7 @@ bool advance(fdf_server* S, Request* r)
         if (r->issued == r->p.n_steps) {
             // the deposit of every species, the sampling flag, the completion time
             // and the completion event, in stream order after the last slice
-            int rc = deposit_enqueue(r->ctx, -1, FDF_Q_W_EPS, ctx_deposit_grid(r->ctx));
+            int rc = deposit_enqueue(r->ctx, -1, FDF_Q_W_EPS, -1, ctx_deposit_grid(r->ctx));
             cudaError_t e = cudaSuccess;
             if (!rc) e = cudaMemcpyAsync(r->hflag, ctx_error_flag(r->ctx), sizeof(int), cudaMemcpyDeviceToHost,
                                          r->stream);

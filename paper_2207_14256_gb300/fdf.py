@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libfdf.so")
 FDF_OK, FDF_EINVAL, FDF_ENOMEM, FDF_ECUDA, FDF_ESTATE, FDF_ETIMEOUT, FDF_ENAN, FDF_ENOSYS = 0, -1, -2, -3, -4, -5, -6, -7
 FDF_PREC_F64, FDF_PREC_F32, FDF_PREC_BF16 = 0, 1, 2
 FDF_FLAG_FIXED_AMPLITUDE = 1
-FDF_Q_W_EPS, FDF_Q_W, FDF_Q_EPS, FDF_Q_COUNT = 0, 1, 2, 3
+FDF_Q_W_EPS, FDF_Q_W, FDF_Q_EPS, FDF_Q_COUNT, FDF_Q_W_QX, FDF_Q_W_QY, FDF_Q_W_QZ = 0, 1, 2, 3, 4, 5, 6
 FDF_K_PUSH, FDF_K_FIELDS_Z, FDF_K_FIELDS_Y, FDF_K_FIELDS_X, FDF_K_OTHER, FDF_K_SORT = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = {"push": 0, "fields_z": 1, "fields_y": 2, "fields_x": 3, "other": 4, "sort": 5}
 
@@ -53,6 +53,8 @@ class fdf_params(C.Structure):
         ("steps_per_pass", C.c_int32),
         ("sort_tile", C.c_int32),
         ("sort_cells", C.c_int32),
+        ("interp_order", C.c_int32),
+        ("superstep_tol", C.c_double),
     ]
 
 
@@ -108,11 +110,13 @@ def lib():
             "fdf_sample": (C.c_int, [_V]),
             "fdf_step": (C.c_int, [_V, C.c_int32]),
             "fdf_deposit": (C.c_int, [_V, C.c_int32, C.c_int32, _V, C.c_int32]),
+            "fdf_deposit_subset": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, _V, C.c_int32]),
             "fdf_get": (C.c_int, [_V, C.c_int32, _V, _V, _V, C.c_int32]),
             "fdf_get_initial": (C.c_int, [_V, C.c_int32, _V, _V, _V, C.c_int32]),
             "fdf_build_fields": (C.c_int, [_V, C.c_double, _V, C.c_int32]),
             "fdf_set_fields": (C.c_int, [_V, _V, C.c_int32]),
             "fdf_build_fields_noalloc": (C.c_int, [P, T, C.c_double, _V, _V]),
+            "fdf_supersteps": (C.c_int, [_V, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
             "fdf_state": (C.c_int, [_V, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
             "fdf_timing": (C.c_int, [_V, C.c_int32]),
             "fdf_kernel_time": (C.c_int, [_V, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -190,6 +194,8 @@ def make_params(d):
     p.steps_per_pass = int(d.get("steps_per_pass", 0))
     p.sort_tile = int(d.get("sort_tile", 0))
     p.sort_cells = int(d.get("sort_cells", 0))
+    p.interp_order = int(d.get("interp_order", 0))
+    p.superstep_tol = float(d.get("superstep_tol", 0.0))
     return p
 
 
@@ -244,6 +250,12 @@ def fdf_deposit(ctx, species, quantity, out):
     return out
 
 
+def fdf_deposit_subset(ctx, species, quantity, parity, out):
+    p, dev = _ptr(out)
+    _check(lib().fdf_deposit_subset(ctx, species, quantity, parity, p, dev), "fdf_deposit_subset")
+    return out
+
+
 def fdf_get(ctx, species, x=None, q=None, w=None):
     ptrs = [_ptr(a) for a in (x, q, w)]
     dev = _same_side(ptrs)
@@ -283,6 +295,15 @@ def fdf_set_fields(ctx, fields):
         fields = np.ascontiguousarray(fields, dtype=np.float64)
     p, dev = _ptr(fields)
     _check(lib().fdf_set_fields(ctx, p, dev), "fdf_set_fields")
+
+
+def fdf_supersteps(ctx, n_steps):
+    """(is_super array of n_steps + 1, count)."""
+    out = np.zeros(n_steps + 1, np.int32)
+    cnt = C.c_int32(0)
+    _check(lib().fdf_supersteps(ctx, out.ctypes.data_as(C.POINTER(C.c_int32)), len(out), C.byref(cnt)),
+           "fdf_supersteps")
+    return out, cnt.value
 
 
 def fdf_state(ctx):
@@ -441,9 +462,9 @@ class Run:
         fdf_get_initial(self.ctx, species, X, qs, p)
         return X, qs, p
 
-    def deposit(self, species=-1, quantity=FDF_Q_W_EPS):
+    def deposit(self, species=-1, quantity=FDF_Q_W_EPS, parity=-1):
         out = np.zeros((self.N, self.N, self.N))
-        fdf_deposit(self.ctx, species, quantity, out)
+        fdf_deposit_subset(self.ctx, species, quantity, parity, out)
         return out
 
     def build_fields(self, lna):
@@ -456,6 +477,9 @@ class Run:
 
     def state(self):
         return fdf_state(self.ctx)
+
+    def supersteps(self):
+        return fdf_supersteps(self.ctx, int(self.params["n_steps"]))[0]
 
 
 class Server:

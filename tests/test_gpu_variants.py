@@ -1,0 +1,153 @@
+"""GPU parity of the paper's variants against the oracle.
+
+* Interpolation order r = 2 (Sec. 4: the force read, the momentum transform
+  and the deposit use the quadratic B-spline): whole runs in the plain FP64
+  form (held to 1e-9) and in the split FP32 form (the contract's 1e-6 L,
+  1e-5, 1e-5), two species of different masses, a ragged particle count.
+* The delta-f momentum density (FDF_Q_W_QX..QZ), whose divergence gives the
+  (1 + delta) theta spectrum of Sec. 4, against the oracle's deposit of the
+  oracle's particles (relative L2 norm).
+* The half-ensemble deposits (Sec. 4 takes power spectra as the cross-spectrum
+  of two halves): even and odd ids against the oracle's deposit of those ids,
+  and the two halves summing to the whole.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_X, TOL_Q, TOL_W = 1e-6, 1e-5, 1e-5
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2207_14256_gb300 import build
+    from paper_2207_14256_gb300 import fdf
+
+    build.build()
+    fdf.lib()
+    return fdf
+
+
+def pdiff(a, b, L):
+    return (a - b + L / 2) % L - L / 2
+
+
+def errors(x, q, w, ref, L):
+    ex = np.max(np.abs(pdiff(x, ref["x"], L))) / L
+    eq = np.max(np.linalg.norm(q - ref["q"], axis=0) / np.linalg.norm(ref["q"], axis=0))
+    ew = np.max(np.abs(w - ref["w"]))
+    return ex, eq, ew
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tsc_runs_match_the_oracle(F, inputs, c1_tables, prec):
+    p = inputs.config("c1_32", n_part=4099, n_species=2, m_ev=[0.05, 0.2], n_grid=32, n_steps=60, precision=prec,
+                      seed=131, interp_order=2)
+    o = O.Oracle(p, c1_tables)
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        r.step(p["n_steps"])
+        res = [r.get(s) for s in range(2)]
+        dep = r.deposit(-1, F.FDF_Q_W_EPS)
+    a = math.exp(o.lna(p["n_steps"]))
+    dref = np.zeros_like(dep)
+    for s in range(2):
+        g = np.arange(s * p["n_part"], (s + 1) * p["n_part"])
+        ref = o.run(g)
+        ex, eq, ew = errors(*res[s], ref, p["box"])
+        print("TSC prec %d species %d: x %.3e L, q %.3e, w %.3e" % (prec, s, ex, eq, ew))
+        if prec == 0:
+            assert ex < 1e-9 and eq < 1e-9 and ew < 1e-10, (ex, eq, ew)
+        else:
+            assert ex < TOL_X and eq < TOL_Q and ew < TOL_W, (ex, eq, ew)
+        dref += o.deposit(g, ref["x"], ref["q"], ref["w"], a, 0)
+    err = np.linalg.norm(dep - dref) / np.linalg.norm(dref)
+    print("TSC prec %d deposit: %.3e" % (prec, err))
+    assert err < (1e-8 if prec == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_momentum_density_and_half_ensembles(F, inputs, c1_tables, order):
+    p = inputs.config("c1_32", n_part=5000, n_grid=16, n_steps=30, precision=1, seed=137, interp_order=order)
+    o = O.Oracle(p, c1_tables)
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        r.step(p["n_steps"])
+        mom = [r.deposit(-1, q) for q in (F.FDF_Q_W_QX, F.FDF_Q_W_QY, F.FDF_Q_W_QZ)]
+        whole = r.deposit(-1, F.FDF_Q_W_EPS)
+        halves = [r.deposit(-1, F.FDF_Q_W_EPS, parity) for parity in (0, 1)]
+    g = np.arange(p["n_part"])
+    ref = o.run(g)
+    a = math.exp(o.lna(p["n_steps"]))
+    for d, m in enumerate(mom):
+        dref = o.deposit(g, ref["x"], ref["q"], ref["w"], a, 4 + d)
+        err = np.linalg.norm(m - dref) / np.linalg.norm(dref)
+        print("order %d momentum density %d: %.3e" % (order, d, err))
+        assert err < 1e-5
+    for parity, h in zip((0, 1), halves):
+        sel = g[g % 2 == parity]
+        dref = o.deposit(sel, ref["x"][:, sel], ref["q"][:, sel], ref["w"][sel], a, 0)
+        err = np.linalg.norm(h - dref) / np.linalg.norm(dref)
+        print("order %d half %d: %.3e" % (order, parity, err))
+        assert err < 1e-5
+    assert np.abs(halves[0] + halves[1] - whole).max() <= 1e-12 * np.abs(whole).max()
+
+
+def test_bad_deposit_arguments_are_refused(F, inputs, c1_tables):
+    p = inputs.config("c1_32", n_part=100, n_grid=8, n_steps=2, precision=1)
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        for quantity, parity in ((7, -1), (-1, -1), (0, 2), (0, -2)):
+            with pytest.raises(F.FdfError) as e:
+                r.deposit(-1, quantity, parity)
+            assert e.value.code == F.FDF_EINVAL
+    with pytest.raises(F.FdfError):
+        F.fdf_footprint(F.make_params(dict(p, interp_order=3)))
+
+
+# ---- super-steps (Sec. 2.1) ------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+def test_supersteps_match_the_oracle(F, inputs, c1_tables, prec):
+    """The library's schedule equals the oracle's; each super-step is built by transform
+    once per run (the y pass counts the transforms); the run matches the oracle's
+    super-stepped run at the usual bars."""
+    p = inputs.config("c1_32", n_part=3000, n_grid=16, n_steps=80, precision=prec, seed=141, superstep_tol=0.01)
+    o = O.Oracle(p, c1_tables)
+    want = o.supersteps()
+    assert 2 < want.sum() < p["n_steps"] // 2, want.sum()
+    with F.Run(p, c1_tables) as r:
+        got = r.supersteps()
+        assert np.array_equal(got, want), (np.flatnonzero(got), np.flatnonzero(want))
+        F.fdf_timing(r.ctx, True)
+        r.sample()
+        r.step(p["n_steps"])
+        builds = F.fdf_kernel_time(r.ctx, F.FDF_K_FIELDS_Y)[1]
+        F.fdf_timing(r.ctx, False)
+        res = r.get(0)
+    print("super-steps: %d of %d steps built by transform (%d builds)" % (want.sum(), p["n_steps"] + 1, builds))
+    assert builds == want.sum()
+    ref = o.run(np.arange(p["n_part"]))
+    ex, eq, ew = errors(*res, ref, p["box"])
+    print("super-steps prec %d: x %.3e L, q %.3e, w %.3e" % (prec, ex, eq, ew))
+    if prec == 0:
+        assert ex < 1e-9 and eq < 1e-9 and ew < 1e-10, (ex, eq, ew)
+    else:
+        assert ex < TOL_X and eq < TOL_Q and ew < TOL_W, (ex, eq, ew)
+    # and the super-steps do change the result (the fields are interpolated)
+    exact = O.Oracle(dict(p, superstep_tol=0.0), c1_tables).run(np.arange(p["n_part"]))
+    assert np.max(np.abs(exact["q"] - ref["q"])) > 0
+
+
+def test_superstep_schedule_of_the_throughput_workload(F, inputs):
+    p = inputs.config("c3_3x256", n_part=1000, superstep_tol=0.01)
+    tables = inputs.transfer_tables(p)
+    with F.Run(p, tables) as r:
+        got = r.supersteps()
+    want = O.Oracle(p, tables).supersteps()
+    print("3 x 256^3 workload: %d of %d steps built by transform" % (want.sum(), p["n_steps"] + 1))
+    assert np.array_equal(got, want)

@@ -1,0 +1,166 @@
+"""Pins of the oracle's paper variants.
+
+* Interpolation order r = 2 (Sec. 4 offers r = 1 and r = 2), the quadratic
+  B-spline (triangular-shaped cloud) on the node grid:
+  - its weights at a node are 3/4 and 1/8, 1/8 per axis (a unit spike at node j
+    read at node j gives (3/4)^3, at a face neighbour (3/4)^2 (1/8), ...);
+  - it reproduces constants and linear fields exactly (the first moment of a
+    centred B-spline is preserved);
+  - the deposit is the transpose of the gather: sum_n grid_n F_n =
+    sum_k v_k F(x_k) for any field F (checked for both orders), and conserves
+    the deposited total.
+* The delta-f momentum density (quantities 4-6: w q_x, w q_y, w q_z), the
+  moment whose divergence gives the (1 + delta) theta spectrum of Sec. 4: it
+  is the deposit of v = w q_d, checked through the transpose identity against
+  an independent sum.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _oracle(inputs, c1_tables, order):
+    p = inputs.config("c1_32", n_grid=16, n_part=4096, n_steps=40, seed=21, interp_order=order)
+    return O.Oracle(p, c1_tables), p
+
+
+def test_tsc_weights_at_nodes(inputs, c1_tables):
+    o, p = _oracle(inputs, c1_tables, 2)
+    N, L = p["n_grid"], p["box"]
+    h = L / N
+    F = np.zeros((8, N, N, N))
+    F[:, 7, 5, 3] = 1.0            # spike at node (x=3, y=5, z=7)
+    at = lambda ix, iy, iz: o.gather(F, [ix * h, iy * h, iz * h])[0]
+    assert at(3, 5, 7) == pytest.approx(0.75 ** 3, abs=1e-15)
+    assert at(4, 5, 7) == pytest.approx(0.75 ** 2 * 0.125, abs=1e-15)
+    assert at(4, 6, 7) == pytest.approx(0.75 * 0.125 ** 2, abs=1e-15)
+    assert at(2, 4, 6) == pytest.approx(0.125 ** 3, abs=1e-15)
+    assert at(5, 5, 7) == 0.0
+    # periodic neighbour across the box edge
+    F[:] = 0.0
+    F[:, 0, 0, 0] = 1.0
+    assert o.gather(F, [(N - 1) * h, 0.0, 0.0])[0] == pytest.approx(0.75 ** 2 * 0.125, abs=1e-15)
+
+
+def test_tsc_reproduces_constants_and_linear_fields(inputs, c1_tables):
+    o, p = _oracle(inputs, c1_tables, 2)
+    N, L = p["n_grid"], p["box"]
+    h = L / N
+    rng = np.random.default_rng(8)
+    const = np.full((8, N, N, N), 2.5)
+    n = np.arange(N, dtype=float)
+    z, y, x = np.meshgrid(n, n, n, indexing="ij")
+    lin = np.stack([x - 3 * y + 7 * z] * 8)
+    for _ in range(50):
+        u = rng.uniform(1.5, N - 2.5, 3)     # the 3-node stencil stays clear of the wrap
+        assert np.allclose(o.gather(const, u * h), 2.5, rtol=0, atol=1e-14)
+        assert np.allclose(o.gather(lin, u * h), u[0] - 3 * u[1] + 7 * u[2], rtol=1e-13, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_deposit_is_the_transpose_of_the_gather(inputs, c1_tables, order):
+    o, p = _oracle(inputs, c1_tables, order)
+    N, L = p["n_grid"], p["box"]
+    rng = np.random.default_rng(11 + order)
+    n = 500
+    x = rng.uniform(0, L, (3, n))
+    q = rng.standard_normal((3, n)) * 5e-4
+    w = rng.standard_normal(n) * 1e-3
+    F = rng.standard_normal((8, N, N, N))
+    reads = np.array([o.gather(F, x[:, k])[0] for k in range(n)])
+    a = 1 / 32
+    grid = o.deposit(np.zeros(n, np.int64), x, q, w, a, 1)
+    assert abs((grid * F[0]).sum() - (w * reads).sum()) < 1e-12 * np.abs(w * reads).sum()
+    assert abs(grid.sum() - w.sum()) < 1e-13 * np.abs(w).sum()
+    # the momentum density, component by component
+    for d in range(3):
+        gq = o.deposit(np.zeros(n, np.int64), x, q, w, a, 4 + d)
+        v = w * q[d]
+        assert abs((gq * F[0]).sum() - (v * reads).sum()) < 1e-12 * np.abs(v * reads).sum()
+
+
+def test_tsc_deposit_of_a_particle_on_a_node(inputs, c1_tables):
+    o, p = _oracle(inputs, c1_tables, 2)
+    N, L = p["n_grid"], p["box"]
+    h = L / N
+    x = np.array([[3 * h], [5 * h], [7 * h]])
+    q = np.full((3, 1), 1e-4)
+    g = o.deposit(np.zeros(1, np.int64), x, q, np.array([2.0]), 1 / 32, 1)
+    assert g[7, 5, 3] == pytest.approx(2 * 0.75 ** 3, abs=1e-15)
+    assert g[8, 6, 4] == pytest.approx(2 * 0.125 ** 3, abs=1e-15)
+    assert np.count_nonzero(g) == 27
+
+
+# ---- super-steps (Sec. 2.1) ------------------------------------------------------------------
+def _ss_oracle(inputs, tables, tol, **over):
+    p = inputs.config("c1_32", n_grid=8, n_part=300, n_steps=40, seed=23, superstep_tol=tol)
+    p.update(over)
+    return O.Oracle(p, tables), p
+
+
+def test_superstep_schedule_rule(inputs, c1_tables):
+    """Every step inside an interval changes the tables by at most tol from its
+    first super-step; each super-step after the first exceeds tol from the one
+    before; the ends are super-steps; tol = 0 computes every step."""
+    o, p = _ss_oracle(inputs, c1_tables, 0.01)
+    s = o.supersteps()
+    n = p["n_steps"]
+    assert s[0] == 1 and s[n] == 1
+    sup = np.flatnonzero(s)
+    assert 2 < len(sup) < n + 1
+    for a, b in zip(sup[:-1], sup[1:]):
+        for k in range(a + 1, b):
+            assert o.tf_change(a, k) <= 0.01
+        if b != n:
+            assert o.tf_change(a, b) > 0.01
+    o0, _ = _ss_oracle(inputs, c1_tables, 0.0)
+    assert np.all(o0.supersteps() == 1)
+
+
+def test_superstep_change_closed_form(inputs, c1_tables):
+    """Tables T = c(k) (1 + b ln a): the change between two steps is |b| |ln a1 - ln a0| / |1 + b ln a0| scaled by
+    the same c, so it has a closed form, and tables constant in a never trigger a super-step."""
+    t = {k: np.array(v, copy=True) for k, v in c1_tables.items()}
+    lna = t["lna"]
+    b = 0.01
+    ck = 1.0 + 0.5 * np.cos(t["lnk"])
+    for key in ("T_psi", "T_phi"):
+        t[key] = ck[None, :] * (1.0 + b * lna[:, None])
+    o, p = _ss_oracle(inputs, t, 0.01)
+    for j0, j1 in ((0, 5), (10, 30), (3, 4)):
+        l0, l1 = o.lna(j0), o.lna(j1)
+        want = abs(b * (l1 - l0)) / abs(1.0 + b * l0)
+        assert o.tf_change(j0, j1) == pytest.approx(want, rel=1e-9)
+    for key in ("T_psi", "T_phi"):
+        t[key] = np.tile(ck, (len(lna), 1))
+    oc, pc = _ss_oracle(inputs, t, 0.01)
+    s = oc.supersteps()
+    assert s.sum() == 2 and s[0] == 1 and s[-1] == 1
+
+
+def test_supersteps_exact_for_tables_linear_in_ln_a(inputs, c1_tables):
+    """Fields that are linear in ln a are reproduced exactly by the interpolation, so a
+    super-stepped run equals the run that computes every step (to rounding); a
+    plausible slip (interpolating in a, or weighting the wrong end) breaks it."""
+    t = {k: np.array(v, copy=True) for k, v in c1_tables.items()}
+    lna = t["lna"]
+    ck = 1e-5 * (1.0 + np.sin(t["lnk"]))
+    # psi linear in ln a; phi constant, so phi_dot = a H dT_phi/d ln a = 0 (a H itself is
+    # not linear in ln a and would not interpolate exactly)
+    t["T_psi"] = ck[None, :] * (2.0 + 0.05 * lna[:, None])
+    t["T_phi"] = np.tile(1.5 * ck, (len(lna), 1))
+    t["dTphi_dlna"] = np.zeros_like(t["T_phi"])
+    o, p = _ss_oracle(inputs, t, 0.05)
+    assert 2 < o.supersteps().sum() < p["n_steps"] // 2
+    o0, _ = _ss_oracle(inputs, t, 0.0)
+    g = np.arange(p["n_part"])
+    a, b = o.run(g), o0.run(g)
+    assert np.max(np.abs(a["x"] - b["x"])) < 1e-9 * p["box"]
+    assert np.max(np.abs(a["q"] - b["q"]) / np.abs(b["q"]).max()) < 1e-12
+    # with the synthetic tables (not linear in ln a) the runs differ, but only a little
+    o1, _ = _ss_oracle(inputs, c1_tables, 0.01)
+    o2, _ = _ss_oracle(inputs, c1_tables, 0.0)
+    r1, r2 = o1.run(g), o2.run(g)
+    dq = np.max(np.linalg.norm(r1["q"] - r2["q"], axis=0) / np.linalg.norm(r2["q"], axis=0))
+    assert 0 < dq < 1e-3
