@@ -41,9 +41,9 @@ GRID_READ_BYTES_PER_CELL = {1: 28, 2: 14, 0: 56}
 
 # DRAM bytes per particle pass of the FP32 split form, from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean over the 50 passes of a one-species 256^3 run, profiles/
-# k_push_split_1x256.md), per particle of the launch.  Valid only for the kernel sources
+# k_push_split_1x256.md; schedule of the autotuner, sort_tile = 1), per particle of the launch.  Valid only for the kernel sources
 # it was measured on: their hash is checked and the figure dropped if they changed.
-PUSH_TRAFFIC = {"bytes_per_particle": 4.447e9 / 256 ** 3, "sources_sha256": "8decf3be1c918365:bb45ba9f916a8aff:e8b1efa1a66072ac"}
+PUSH_TRAFFIC = {"bytes_per_particle": 3.875e9 / 256 ** 3, "sources_sha256": "74e8eb820fbd581a:6e88be4572cdbdf4:e8b1efa1a66072ac"}
 PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
 
 
@@ -167,7 +167,11 @@ def bench_ours(args, rank, world, dist):
     T, keep = fdf.make_tables(tables)
     # the schedule knobs (re-sort distance, bucket size, steps per pass) from the autotuner
     tune = None
-    if not args.no_tune:
+    if args.schedule:
+        for k, v in json.loads(args.schedule).items():
+            setattr(P, k, int(v))
+        tune = {"knobs": fdf.knobs(P), "source": "--schedule"}
+    elif not args.no_tune:
         P, tune_ms, tune_trials = fdf.fdf_tune(P, T, stream)
         tune = {"knobs": fdf.knobs(P), "best_run_ms": tune_ms, "timed_runs": tune_trials}
     N = p["n_grid"]
@@ -201,6 +205,13 @@ def bench_ours(args, rank, world, dist):
             ktimes = {k: fdf.fdf_kernel_time(ctx, v) for k, v in fdf.KERNEL_CLASSES.items()}
             fdf.fdf_timing(ctx, False)
             clk = clocks.stop()
+            # host time to enqueue the steps of one run while the device works through
+            # them: the most a captured graph of the run could save
+            fdf.fdf_sample(ctx)
+            h0 = time.perf_counter()
+            fdf.fdf_step(ctx, p["n_steps"])
+            host_ms = (time.perf_counter() - h0) * 1e3
+            barrier()
     finally:
         fdf.fdf_destroy(ctx)
 
@@ -250,6 +261,7 @@ def bench_ours(args, rank, world, dist):
         plain = {"value": units / (pms / 1e3), "ms_per_step": pms, "push_ms_per_launch": push64[0] / push64[1]}
 
     return dict(p=p, ms=ms, units=units, launches=launches, ktimes=ktimes, clocks=clk, e2e_s=e2e_s, tune=tune,
+                host_ms=host_ms,
                 e2e_steps=e2e_steps, tab_bytes=tab_bytes, d2h=p["n_species"] * np_ * 7 * 8, plain=plain)
 
 
@@ -379,6 +391,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-served", action="store_true", help="skip the served stream")
     ap.add_argument("--no-tune", action="store_true", help="use the automatic schedule knobs")
+    ap.add_argument("--schedule", default="", help='schedule knobs as JSON, e.g. {"sort_tile": 1} (no tuning)')
     ap.add_argument("--served-requests", type=int, default=64)
     ap.add_argument("--n-species", type=int, default=0,
                     help="override the species count (smaller device footprint for profiler captures)")
@@ -468,6 +481,7 @@ def main():
                 "note": "fdf_create (table upload) + sample + steps + fdf_get of every species into pinned host "
                         "memory + fdf_destroy, per step"},
         "gpu_launches": r["launches"],
+        "host_enqueue_ms_per_step": r["host_ms"],
         "kernels": per_run,
         "clocks": r["clocks"],
     })

@@ -354,12 +354,25 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
     const size_t N3 = NN * N;
 #pragma unroll 1
     for (int p = 0; p < 4; ++p) {
+        // one branch per packed grid, so that each reads only the amplitudes it uses
+        // (psi; psi and phi; phi; phi_dot and psi) from shared memory
         V v[N1];
-        sfor<N1>([&](auto I) {
-            const T kz = kf * (T)sidx(N2 * I + t, N);
-            v[I] = packed<V>(p, Rv[I], As[(0 * N1 + I) * NT + threadIdx.x], As[(1 * N1 + I) * NT + threadIdx.x],
-                             As[(2 * N1 + I) * NT + threadIdx.x], kx, ky, kz);
-        });
+        auto form = [&](auto P) {
+            sfor<N1>([&](auto I) {
+                const T kz = kf * (T)sidx(N2 * I + t, N);
+                const int o = I * NT + threadIdx.x;
+                const T apsi = (P == 2) ? T(0) : As[0 * N1 * NT + o];
+                const T aphi = (P == 1 || P == 2) ? As[1 * N1 * NT + o] : T(0);
+                const T adot = (P == 3) ? As[2 * N1 * NT + o] : T(0);
+                v[I] = packed<V>(P, Rv[I], apsi, aphi, adot, kx, ky, kz);
+            });
+        };
+        switch (p) {
+            case 0: form(Idx<0>{}); break;
+            case 1: form(Idx<1>{}); break;
+            case 2: form(Idx<2>{}); break;
+            default: form(Idx<3>{}); break;
+        }
         line_first<V, N>(v, t, s_tw, tr + xo * S::TSZ);
         __syncthreads();
         V* dst = W0 + p * N3 + (size_t)jy * N + x0 + xo;
