@@ -133,7 +133,20 @@ typedef struct fdf_params {
                                   for T = T_psi and T_phi, max |T(k, a_j1) - T(k, a_j0)| over 64
                                   ln k points from 2 pi/L to sqrt(3) pi N/L, relative to
                                   max |T(k, a_j0)| there; the larger of the two. */
+    int32_t  eom;              /* the kick's equation of motion, each with the momentum frozen at
+                                  its z = 1e9 value so that the leapfrog stays symplectic:
+                                  FDF_EOM_GEODESIC (0, eq:releq_approx, the method's), or, in the
+                                  plain FP64 form only (FDF_ENOSYS otherwise), the comparison
+                                  forms FDF_EOM_CANONICAL (eq:releq_lag), FDF_EOM_SR_NEWTON
+                                  (eq:p_eq), FDF_EOM_Q_SIMPLE (eq:q_eq), FDF_EOM_NEWTONIAN */
 } fdf_params;
+
+/* ---- equations of motion (fdf_params.eom) -------------------------------- */
+#define FDF_EOM_GEODESIC  0  /* dq/dtau = -eps0 grad psi - (q0^2/eps0) grad phi + q0 (q0.grad phi)/eps0 + q0 phi_dot */
+#define FDF_EOM_CANONICAL 1  /* dP/dtau = -eps0 grad psi - (P0^2/eps0) grad phi (Sec. 3.2) */
+#define FDF_EOM_SR_NEWTON 2  /* dP/dtau = -((2 P0^2 + m^2 a^2)/eps0) grad psi (Sec. 5) */
+#define FDF_EOM_Q_SIMPLE  3  /* dq/dtau = -eps0 grad psi (Sec. 5) */
+#define FDF_EOM_NEWTONIAN 4  /* dq/dtau = -m a grad psi (Sec. 5: dq/dt = -m grad psi, dtau = dt/a) */
 
 /* Input tables, host memory, copied by fdf_create.
  *  T_psi, T_phi, dTphi_dlna: [na][nk] row-major, the transfer functions of

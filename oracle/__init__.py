@@ -36,6 +36,7 @@ class OrParams(C.Structure):
         ("k_pivot", C.c_double),
         ("interp_order", C.c_int32),
         ("superstep_tol", C.c_double),
+        ("eom", C.c_int32),
     ]
 
 

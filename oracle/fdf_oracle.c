@@ -566,19 +566,39 @@ static double mass_of(const or_params* p, int64_t g) { return p->m_ev[g / p->n_p
 /* One half-kick of eq:releq_approx (Sec. 3.3) with the potentials frozen at the half-step's
  * end point (reading R1): grad psi * int eps0 dtau, grad phi * q0^2 int
  * dtau/eps0, q0 (q0.grad phi) int dtau/eps0 and q0 phi_dot * int dtau. */
-static void kick(const double g[8], const double q0[3], double m, const or_quad* Q, double q[3])
+/*
+ * The other equations of motion (eom), each with the momentum (q or the canonical
+ * P) frozen at its z = 1e9 value so that the kick stays separable:
+ *   1 eq:releq_lag (Sec. 3.2):  dP/dtau = -eps0 grad psi - (P0^2/eps0) grad phi
+ *   2 eq:p_eq (Sec. 5):         dP/dtau = -((2 P0^2 + m^2 a^2)/eps0) grad psi
+ *   3 eq:q_eq (Sec. 5):         dq/dtau = -eps0 grad psi
+ *   4 Newtonian (Sec. 5):       dq/dtau = -m a grad psi  (reading: the paper's
+ *                               dq/dt = -m grad psi per cosmic time, dtau = dt/a)
+ * with eps0 = sqrt(P0^2 + m^2 a^2); the drift is eq:geodesic_approx for all.
+ */
+static void kick(const double g[8], const double q0[3], double m, const or_quad* Q, int eom, double q[3])
 {
     double q02 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
-    double Kpsi = 0.0, Kphi = 0.0, dtau = 0.0;
+    double Kpsi = 0.0, Kphi = 0.0, dtau = 0.0, Ka = 0.0;
     for (int j = 0; j < OR_NGL; ++j) {
         double e0 = sqrt(q02 + m * m * Q->a2[j]);
         Kpsi += Q->wdt[j] * e0;
         Kphi += Q->wdt[j] / e0;
         dtau += Q->wdt[j];
+        Ka += Q->wdt[j] * m * sqrt(Q->a2[j]);
     }
     double qdphi = q0[0] * g[3] + q0[1] * g[4] + q0[2] * g[5];
-    for (int d = 0; d < 3; ++d)
-        q[d] += -g[d] * Kpsi - g[3 + d] * (q02 * Kphi) + q0[d] * (qdphi * Kphi) + q0[d] * (g[6] * dtau);
+    if (eom == 0) {
+        for (int d = 0; d < 3; ++d)
+            q[d] += -g[d] * Kpsi - g[3 + d] * (q02 * Kphi) + q0[d] * (qdphi * Kphi) + q0[d] * (g[6] * dtau);
+        return;
+    }
+    for (int d = 0; d < 3; ++d) {
+        if (eom == 1) q[d] += -g[d] * Kpsi - g[3 + d] * (q02 * Kphi);
+        else if (eom == 2) q[d] += -g[d] * (Kpsi + q02 * Kphi);
+        else if (eom == 3) q[d] += -g[d] * Kpsi;
+        else q[d] += -g[d] * Ka;
+    }
 }
 
 /* The fields used at step index k: the frozen set if given, else built. */
@@ -751,13 +771,13 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
                 q0i[d] = q0[d * n + i];
             }
             gather(N, L, order_of(p), Fk, 0x7Fu, xi, g);
-            kick(g, q0i, m, &Qopen, qi);
+            kick(g, q0i, m, &Qopen, p->eom, qi);
             double qq = qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2];
             double D = 0.0;
             for (int j = 0; j < OR_NGL; ++j) D += Qdrift.wdt[j] / sqrt(qq + m * m * Qdrift.a2[j]);
             for (int d = 0; d < 3; ++d) xi[d] = wrap(xi[d] + D * qi[d], L);
             gather(N, L, order_of(p), Fn, 0x7Fu, xi, g);
-            kick(g, q0i, m, &Qclose, qi);
+            kick(g, q0i, m, &Qclose, p->eom, qi);
             for (int d = 0; d < 3; ++d) {
                 x[d * n + i] = xi[d];
                 q[d * n + i] = qi[d];

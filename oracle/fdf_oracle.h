@@ -34,6 +34,12 @@ typedef struct {
     double   superstep_tol; /* super-steps of Sec. 2.1: > 0 builds the fields only where the
                                transfer functions changed by more than this fraction (paper:
                                0.01) and interpolates linearly in ln a in between; 0 = off */
+    int32_t  eom;           /* equation of motion of the kick, each with the momentum frozen at
+                               its z = 1e9 value (separable, symplectic):
+                               0 eq:releq_approx (Sec. 3.3, the method's), 1 eq:releq_lag
+                               (canonical P), 2 eq:p_eq (special-relativistic, Newtonian
+                               gravity), 3 eq:q_eq (Sec. 5's simpler form), 4 Newtonian
+                               acceleration -m a grad psi (Sec. 5) */
 } or_params;
 
 typedef struct {

@@ -225,6 +225,9 @@ int fdf::validate_params(const fdf_params* p)
     if (p->interp_order < 0 || p->interp_order > 2) return fail(FDF_EINVAL, "interp_order must be 0, 1 or 2");
     if (!(p->superstep_tol >= 0.0) || !std::isfinite(p->superstep_tol))
         return fail(FDF_EINVAL, "superstep_tol must be finite and >= 0");
+    if (p->eom < FDF_EOM_GEODESIC || p->eom > FDF_EOM_NEWTONIAN) return fail(FDF_EINVAL, "unknown eom");
+    if (p->eom != FDF_EOM_GEODESIC && p->precision != FDF_PREC_F64)
+        return fail(FDF_ENOSYS, "the comparison equations of motion run in the plain FP64 form only");
     return FDF_OK;
 }
 
@@ -402,6 +405,7 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.n_kick = c->nkick;
     a.uniform_species = c->uniform;
     a.order = c->p.interp_order == 2 ? 2 : 1;
+    a.eom = c->p.eom;
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
     a.invL = 1.0 / c->p.box_mpc;
@@ -452,14 +456,16 @@ void fill_substep(const fdf_ctx* c, bool drift, double d1, double d2, bool kick,
             }
         }
         if (kick) {
-            double dt = 0;
+            double dt = 0, ka = 0;
             for (int j = 0; j < c->nkick; ++j) {
                 sc.Wk[j] = Wk[j];
                 sc.muk[j] = m2 * ak[j];
                 sc.Wk_f[j] = (float)Wk[j];
                 sc.muk_f[j] = (float)sc.muk[j];
                 dt += Wk[j];
+                ka += Wk[j] * std::sqrt(ak[j]);
             }
+            sc.Ka = c->p.m_ev[s] * ka;
             sc.dtau_k = dt;
             sc.dtau_k_f = (float)dt;
         }

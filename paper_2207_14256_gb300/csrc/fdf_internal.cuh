@@ -38,6 +38,7 @@ struct SpeciesCoef {
     double Wk[kMaxGL];
     double muk[kMaxGL];
     double dtau_k;
+    double Ka;                  // m sum_j Wk_j a_j (the Newtonian kick's integral)
     float Wk_f[kMaxGL];
     float muk_f[kMaxGL];
     float dtau_k_f;
@@ -65,6 +66,7 @@ struct PushArgs {
     int uniform_species;        // every species has the same mass: use sp[0]
     int drift_series;           // the drift corrections of this pass converge as a series
     int order;                  // interpolation order r: 1 cloud-in-cell, 2 TSC
+    int eom;                    // FDF_EOM_* (the plain FP64 form)
     int N;                      // grid side
     int nsub;                   // sub-steps in this pass, 1..kMaxSub
     double L, invL, invh;

@@ -501,9 +501,16 @@ __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ P
                     Kphi += c.Wk[j] / e;
                 }
                 const double qdphi = q0[0] * g[3] + q0[1] * g[4] + q0[2] * g[5];
+                // the terms of the kick by equation of motion (FDF_EOM_*): grad psi,
+                // grad phi, q0 (q0.grad phi) and q0 phi_dot coefficients
+                double A = Kpsi, B = q02 * Kphi, C = Kphi, Dt = c.dtau_k;
+                if (a.eom == FDF_EOM_CANONICAL) C = Dt = 0.0;
+                else if (a.eom == FDF_EOM_SR_NEWTON) { A = Kpsi + q02 * Kphi; B = C = Dt = 0.0; }
+                else if (a.eom == FDF_EOM_Q_SIMPLE) B = C = Dt = 0.0;
+                else if (a.eom == FDF_EOM_NEWTONIAN) { A = c.Ka; B = C = Dt = 0.0; }
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
-                    q[d] += -g[d] * Kpsi - g[3 + d] * (q02 * Kphi) + q0[d] * (qdphi * Kphi) + q0[d] * (g[6] * c.dtau_k);
+                    q[d] += -g[d] * A - g[3 + d] * B + q0[d] * (qdphi * C) + q0[d] * (g[6] * Dt);
                 kicked = true;
             }
         }

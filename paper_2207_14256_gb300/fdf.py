@@ -18,6 +18,7 @@ FDF_OK, FDF_EINVAL, FDF_ENOMEM, FDF_ECUDA, FDF_ESTATE, FDF_ETIMEOUT, FDF_ENAN, F
 FDF_PREC_F64, FDF_PREC_F32, FDF_PREC_BF16 = 0, 1, 2
 FDF_FLAG_FIXED_AMPLITUDE = 1
 FDF_Q_W_EPS, FDF_Q_W, FDF_Q_EPS, FDF_Q_COUNT, FDF_Q_W_QX, FDF_Q_W_QY, FDF_Q_W_QZ = 0, 1, 2, 3, 4, 5, 6
+FDF_EOM_GEODESIC, FDF_EOM_CANONICAL, FDF_EOM_SR_NEWTON, FDF_EOM_Q_SIMPLE, FDF_EOM_NEWTONIAN = 0, 1, 2, 3, 4
 FDF_K_PUSH, FDF_K_FIELDS_Z, FDF_K_FIELDS_Y, FDF_K_FIELDS_X, FDF_K_OTHER, FDF_K_SORT = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = {"push": 0, "fields_z": 1, "fields_y": 2, "fields_x": 3, "other": 4, "sort": 5}
 
@@ -55,6 +56,7 @@ class fdf_params(C.Structure):
         ("sort_cells", C.c_int32),
         ("interp_order", C.c_int32),
         ("superstep_tol", C.c_double),
+        ("eom", C.c_int32),
     ]
 
 
@@ -196,6 +198,7 @@ def make_params(d):
     p.sort_cells = int(d.get("sort_cells", 0))
     p.interp_order = int(d.get("interp_order", 0))
     p.superstep_tol = float(d.get("superstep_tol", 0.0))
+    p.eom = int(d.get("eom", 0))
     return p
 
 

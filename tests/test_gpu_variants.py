@@ -10,6 +10,9 @@
 * The half-ensemble deposits (Sec. 4 takes power spectra as the cross-spectrum
   of two halves): even and odd ids against the oracle's deposit of those ids,
   and the two halves summing to the whole.
+* Super-steps (Sec. 2.1): the same schedule as the oracle's, one transform per
+  super-step, and the run against the oracle's super-stepped run.
+* The comparison equations of motion (Sec. 3.2 and 5) in the plain FP64 form.
 """
 import math
 
@@ -151,3 +154,26 @@ def test_superstep_schedule_of_the_throughput_workload(F, inputs):
     want = O.Oracle(p, tables).supersteps()
     print("3 x 256^3 workload: %d of %d steps built by transform" % (want.sum(), p["n_steps"] + 1))
     assert np.array_equal(got, want)
+
+
+# ---- equations of motion (Sec. 3.2, 3.3, 5) ---------------------------------------------------
+@pytest.mark.parametrize("eom", [1, 2, 3, 4])
+def test_comparison_equations_of_motion_match_the_oracle(F, inputs, c1_tables, eom):
+    """The comparison forms of the kick (canonical P, special-relativistic with Newtonian
+    gravity, the simpler q form, Newtonian acceleration) in the plain FP64 form against
+    the oracle, and each differs from the method's own form."""
+    p = inputs.config("c1_32", n_part=2000, n_species=2, m_ev=[0.05, 0.2], n_grid=16, n_steps=40, precision=0,
+                      seed=151, eom=eom)
+    o = O.Oracle(p, c1_tables)
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        r.step(p["n_steps"])
+        res = [r.get(s) for s in range(2)]
+    for s in range(2):
+        g = np.arange(s * p["n_part"], (s + 1) * p["n_part"])
+        ref = o.run(g)
+        ex, eq, ew = errors(*res[s], ref, p["box"])
+        print("eom %d species %d: x %.3e L, q %.3e, w %.3e" % (eom, s, ex, eq, ew))
+        assert ex < 1e-9 and eq < 1e-9 and ew < 1e-10, (ex, eq, ew)
+    base = O.Oracle(dict(p, eom=0), c1_tables).run(np.arange(p["n_part"]))
+    assert np.max(np.abs(base["q"] - res[0][1])) > 1e-3 * np.max(np.abs(base["q"] - base["qs"]))

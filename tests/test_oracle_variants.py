@@ -9,11 +9,17 @@
   - the deposit is the transpose of the gather: sum_n grid_n F_n =
     sum_k v_k F(x_k) for any field F (checked for both orders), and conserves
     the deposited total.
+* Super-steps (Sec. 2.1): the schedule rule, the change measure in closed form,
+  and exactness for fields linear in ln a.
+* The equations of motion (eq:releq_approx, eq:releq_lag, eq:p_eq, eq:q_eq and
+  the Newtonian acceleration): the total kick under uniform fields in closed form.
 * The delta-f momentum density (quantities 4-6: w q_x, w q_y, w q_z), the
   moment whose divergence gives the (1 + delta) theta spectrum of Sec. 4: it
   is the deposit of v = w q_d, checked through the transpose identity against
   an independent sum.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -164,3 +170,50 @@ def test_supersteps_exact_for_tables_linear_in_ln_a(inputs, c1_tables):
     r1, r2 = o1.run(g), o2.run(g)
     dq = np.max(np.linalg.norm(r1["q"] - r2["q"], axis=0) / np.linalg.norm(r2["q"], axis=0))
     assert 0 < dq < 1e-3
+
+
+# ---- equations of motion (Sec. 3.2, 3.3, 5) ---------------------------------------------------
+def _quad(o, f, l0, l1, n=200):
+    from scipy import integrate
+    edges = np.linspace(l0, l1, n + 1)
+    return math.fsum(integrate.quad(lambda s: f(math.exp(s)) / (math.exp(s) * o.hubble(math.exp(s))), a, b,
+                                    epsrel=1e-13, epsabs=0)[0] for a, b in zip(edges[:-1], edges[1:]))
+
+
+@pytest.mark.parametrize("eom", [0, 1, 2, 3, 4])
+def test_eom_kicks_under_uniform_fields(inputs, c1_tables, eom):
+    """With frozen uniform fields every variant's total kick over a run is a closed form
+    in integrals over conformal time (scipy quadrature here):
+      0: -grad psi int eps0 - (q0^2 grad phi - q0 (q0.grad phi)) int 1/eps0 + q0 phi_dot int 1
+      1: -grad psi int eps0 - q0^2 grad phi int 1/eps0
+      2: -grad psi int (2 q0^2 + m^2 a^2)/eps0
+      3: -grad psi int eps0
+      4: -grad psi m int a
+    with eps0 = sqrt(q0^2 + m^2 a^2).  A dropped or swapped term changes the result
+    by far more than the quadrature error."""
+    m = 0.05
+    p = inputs.config("c1_32", n_grid=16, n_part=4096, n_steps=30, seed=21, m_ev=[m], eom=eom)
+    N = p["n_grid"]
+    gpsi, gphi, cdot = np.array([2e-6, -1e-6, 5e-7]), np.array([-3e-7, 4e-7, 1e-6]), 3e-9
+    frozen = inputs.uniform_fields(N, gpsi, gphi, cdot, 0.0)
+    o = O.Oracle(p, c1_tables)
+    g = np.arange(8)
+    ic = o.initial(g, frozen=np.zeros_like(frozen))
+    x, q = o.integrate(g, ic["x"], ic["q"], ic["q0"], 0, p["n_steps"], frozen=frozen)
+    l0, l1 = o.lna(0), o.lna(p["n_steps"])
+    for i in range(len(g)):
+        q0 = ic["q0"][:, i]
+        q02 = q0 @ q0
+        e = lambda a: math.sqrt(q02 + m * m * a * a)
+        if eom == 0:
+            dq = (-gpsi * _quad(o, e, l0, l1) - (q02 * gphi - q0 * (q0 @ gphi)) * _quad(o, lambda a: 1 / e(a), l0, l1)
+                  + q0 * cdot * _quad(o, lambda a: 1.0, l0, l1))
+        elif eom == 1:
+            dq = -gpsi * _quad(o, e, l0, l1) - q02 * gphi * _quad(o, lambda a: 1 / e(a), l0, l1)
+        elif eom == 2:
+            dq = -gpsi * _quad(o, lambda a: (2 * q02 + m * m * a * a) / e(a), l0, l1)
+        elif eom == 3:
+            dq = -gpsi * _quad(o, e, l0, l1)
+        else:
+            dq = -gpsi * m * _quad(o, lambda a: a, l0, l1)
+        assert np.linalg.norm(q[:, i] - q0 - dq) < 1e-10 * np.linalg.norm(dq), (eom, i)
