@@ -153,50 +153,80 @@ struct alignas(32) PlainRec {   // 96 bytes: three whole sectors
     uint32_t id, pad[7];
 };
 
+template <int Prec> struct RecOf { using T = SplitRec; };
+template <> struct RecOf<FDF_PREC_F64> { using T = PlainRec; };
+
+template <int Prec>
+__device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int64_t i, typename RecOf<Prec>::T& r)
+{
+    if constexpr (Prec == FDF_PREC_F64) {
+        for (int d = 0; d < 3; ++d) {
+            r.x[d] = a.xd[d * n + i];
+            r.q[d] = a.qd[d * n + i];
+            r.q0[d] = a.q0d[d * n + i];
+        }
+        r.pmag = a.pmag[i];
+        r.id = a.id[i];
+        for (int q = 0; q < 7; ++q) r.pad[q] = 0;
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            r.X[d] = a.X[d * n + i];
+            r.q0[d] = a.q0f[d * n + i];
+            r.dq[d] = a.dqf[d * n + i];
+        }
+        r.id = a.id[i];
+        r.pmag = a.pmag[i];
+        r.pad[0] = r.pad[1] = r.pad[2] = r.pad[3] = 0;
+    }
+}
+
+// Each thread takes kPackU particles per trip and issues all their offset atomics
+// before it waits for any: the keys of a warp are mostly distinct, so an atomic's
+// round trip to L2 is what a particle waits for, and kPackU of them overlap.
+constexpr int kPackU = 2;
+
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t n, const uint32_t* __restrict__ key,
                                                         uint32_t* __restrict__ offset, void* __restrict__ recs)
 {
+    using Rec = typename RecOf<Prec>::T;
     // Grid-stride loop with a warp-uniform trip count, so that every lane can take
-    // part in the warp-aggregated atomic: lanes sharing a key (the common case once
-    // the state is nearly sorted) take one atomicAdd through their leader.
+    // part in the warp-aggregated atomics: lanes sharing a key take one atomicAdd
+    // through their leader.
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += stride) {
-        const int64_t i = i0 + threadIdx.x;
-        const bool live = i < n;
-        const unsigned active = __ballot_sync(0xffffffffu, live);
-        if (!live) continue;
-        const uint32_t k = key[i];
-        const unsigned peers = __match_any_sync(active, k);
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(peers) - 1;
-        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(offset + k, (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        const int64_t j = (int64_t)base + rank;
-        if constexpr (Prec == FDF_PREC_F64) {
-            PlainRec r;
-            for (int d = 0; d < 3; ++d) {
-                r.x[d] = a.xd[d * n + i];
-                r.q[d] = a.qd[d * n + i];
-                r.q0[d] = a.q0d[d * n + i];
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += kPackU * stride) {
+        int64_t idx[kPackU];
+        uint32_t k[kPackU], base[kPackU];
+        unsigned peers[kPackU];
+        int leader[kPackU];
+        bool live[kPackU];
+        Rec r[kPackU];
+#pragma unroll
+        for (int u = 0; u < kPackU; ++u) {
+            idx[u] = i0 + u * stride + threadIdx.x;
+            live[u] = idx[u] < n;
+            k[u] = live[u] ? key[idx[u]] : 0u;
+            base[u] = 0u;
+            if (live[u]) make_rec<Prec>(a, n, idx[u], r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kPackU; ++u) {
+            const unsigned active = __ballot_sync(0xffffffffu, live[u]);
+            peers[u] = 0u;
+            leader[u] = 0;
+            if (live[u]) {
+                peers[u] = __match_any_sync(active, k[u]);
+                leader[u] = __ffs(peers[u]) - 1;
+                if (lane == leader[u]) base[u] = atomicAdd(offset + k[u], (uint32_t)__popc(peers[u]));
             }
-            r.pmag = a.pmag[i];
-            r.id = a.id[i];
-            for (int q = 0; q < 7; ++q) r.pad[q] = 0;
-            reinterpret_cast<PlainRec*>(recs)[j] = r;
-        } else {
-            SplitRec r;
-            for (int d = 0; d < 3; ++d) {
-                r.X[d] = a.X[d * n + i];
-                r.q0[d] = a.q0f[d * n + i];
-                r.dq[d] = a.dqf[d * n + i];
-            }
-            r.id = a.id[i];
-            r.pmag = a.pmag[i];
-            r.pad[0] = r.pad[1] = r.pad[2] = r.pad[3] = 0;
-            reinterpret_cast<SplitRec*>(recs)[j] = r;
+        }
+#pragma unroll
+        for (int u = 0; u < kPackU; ++u) {
+            if (!live[u]) continue;
+            const uint32_t b = __shfl_sync(peers[u], base[u], leader[u]);
+            const int64_t j = (int64_t)b + __popc(peers[u] & ((1u << lane) - 1u));
+            reinterpret_cast<Rec*>(recs)[j] = r[u];
         }
     }
 }
