@@ -15,6 +15,8 @@
 // that no FP64 instruction runs in the per-step pass.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "device_math.cuh"
 
 namespace fdf {
@@ -614,15 +616,32 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
         double x[3], q[3];
         load_state<Prec>(st, n, i, L, x, q);
         const double qm = norm3_rn(q);
-        const double eps = sqrt(qm * qm + m * m * a * a);
         double v = 1.0;
-        if (quantity == FDF_Q_W_EPS) v = dfweight(qm, st.pmag[i], T) * eps;
-        else if (quantity == FDF_Q_W) v = dfweight(qm, st.pmag[i], T);
-        else if (quantity == FDF_Q_EPS) v = eps;
-        else if (quantity >= FDF_Q_W_QX) v = dfweight(qm, st.pmag[i], T) * q[quantity - FDF_Q_W_QX];
-        // per axis: the kernel's nodes and weights (order 1: 2 nodes, order 2: 3)
+        if constexpr (Prec == FDF_PREC_F64) {
+            const double eps = sqrt(qm * qm + m * m * a * a);
+            if (quantity == FDF_Q_W_EPS) v = dfweight(qm, st.pmag[i], T) * eps;
+            else if (quantity == FDF_Q_W) v = dfweight(qm, st.pmag[i], T);
+            else if (quantity == FDF_Q_EPS) v = eps;
+            else if (quantity >= FDF_Q_W_QX) v = dfweight(qm, st.pmag[i], T) * q[quantity - FDF_Q_W_QX];
+        } else {
+            // The split form deposits in FP32 arithmetic (FP64 sums): its momenta carry
+            // FP32 rounding already.  The weight's argument p - |q| (a small difference)
+            // is formed in FP64 first.
+            const float qf = (float)qm;
+            const float ma = (float)(m * a);
+            const float eps = sqrtf(fmaf(qf, qf, ma * ma));
+            const float arg = (float)((st.pmag[i] - qm) / T);
+            const float w = -expm1f(arg) / (1.f + expf(-qf / (float)T));
+            if (quantity == FDF_Q_W_EPS) v = (double)(w * eps);
+            else if (quantity == FDF_Q_W) v = (double)w;
+            else if (quantity == FDF_Q_EPS) v = (double)eps;
+            else if (quantity >= FDF_Q_W_QX) v = (double)(w * (float)q[quantity - FDF_Q_W_QX]);
+        }
+        // per axis: the kernel's nodes and weights (order 1: 2 nodes, order 2: 3), in the
+        // form's deposit precision
+        using Wt = typename std::conditional<Prec == FDF_PREC_F64, double, float>::type;
         int idx[3][3];
-        double w[3][3];
+        Wt w[3][3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             double u;
@@ -633,7 +652,7 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
                 u = (double)__umulhi(Xd, (uint32_t)N) + (double)(Xd * (uint32_t)N) * 2.3283064365386963e-10;
             }
             const double c = order == 2 ? floor(u + 0.5) : floor(u);
-            const double e = u - c;
+            const Wt e = (Wt)(u - c);
             int ii = (int)c;
             if (ii >= N) ii -= N;
             if (ii < 0) ii += N;
@@ -641,25 +660,26 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
                 idx[d][0] = ii == 0 ? N - 1 : ii - 1;
                 idx[d][1] = ii;
                 idx[d][2] = ii + 1 == N ? 0 : ii + 1;
-                w[d][0] = 0.5 * (0.5 - e) * (0.5 - e);
-                w[d][1] = 0.75 - e * e;
-                w[d][2] = 0.5 * (0.5 + e) * (0.5 + e);
+                w[d][0] = Wt(0.5) * (Wt(0.5) - e) * (Wt(0.5) - e);
+                w[d][1] = Wt(0.75) - e * e;
+                w[d][2] = Wt(0.5) * (Wt(0.5) + e) * (Wt(0.5) + e);
             } else {
                 idx[d][0] = ii;
                 idx[d][1] = ii + 1 == N ? 0 : ii + 1;
                 idx[d][2] = ii;
-                w[d][0] = 1.0 - e;
+                w[d][0] = Wt(1) - e;
                 w[d][1] = e;
-                w[d][2] = 0.0;
+                w[d][2] = Wt(0);
             }
         }
+        const Wt vw = (Wt)v;
         const int m3 = order == 2 ? 3 : 2;
         for (int cz = 0; cz < m3; ++cz)
             for (int cy = 0; cy < m3; ++cy)
                 for (int cx = 0; cx < m3; ++cx) {
-                    const double wt = w[0][cx] * w[1][cy] * w[2][cz];
+                    const Wt wt = w[0][cx] * w[1][cy] * w[2][cz];
                     const size_t cell = ((size_t)idx[2][cz] * N + idx[1][cy]) * N + idx[0][cx];
-                    atomicAdd(grid + cell, wt * v);
+                    atomicAdd(grid + cell, (double)(wt * vw));
                 }
     }
 }
