@@ -16,20 +16,37 @@
 
 namespace fdf {
 
+// u = m 2^-53 with the 53-bit integer m = (w0 >> 5) 2^26 + (w1 >> 6): the integer is
+// formed exactly in 64 bits and converted exactly (m < 2^53), so only one FP64
+// conversion and one exact power-of-two scaling are spent (the GPU's FP64 rate is low).
+__device__ __forceinline__ uint64_t m53(uint32_t w0, uint32_t w1)
+{
+    return ((uint64_t)(w0 >> 5) << 26) | (uint64_t)(w1 >> 6);
+}
+
 __device__ __forceinline__ double u53(uint32_t w0, uint32_t w1)
 {
-    return __dmul_rn(__dadd_rn(__dmul_rn((double)(w0 >> 5), 67108864.0), (double)(w1 >> 6)),
-                     1.1102230246251565404e-16);  // 2^-53
+    return __dmul_rn(__ull2double_rn(m53(w0, w1)), 1.1102230246251565404e-16);  // 2^-53
+}
+
+// v = 2u - 1 = (m - 2^52) 2^-52, exact (|m - 2^52| <= 2^52)
+__device__ __forceinline__ double v53(uint32_t w0, uint32_t w1)
+{
+    return __dmul_rn(__ll2double_rn((long long)m53(w0, w1) - (1ll << 52)), 2.220446049250313080847e-16);  // 2^-52
 }
 
 __device__ __forceinline__ double fd_inverse(const double* __restrict__ t, const double* __restrict__ F, int n,
                                              double u)
 {
     if (u >= F[n - 1]) return t[n - 1];
+    // F and u are non-negative, so their IEEE bit patterns order like their values:
+    // the bisection compares 64-bit integers instead of FP64 values
+    const long long ub = __double_as_longlong(u);
+    const long long* Fb = reinterpret_cast<const long long*>(F);
     int lo = 0, hi = n - 1;  // F[lo] <= u < F[hi]
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (F[mid] <= u) lo = mid;
+        if (Fb[mid] <= ub) lo = mid;
         else hi = mid;
     }
     const double du = __dsub_rn(u, F[lo]);
@@ -56,9 +73,9 @@ __global__ void __launch_bounds__(256) k_sample(int64_t n, uint32_t key0, uint32
         for (uint32_t att = 0; att < 64u && !ok; ++att) {
             const uint4 a = philox4x32_10(make_uint4(g0, g1, 2u, att), key0, key1);
             const uint4 b = philox4x32_10(make_uint4(g0, g1, 3u, att), key0, key1);
-            v0 = __dadd_rn(__dmul_rn(2.0, u53(a.x, a.y)), -1.0);
-            v1 = __dadd_rn(__dmul_rn(2.0, u53(a.z, a.w)), -1.0);
-            v2 = __dadd_rn(__dmul_rn(2.0, u53(b.x, b.y)), -1.0);
+            v0 = v53(a.x, a.y);
+            v1 = v53(a.z, a.w);
+            v2 = v53(b.x, b.y);
             r2 = __dadd_rn(__dadd_rn(__dmul_rn(v0, v0), __dmul_rn(v1, v1)), __dmul_rn(v2, v2));
             ok = (r2 > 1e-300) && (r2 <= 1.0);
         }
