@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t 
                                                       double a0, double tau0, int order, int N, double L,
                                                       const Gt* __restrict__ G)
 {
+    const double tau0_6 = tau0 / 6.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double m = ms.m[i / n_part];
         const uint32_t X0 = st.X[i], X1 = st.X[n + i], X2 = st.X[2 * n + i];
@@ -283,8 +284,8 @@ __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t 
         }
         const double p = st.pmag[i];
         const double eps = sqrt(p * p + m * m * a0 * a0);
-        const double c = eps * tau0 / 6.0;
-        const double r = 1.0 - g[7] / 2.0;
+        const double c = eps * tau0_6;          // eps tau0 / 6 (tau0/6 formed once)
+        const double r = 1.0 - 0.5 * g[7];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double q = st.qs[d * n + i] * r - c * g[d];
