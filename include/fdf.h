@@ -115,7 +115,8 @@ typedef struct fdf_params {
                                   this step size (4 at d ln a = 0.17) */
     int32_t  sort_every;       /* re-bucket particles by position (gather locality): 0 = after
                                   sampling and whenever the typical displacement since the last
-                                  sort exceeds four sort tiles; k > 0 = every k steps; -1 = never */
+                                  sort exceeds sort_cells cells; k > 0 = every k steps; -1 = never
+                                  (always after sampling unless -1) */
     int32_t  steps_per_pass;   /* leapfrog steps per particle pass, 1..4: the particle state is
                                   read and written once per pass (0 = 4 for the split forms,
                                   1 for the plain FP64 form) */

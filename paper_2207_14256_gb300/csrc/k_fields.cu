@@ -12,12 +12,15 @@
 // signed mode (so the realisation does not depend on the launch), with
 // <|R_n|^2> = P_R(k)/V, P_R = 2 pi^2 A_s k^-3 (k/k_pivot)^(n_s-1).
 //
-// Three passes over the 4 x N^3 complex work arrays, each an inverse DFT
-// along one axis of tiles held in shared memory (Stockham autosort, radix 4
-// and 2, an even number of stages so the result ends where it started):
-//   z: generate the spectrum of a tile (no read) and transform along z;
+// Three passes over the 4 x N^3 complex work arrays, each an inverse DFT of
+// length N = N1 N2 along one axis (16 x 16 at N = 256): a line's N2 threads
+// each hold N1 values in registers, transform them, twiddle, exchange through
+// a padded transpose in shared memory and transform the other factor:
+//   z: form the spectrum from the stored unit Gaussian field and the per-step
+//      amplitude table, and transform along z;
 //   y: transform along y;
-//   x: transform along x and write the interleaved gather grid G[cell][8].
+//   x: transform along x and write the interleaved gather grid G[cell][8] as
+//      whole 32-byte records.
 #include <cuda_bf16.h>
 
 #include <utility>

@@ -3,14 +3,18 @@
 // Each particle's arithmetic is independent of the others (the metric is
 // computed beforehand in linear theory, Sec. 2.1), so the particle arrays may
 // be permuted freely; results are read back by particle id.  Particles are
-// ordered by key = species * B + Morton(tile), the tile being a cube of
-// ts^3 cells (B tiles per species), with a counting sort:
+// ordered by key = species * B + Morton(bucket), a bucket being a cube of
+// 2^sort_tile cells per axis (B buckets per species) around the particle's
+// predicted position halfway through the next pass, with a counting sort:
 //   keys:    key of every particle and a histogram of keys;
-//   scan:    exclusive prefix sum of the histogram (three small passes);
-//   scatter: every particle's state moves to offset[key]++ in the other half
-//            of the double-buffered state.
-// Within a tile the order is whatever the atomics produce; no result depends
-// on it.
+//   scan:    exclusive prefix sum of the histogram (recursive, any bin count);
+//   pack:    every particle's state, as one 64-byte record, goes to
+//            offset[key]++ (warp-aggregated atomics, two particles in flight
+//            per thread);
+//   unpack:  the records go back to the arrays of the other half of the
+//            double-buffered state.
+// Within a bucket the order is whatever the atomics produce; no result
+// depends on it.
 #include "device_math.cuh"
 
 namespace fdf {
