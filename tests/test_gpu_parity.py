@@ -93,6 +93,27 @@ def test_fields_match_oracle(F, inputs, c1_tables, prec, tol):
     assert all(e[2] > 0 and e[3] < tol for e in errs)
 
 
+@pytest.mark.parametrize("prec,N,tol", [(1, 8, 3e-6), (1, 16, 3e-6), (1, 64, 3e-6), (1, 128, 3e-6), (1, 256, 3e-6),
+                                        (0, 8, 1e-12), (0, 64, 1e-12), (0, 128, 1e-12), (2, 128, 1e-2)])
+def test_fields_match_oracle_at_every_grid_size(F, inputs, c1_tables, prec, N, tol):
+    """The FFT passes are compiled per grid size (each N = N1 N2 has its own register
+    split and shared-memory shape), so every size the workloads use is checked against
+    the oracle, slot by slot, at one scale factor in the matter era."""
+    p = inputs.config("c1_32", n_grid=N, box=1000.0 * N / 32, precision=prec, seed=33)
+    o = O.Oracle(p, c1_tables)
+    lna = o.lna(80)
+    with F.Run(p, c1_tables) as r:
+        g = r.build_fields(lna)
+    ref, _ = o.fields(lna, 0xFF, o.noise())
+    worst = 0.0
+    for s in range(8):
+        pair = s & ~1
+        scale = max(np.max(np.abs(ref[pair])), np.max(np.abs(ref[pair + 1])))
+        worst = max(worst, np.max(np.abs(g[s] - ref[s])) / scale)
+    print("N %d prec %d: largest slot error / pair scale %.3e" % (N, prec, worst))
+    assert worst < tol
+
+
 def test_run_c1_plain_fp64(F, inputs, c1_tables):
     """The full first workload: 32^3 particles, 32^3 grid, 100 steps, all FP64."""
     p = inputs.config("c1_32")
