@@ -313,6 +313,23 @@ __global__ void __launch_bounds__(256) k_mode_table(FieldArgs a, int M, const do
     }
 }
 
+// One entry of the amplitude table (4 values per |n|^2, 16- or 32-byte aligned) in
+// as few loads as the type allows.
+__device__ __forceinline__ void amp_entry(const float* A, int m, float& ap, float& af, float& ad)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4*>(A) + m);
+    ap = v.x;
+    af = v.y;
+    ad = v.z;
+}
+__device__ __forceinline__ void amp_entry(const double* A, int m, double& ap, double& af, double& ad)
+{
+    const double2 u = __ldg(reinterpret_cast<const double2*>(A) + 2 * m);
+    ap = u.x;
+    af = u.y;
+    ad = __ldg(A + 4 * m + 2);
+}
+
 // ---- pass z: spectrum + inverse DFT along z ---------------------------------
 // Block (x-tile, jy): TX columns along z.  Each thread reads the unit Gaussians of
 // its N1 modes once, with their amplitudes A[|n|^2] at this scale factor, then forms,
@@ -343,12 +360,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
         const int nz = sidx(z, N);
         Rv[I] = R[(size_t)z * NN + (size_t)jy * N + x0 + xo];
         T ap = T(0), af = T(0), ad = T(0);
-        if (nx != h && ny != h && nz != h) {
-            const T* am = A + 4 * (nx * nx + ny * ny + nz * nz);
-            ap = am[0];
-            af = am[1];
-            ad = am[2];
-        }
+        if (nx != h && ny != h && nz != h) amp_entry(A, nx * nx + ny * ny + nz * nz, ap, af, ad);
         As[(0 * N1 + I) * NT + threadIdx.x] = ap;
         As[(1 * N1 + I) * NT + threadIdx.x] = af;
         As[(2 * N1 + I) * NT + threadIdx.x] = ad;
