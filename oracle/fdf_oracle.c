@@ -443,7 +443,8 @@ void or_dft3d_inverse_naive(int N, const double complex* in, double complex* out
 }
 
 /* Real-space fields at ln a: slots 0-2 grad psi, 3-5 grad phi, 6 phi_dot =
- * a H dphi/dln a, 7 psi; only slots set in mask are computed.  Each slot is
+ * a H dphi/dln a, 7 psi (phi + psi if mask has OR_SLOT7_PHI_PLUS_PSI); only
+ * slots set in mask are computed.  Each slot is
  * the inverse transform of its own Hermitian spectrum; max_imag returns the
  * largest |Im| met (zero up to round-off). */
 void or_fields(const or_params* p, const or_tables* t, const double complex* R, double lna,
@@ -469,6 +470,8 @@ void or_fields(const or_params* p, const or_tables* t, const double complex* R, 
                 if (slot < 3) v = I * (kf * n[slot]) * or_interp_table(t, t->T_psi, lnk, lna) * R[c];
                 else if (slot < 6) v = I * (kf * n[slot - 3]) * or_interp_table(t, t->T_phi, lnk, lna) * R[c];
                 else if (slot == 6) v = aH * or_interp_table(t, t->dTphi_dlna, lnk, lna) * R[c];
+                else if (mask & OR_SLOT7_PHI_PLUS_PSI)
+                    v = (or_interp_table(t, t->T_psi, lnk, lna) + or_interp_table(t, t->T_phi, lnk, lna)) * R[c];
                 else v = or_interp_table(t, t->T_psi, lnk, lna) * R[c];
             }
             s[c] = v;
@@ -738,6 +741,15 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
 /*   q_{k+1/2} = q_k + kick(x_k, a_k; [a_k, a_{k+1/2}])                      */
 /*   x_{k+1}   = x_k + q_{k+1/2} int_{a_k}^{a_{k+1}} dtau / eps              */
 /*   q_{k+1}   = q_{k+1/2} + kick(x_{k+1}, a_{k+1}; [a_{k+1/2}, a_{k+1}])    */
+/*                                                                          */
+/* eom 5, the non-symplectic leapfrog on the exact eq:releq and             */
+/* eq:geodesic that Sec. 3.3 uses as a check (reading: the same three       */
+/* stages, each explicit in what it does not advance):                      */
+/*   each half kick is eq:releq with q, eps = sqrt(q^2 + m^2 a^2) and the   */
+/*   products q (q.grad phi), q phi_dot held at the kick's starting q (the  */
+/*   kick of eom 0 with that q in place of q0);                             */
+/*   the drift is eq:geodesic, x_{k+1} = x_k + (1 + phi + psi)_k q_{k+1/2}  */
+/*   int dtau / eps, with phi + psi read at x_k from the fields of a_k.     */
 /* ------------------------------------------------------------------------ */
 int or_integrate(const or_params* p, const or_tables* t, const double* frozen, const int64_t* gidx,
                  int64_t n, int k_from, int k_to, double* x, double* q, const double* q0)
@@ -753,9 +765,12 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
         or_noise(p, fs.R);
     }
     field_src_schedule(&fs);
-    const double* Fk = fields_at(&fs, (double)k_from, 0x7Fu);
+    const int exact = p->eom == 5;
+    const unsigned gmask = exact ? 0xFFu : 0x7Fu;
+    const unsigned fmask = exact ? (0xFFu | OR_SLOT7_PHI_PLUS_PSI) : 0x7Fu;
+    const double* Fk = fields_at(&fs, (double)k_from, fmask);
     for (int k = k_from; k != k_to; k += dir) {
-        const double* Fn = fields_at(&fs, (double)(k + dir), 0x7Fu);
+        const double* Fn = fields_at(&fs, (double)(k + dir), fmask);
         double lk = or_lna(p, k), lh = or_lna(p, k + 0.5 * dir), ln = or_lna(p, k + dir);
         or_quad Qopen, Qdrift, Qclose;
         quad_nodes(p, lk, lh, &Qopen);
@@ -770,14 +785,25 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
                 qi[d] = q[d * n + i];
                 q0i[d] = q0[d * n + i];
             }
-            gather(N, L, order_of(p), Fk, 0x7Fu, xi, g);
-            kick(g, q0i, m, &Qopen, p->eom, qi);
+            gather(N, L, order_of(p), Fk, gmask, xi, g);
+            const double metric = exact ? 1.0 + g[7] : 1.0;   /* (1 + phi + psi) at x_k, a_k */
+            if (exact) {
+                double qstart[3] = {qi[0], qi[1], qi[2]};
+                kick(g, qstart, m, &Qopen, 0, qi);
+            } else {
+                kick(g, q0i, m, &Qopen, p->eom, qi);
+            }
             double qq = qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2];
             double D = 0.0;
             for (int j = 0; j < OR_NGL; ++j) D += Qdrift.wdt[j] / sqrt(qq + m * m * Qdrift.a2[j]);
-            for (int d = 0; d < 3; ++d) xi[d] = wrap(xi[d] + D * qi[d], L);
-            gather(N, L, order_of(p), Fn, 0x7Fu, xi, g);
-            kick(g, q0i, m, &Qclose, p->eom, qi);
+            for (int d = 0; d < 3; ++d) xi[d] = wrap(xi[d] + metric * D * qi[d], L);
+            gather(N, L, order_of(p), Fn, gmask, xi, g);
+            if (exact) {
+                double qstart[3] = {qi[0], qi[1], qi[2]};
+                kick(g, qstart, m, &Qclose, 0, qi);
+            } else {
+                kick(g, q0i, m, &Qclose, p->eom, qi);
+            }
             for (int d = 0; d < 3; ++d) {
                 x[d * n + i] = xi[d];
                 q[d * n + i] = qi[d];

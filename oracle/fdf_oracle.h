@@ -39,8 +39,14 @@ typedef struct {
                                0 eq:releq_approx (Sec. 3.3, the method's), 1 eq:releq_lag
                                (canonical P), 2 eq:p_eq (special-relativistic, Newtonian
                                gravity), 3 eq:q_eq (Sec. 5's simpler form), 4 Newtonian
-                               acceleration -m a grad psi (Sec. 5) */
+                               acceleration -m a grad psi (Sec. 5); or
+                               5 the exact eq:releq and eq:geodesic in the non-symplectic
+                               leapfrog of Sec. 3.3 (or_integrate says how) */
 } or_params;
+
+/* or_fields mask bit: slot 7 holds phi + psi (the drift factor of eq:geodesic)
+ * instead of psi. */
+#define OR_SLOT7_PHI_PLUS_PSI 0x100u
 
 typedef struct {
     int32_t nk, na;

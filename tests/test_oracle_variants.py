@@ -13,6 +13,10 @@
   and exactness for fields linear in ln a.
 * The equations of motion (eq:releq_approx, eq:releq_lag, eq:p_eq, eq:q_eq and
   the Newtonian acceleration): the total kick under uniform fields in closed form.
+* The exact eq:releq and eq:geodesic in the non-symplectic leapfrog (eom 5, the
+  check of Sec. 3.3): convergence to scipy's ODE solution of those equations,
+  the (1 + phi + psi) drift scaling, no force on a momentum parallel to grad phi,
+  and the phi + psi slot against the spectral gradient of grad phi.
 * The delta-f momentum density (quantities 4-6: w q_x, w q_y, w q_z), the
   moment whose divergence gives the (1 + delta) theta spectrum of Sec. 4: it
   is the deposit of v = w q_d, checked through the transpose identity against
@@ -217,3 +221,112 @@ def test_eom_kicks_under_uniform_fields(inputs, c1_tables, eom):
         else:
             dq = -gpsi * m * _quad(o, lambda a: a, l0, l1)
         assert np.linalg.norm(q[:, i] - q0 - dq) < 1e-10 * np.linalg.norm(dq), (eom, i)
+
+
+# ---- the exact equations of motion in the non-symplectic leapfrog (Sec. 3.3) ---------------
+def _exact_ode_solution(o, m, x0, q0, l0, l1, gpsi, gphi, cdot, s):
+    """eq:releq and eq:geodesic under uniform fields, integrated in ln a by scipy's DOP853."""
+    from scipy.integrate import solve_ivp
+
+    def f(l, y):
+        a = math.exp(l)
+        q = y[3:]
+        e = math.sqrt(q @ q + m * m * a * a)
+        dx = q / e * (1.0 + s)
+        dq = -e * gpsi - (q @ q) / e * gphi + q * (q @ gphi) / e + q * cdot
+        return np.concatenate([dx, dq]) / (a * o.hubble(a))
+
+    sol = solve_ivp(f, (l0, l1), np.concatenate([x0, q0]), method="DOP853", rtol=1e-12, atol=1e-14)
+    assert sol.success
+    return sol.y[:3, -1], sol.y[3:, -1]
+
+
+def test_exact_eom_converges_to_the_ode_solution(inputs, c1_tables):
+    """eom 5 integrates eq:releq and eq:geodesic themselves, so under uniform fields its
+    leapfrog converges to an ODE solver's solution of those equations as the step shrinks
+    (first order in q: each half kick holds q at its start), while the method's separable
+    form (eom 0) converges to a different curve."""
+    m = 0.05
+    gpsi, gphi, cdot, s = np.array([2e-6, -1e-6, 5e-7]), np.array([-3e-7, 4e-7, 1e-6]), 3e-9, 1e-3
+    g = np.arange(4)
+    err = {}
+    for ns in (60, 240):
+        p = inputs.config("c1_32", n_grid=16, n_part=4096, n_steps=ns, seed=21, m_ev=[m], eom=5)
+        L = p["box"]
+        frozen = inputs.uniform_fields(p["n_grid"], gpsi, gphi, cdot, s)
+        o = O.Oracle(p, c1_tables)
+        ic = o.initial(g, frozen=np.zeros_like(frozen))
+        x, q = o.integrate(g, ic["x"], ic["q"], ic["q0"], 0, ns, frozen=frozen)
+        xs, qs = O.Oracle(dict(p, eom=0), c1_tables).integrate(g, ic["x"], ic["q"], ic["q0"], 0, ns, frozen=frozen)
+        ex = eq = eq_sep = 0.0
+        for i in range(len(g)):
+            xe, qe = _exact_ode_solution(o, m, ic["x"][:, i], ic["q"][:, i], o.lna(0), o.lna(ns), gpsi, gphi, cdot, s)
+            moved = np.linalg.norm((xe - ic["x"][:, i] + L / 2) % L - L / 2)
+            kicked = np.linalg.norm(qe - ic["q"][:, i])
+            ex = max(ex, np.linalg.norm((x[:, i] - xe + L / 2) % L - L / 2) / moved)
+            eq = max(eq, np.linalg.norm(q[:, i] - qe) / kicked)
+            eq_sep = max(eq_sep, np.linalg.norm(qs[:, i] - qe) / kicked)
+        err[ns] = (ex, eq, eq_sep)
+        print("exact eom, %d steps: x %.2e of the displacement, q %.2e of the kick (separable form: %.2e)"
+              % (ns, ex, eq, eq_sep))
+    assert err[240][0] < 1e-5 and err[240][1] < 3e-5
+    assert err[240][1] < err[60][1] / 3          # first order in the step
+    assert err[240][2] > 30 * err[240][1]         # eom 0 is another equation
+
+
+def test_exact_eom_invariants(inputs, c1_tables):
+    """Two exact properties of eq:releq and eq:geodesic that a sign or factor slip breaks:
+    * with no gradients and no phi_dot, q is constant and the drift is (1 + phi + psi)
+      times the drift with phi + psi = 0;
+    * with grad psi = 0 and phi_dot = 0, a momentum parallel to grad phi feels no force
+      (-(q^2/eps) grad phi + q (q.grad phi)/eps vanishes), so it never changes."""
+    # a box much larger than the distance travelled, so that no wrap hides the scaling
+    p = inputs.config("c1_32", n_grid=16, n_part=4096, n_steps=40, seed=21, m_ev=[0.05], eom=5, box=1e5)
+    L, N = p["box"], p["n_grid"]
+    o = O.Oracle(p, c1_tables)
+    g = np.arange(6)
+    ic = o.initial(g, frozen=np.zeros((8, N, N, N)))
+    x0 = np.full((3, len(g)), L / 2)
+    s = 2e-3
+    xa, qa = o.integrate(g, x0, ic["q"], ic["q0"], 0, p["n_steps"],
+                         frozen=inputs.uniform_fields(N, np.zeros(3), np.zeros(3), 0.0, s))
+    xb, qb = o.integrate(g, x0, ic["q"], ic["q0"], 0, p["n_steps"],
+                         frozen=inputs.uniform_fields(N, np.zeros(3), np.zeros(3), 0.0, 0.0))
+    assert np.array_equal(qa, ic["q"]) and np.array_equal(qb, ic["q"])
+    da, db = (xa - x0 + L / 2) % L - L / 2, (xb - x0 + L / 2) % L - L / 2
+    assert np.max(np.abs(da - (1 + s) * db)) <= 1e-12 * np.max(np.abs(da))
+    gphi = np.array([3e-6, -2e-6, 1e-6])
+    qpar = np.outer(gphi / np.linalg.norm(gphi), np.linalg.norm(ic["q"], axis=0))
+    _, qc = o.integrate(g, x0, qpar, qpar, 0, p["n_steps"],
+                        frozen=inputs.uniform_fields(N, np.zeros(3), gphi, 0.0, 0.0))
+    assert np.max(np.linalg.norm(qc - qpar, axis=0) / np.linalg.norm(qpar, axis=0)) < 1e-14
+    # the method's separable form does feel it (q0 is parallel too, so it also vanishes there):
+    # break the parallelism and the force appears
+    qtilt = qpar + 0.3 * np.roll(qpar, 1, axis=0)
+    _, qd = o.integrate(g, x0, qtilt, qtilt, 0, p["n_steps"],
+                        frozen=inputs.uniform_fields(N, np.zeros(3), gphi, 0.0, 0.0))
+    assert np.min(np.linalg.norm(qd - qtilt, axis=0) / np.linalg.norm(qtilt, axis=0)) > 1e-6
+
+
+def test_phi_plus_psi_slot_is_psi_plus_the_potential_of_grad_phi(inputs, c1_tables):
+    """The exact drift reads phi + psi from slot 7 built with OR_SLOT7_PHI_PLUS_PSI.  Its
+    difference from the plain slot 7 (psi) is phi, whose spectral gradient must equal the
+    grad phi slots 3-5, which are built from the same transfer function independently."""
+    p = inputs.config("c1_32", n_grid=16, seed=23)
+    o = O.Oracle(p, c1_tables)
+    R = o.noise()
+    lna = o.lna(60)
+    plain, _ = o.fields(lna, 0xFF, R)
+    summed, _ = o.fields(lna, 0xFF | 0x100, R)
+    assert np.array_equal(plain[:7], summed[:7])
+    phi = summed[7] - plain[7]
+    N, kf = p["n_grid"], 2 * math.pi / p["box"]
+    n = np.fft.fftfreq(N, 1.0 / N)
+    Phi = np.fft.fftn(phi)
+    for d, axis in ((0, 2), (1, 1), (2, 0)):          # layout [z][y][x]
+        shape = [1, 1, 1]
+        shape[axis] = N
+        grad = np.fft.ifftn(1j * kf * n.reshape(shape) * Phi).real
+        ref = plain[3 + d]
+        assert np.max(np.abs(grad - ref)) < 1e-10 * np.max(np.abs(ref)), d
+    assert np.max(np.abs(phi)) > 0.1 * np.max(np.abs(plain[7]))
