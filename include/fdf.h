@@ -139,7 +139,9 @@ typedef struct fdf_params {
                                   FDF_EOM_GEODESIC (0, eq:releq_approx, the method's), or, in the
                                   plain FP64 form only (FDF_ENOSYS otherwise), the comparison
                                   forms FDF_EOM_CANONICAL (eq:releq_lag), FDF_EOM_SR_NEWTON
-                                  (eq:p_eq), FDF_EOM_Q_SIMPLE (eq:q_eq), FDF_EOM_NEWTONIAN */
+                                  (eq:p_eq), FDF_EOM_Q_SIMPLE (eq:q_eq), FDF_EOM_NEWTONIAN, and
+                                  FDF_EOM_EXACT (eq:releq and eq:geodesic themselves, not
+                                  symplectic; steps_per_pass 0, 1 or 2) */
 } fdf_params;
 
 /* ---- equations of motion (fdf_params.eom) -------------------------------- */
@@ -148,6 +150,14 @@ typedef struct fdf_params {
 #define FDF_EOM_SR_NEWTON 2  /* dP/dtau = -((2 P0^2 + m^2 a^2)/eps0) grad psi (Sec. 5) */
 #define FDF_EOM_Q_SIMPLE  3  /* dq/dtau = -eps0 grad psi (Sec. 5) */
 #define FDF_EOM_NEWTONIAN 4  /* dq/dtau = -m a grad psi (Sec. 5: dq/dt = -m grad psi, dtau = dt/a) */
+/* The exact eq:releq, dq/dtau = -eps grad psi - (q^2/eps) grad phi + q (q.grad phi)/eps
+ * + q phi_dot, and eq:geodesic, dx/dtau = (q/eps)(1 + phi + psi), in the non-symplectic
+ * leapfrog Sec. 3.3 uses as a check: each half kick holds q (and eps) at its start;
+ * the drift takes 1 + phi + psi at its starting point from the fields of that step.
+ * The steps' grids then carry phi + psi in slot 7 (psi otherwise); the initial
+ * transform and fdf_build_fields still see psi there.  Frozen fields
+ * (fdf_set_fields) are used as given: slot 7 is read as phi + psi by the drift. */
+#define FDF_EOM_EXACT     5
 
 /* Input tables, host memory, copied by fdf_create.
  *  T_psi, T_phi, dTphi_dlna: [na][nk] row-major, the transfer functions of

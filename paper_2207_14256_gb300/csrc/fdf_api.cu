@@ -102,7 +102,7 @@ FF split_ff(double v)
 }
 
 struct StateLayout {
-    size_t X, q0f, dqf, xd, qd, q0d, pmag, id;
+    size_t X, q0f, dqf, xd, qd, q0d, sd, pmag, id;
 };
 
 // Steps per particle pass: the caller's choice, else 4 for the split forms (the
@@ -167,6 +167,9 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
         S.xd = take(split ? 0 : 3 * n * 8);
         S.qd = take(split ? 0 : 3 * n * 8);
         S.q0d = take(split ? 0 : 3 * n * 8);
+        // 1 + phi + psi's phi + psi at each particle, carried from a kick to the next
+        // drift (the exact equations of motion only)
+        S.sd = take(p.eom == FDF_EOM_EXACT ? n * 8 : 0);
         S.pmag = take(n * 8);
         S.id = take(n * 4);
     }
@@ -225,9 +228,13 @@ int fdf::validate_params(const fdf_params* p)
     if (p->interp_order < 0 || p->interp_order > 2) return fail(FDF_EINVAL, "interp_order must be 0, 1 or 2");
     if (!(p->superstep_tol >= 0.0) || !std::isfinite(p->superstep_tol))
         return fail(FDF_EINVAL, "superstep_tol must be finite and >= 0");
-    if (p->eom < FDF_EOM_GEODESIC || p->eom > FDF_EOM_NEWTONIAN) return fail(FDF_EINVAL, "unknown eom");
+    if (p->eom < FDF_EOM_GEODESIC || p->eom > FDF_EOM_EXACT) return fail(FDF_EINVAL, "unknown eom");
     if (p->eom != FDF_EOM_GEODESIC && p->precision != FDF_PREC_F64)
         return fail(FDF_ENOSYS, "the comparison equations of motion run in the plain FP64 form only");
+    // the exact form splits every kick in two sub-steps: an opening kick and two
+    // sub-steps per leapfrog step must fit in one pass
+    if (p->eom == FDF_EOM_EXACT && p->steps_per_pass > 2)
+        return fail(FDF_EINVAL, "steps_per_pass must be 0, 1 or 2 with FDF_EOM_EXACT");
     return FDF_OK;
 }
 
@@ -260,6 +267,7 @@ struct fdf_ctx {
     std::vector<double> tab_host;     // T_psi, T_phi, dT_phi/dln a on the host (super-step schedule)
     std::vector<int> is_super;        // super-step schedule, n_steps + 1 entries
     bool supersteps = false;
+    bool sum7 = false;                   // the steps' grids carry phi + psi in slot 7 (FDF_EOM_EXACT)
     void* Gss[2] = {nullptr, nullptr};
     int ssk[2] = {-1, -1};            // the step each super-step grid holds
     double lnk0 = 0, dlnk = 0, lnat0 = 0, dlnat = 0;
@@ -483,8 +491,8 @@ int draw_noise(fdf_ctx* c)
     return rc;
 }
 
-// The eight fields at ln a into G, on stream s.
-int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s)
+// The eight fields at ln a into G, on stream s; slot 7 is phi + psi if sum7, else psi.
+int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s, bool sum7)
 {
     if (!c->noise_ready) {
         if (s != c->sf) FDF_CUDA(cudaStreamSynchronize(c->stream), "sync");
@@ -492,7 +500,8 @@ int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s)
         if (rc0) return rc0;
         if (s != c->sf) FDF_CUDA(cudaStreamSynchronize(c->sf), "sync");
     }
-    const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
+    FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
+    a.slot7_sum = sum7 ? 1 : 0;
     const int prec = c->p.precision;
     int rc = timed_on(c, s, FDF_K_FIELDS_Z, "mode table",
                       [&] { return launch_mode_table(s, prec, a, c->tabs, c->modeA); });
@@ -588,7 +597,7 @@ void superstep_schedule(fdf_ctx* c)
 // two super-step grids as needed (a step that is itself a super-step is the copy w = 0).
 int produce_grid(fdf_ctx* c, int k, void* G)
 {
-    if (!c->supersteps) return build_fields(c, c->lna(k), G, c->sf);
+    if (!c->supersteps) return build_fields(c, c->lna(k), G, c->sf, c->sum7);
     int s = k, e = k;
     while (!c->is_super[s]) --s;
     while (!c->is_super[e]) ++e;
@@ -605,7 +614,7 @@ int produce_grid(fdf_ctx* c, int k, void* G)
         }
         const int i = slot[1 - n] == 0 ? 1 : 0;   // the grid the other end does not use
         c->ssk[i] = -1;
-        int rc = build_fields(c, c->lna(need[n]), c->Gss[i], c->sf);
+        int rc = build_fields(c, c->lna(need[n]), c->Gss[i], c->sf, c->sum7);
         if (rc) return rc;
         c->ssk[i] = need[n];
         slot[n] = i;
@@ -884,6 +893,7 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
         S2[h]->xd = (double*)(b + S.xd);
         S2[h]->qd = (double*)(b + S.qd);
         S2[h]->q0d = (double*)(b + S.q0d);
+        S2[h]->sd = p->eom == FDF_EOM_EXACT ? (double*)(b + S.sd) : nullptr;
         S2[h]->qs = (double*)(b + L.qs);
         S2[h]->pmag = (double*)(b + S.pmag);
         S2[h]->id = (uint32_t*)(b + S.id);
@@ -966,6 +976,8 @@ int sample_enqueue(fdf_ctx* c)
     if (rc) return rc;
     const void* G0 = nullptr;
     int b0 = -1;
+    if (c->st.sd) FDF_CUDA(cudaMemsetAsync(c->st.sd, 0, (size_t)c->n * 8, c->stream), "clearing phi + psi");
+    c->sum7 = false;                     // the initial transform reads psi from slot 7
     rc = ensure_grid(c, 0, 0u, &G0, &b0);
     if (rc) return rc;
     rc = acquire_grid(c, b0);
@@ -978,6 +990,12 @@ int sample_enqueue(fdf_ctx* c)
     if (rc) return rc;
     rc = release_grid(c, b0);
     if (rc) return rc;
+    if (c->p.eom == FDF_EOM_EXACT) {
+        // the steps' grids carry phi + psi in slot 7: none built so far may be reused
+        c->sum7 = true;
+        for (int i = 0; i < kMaxBuf; ++i) c->gk[i] = -1;
+        c->ssk[0] = c->ssk[1] = -1;
+    }
     c->k = 0;
     if (c->p.sort_every >= 0 && c->n > 0) {
         rc = sort_particles(c, 1);
@@ -1072,10 +1090,24 @@ int fdf_step(fdf_ctx* c, int32_t n)
             const bool last = (j == passes - 1) && (i == pass_len(j) - 1);
             // drift over the step; merged kick (closing half of this step, opening half
             // of the next) at x_{k+1} with the fields of step k+1, or only the closing half
-            fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir),
-                         last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
-            a.G[a.nsub] = grids_cur[gi++];
-            ++a.nsub;
+            if (c->p.eom == FDF_EOM_EXACT) {
+                // the halves stay apart: each holds q at its own start (eq:releq)
+                fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir), c->lna(k1),
+                             a.sub[a.nsub]);
+                a.G[a.nsub] = grids_cur[gi];
+                ++a.nsub;
+                if (!last) {
+                    fill_substep(c, false, 0, 0, true, c->lna(k1), c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
+                    a.G[a.nsub] = grids_cur[gi];
+                    ++a.nsub;
+                }
+                ++gi;
+            } else {
+                fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir),
+                             last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
+                a.G[a.nsub] = grids_cur[gi++];
+                ++a.nsub;
+            }
             c->k = k1;
             c->disp += typical_displacement(c, c->lna(k0), c->lna(k1));
         }
@@ -1219,7 +1251,7 @@ int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device)
     for (int i = 0; i < c->nbuf; ++i)
         if (c->gk[i] != c->k) buf = i;
     c->gk[buf] = -1;
-    int rc = build_fields(c, lna, c->G[buf], c->stream);
+    int rc = build_fields(c, lna, c->G[buf], c->stream, false);
     if (rc) return rc;
     double* dst = out;
     if (!out_on_device) FDF_CUDA(cudaMalloc(&dst, 8 * N3 * 8), "allocating the field copy");

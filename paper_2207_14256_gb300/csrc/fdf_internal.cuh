@@ -89,6 +89,7 @@ struct FieldArgs {
     double lnkp;                // ln k_pivot
     uint32_t key0, key1;        // Philox key (seed)
     int fixed_amp;
+    int slot7_sum;              // slot 7 holds phi + psi instead of psi
 };
 
 inline int ilog2_host(int v)
@@ -141,6 +142,7 @@ struct ParticleState {
     double* xd;         // [3][n] (plain FP64 form)
     double* qd;
     double* q0d;
+    double* sd;         // [n] phi + psi from the last kick (the exact equations of motion), or NULL
     double* qs;         // [3][n] sampled momenta
     double* pmag;       // [n]
     uint32_t* id;       // [n]

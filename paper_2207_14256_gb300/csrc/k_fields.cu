@@ -7,6 +7,7 @@
 // f_a + i f_b):
 //   P0 = d_x psi + i d_y psi     P1 = d_z psi + i d_x phi
 //   P2 = d_y phi + i d_z phi     P3 = phi_dot + i psi
+// (P3 = phi_dot + i (phi + psi) for the steps of the exact equations of motion)
 // with d_j f = sum_n i k_j T_f(k, a) R_n e^{i k.x}, phi_dot = a H dT_phi/dln a R.
 // R_n is a Hermitian Gaussian field drawn from Philox4x32-10 addressed by the
 // signed mode (so the realisation does not depend on the launch), with
@@ -376,9 +377,11 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
             sfor<N1>([&](auto I) {
                 const T kz = kf * (T)sidx(N2 * I + t, N);
                 const int o = I * NT + threadIdx.x;
-                const T apsi = (P == 2) ? T(0) : As[0 * N1 * NT + o];
+                T apsi = (P == 2) ? T(0) : As[0 * N1 * NT + o];
                 const T aphi = (P == 1 || P == 2) ? As[1 * N1 * NT + o] : T(0);
                 const T adot = (P == 3) ? As[2 * N1 * NT + o] : T(0);
+                // slot 7 (the imaginary part of grid 3) as phi + psi for the exact drift
+                if (P == 3 && a.slot7_sum) apsi += As[1 * N1 * NT + o];
                 v[I] = packed<V>(P, Rv[I], apsi, aphi, adot, kx, ky, kz);
             });
         };

@@ -472,16 +472,21 @@ void push_split(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleSta
 }
 
 // ---- the fused leapfrog pass, plain FP64 form --------------------------------
+// FDF_EOM_EXACT (eq:releq and eq:geodesic, not symplectic): each kick holds q at its
+// own start in place of q0, and each drift is scaled by 1 + phi + psi, the slot 7 of
+// the grid of the last kick read at the drift's starting point, carried in sd.
 __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ PushArgs a, double* __restrict__ xd,
-                                                       double* __restrict__ qd, const double* __restrict__ q0d)
+                                                       double* __restrict__ qd, const double* __restrict__ q0d,
+                                                       double* __restrict__ sd)
 {
     const int64_t n = a.n;
+    const bool exact = a.eom == FDF_EOM_EXACT;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(i >= a.sp_begin[0]) + (int)(i >= a.sp_begin[1]) + (int)(i >= a.sp_begin[2]);
         double x[3] = {xd[i], xd[n + i], xd[2 * n + i]};
         double q[3] = {qd[i], qd[n + i], qd[2 * n + i]};
         const double q0[3] = {q0d[i], q0d[n + i], q0d[2 * n + i]};
-        const double q02 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+        double metric = exact ? sd[i] : 0.0;      // phi + psi at the next drift's start
         bool moved = false, kicked = false;
         for (int u = 0; u < a.nsub; ++u) {
             const SubStep& st = a.sub[u];
@@ -490,6 +495,7 @@ __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ P
                 const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
                 double D = 0.0;
                 for (int j = 0; j < a.n_gl; ++j) D += c.Wd[j] / sqrt(qq + c.mud[j]);
+                if (exact) D *= 1.0 + metric;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) x[d] = wrap_f64(x[d] + D * q[d], a.L, a.invL);
                 moved = true;
@@ -497,15 +503,19 @@ __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ P
             if (st.do_kick) {
                 double g[8];
                 gather_f64_order(a.order, reinterpret_cast<const double*>(a.G[u]), a.N, a.invh, x, g);
+                // the kick's momentum: q0 (the separable forms) or q at the kick's start
+                const double qk[3] = {exact ? q[0] : q0[0], exact ? q[1] : q0[1], exact ? q[2] : q0[2]};
+                const double q02 = qk[0] * qk[0] + qk[1] * qk[1] + qk[2] * qk[2];
                 double Kpsi = 0.0, Kphi = 0.0;
                 for (int j = 0; j < a.n_kick; ++j) {
                     const double e = sqrt(q02 + c.muk[j]);
                     Kpsi += c.Wk[j] * e;
                     Kphi += c.Wk[j] / e;
                 }
-                const double qdphi = q0[0] * g[3] + q0[1] * g[4] + q0[2] * g[5];
+                const double qdphi = qk[0] * g[3] + qk[1] * g[4] + qk[2] * g[5];
                 // the terms of the kick by equation of motion (FDF_EOM_*): grad psi,
-                // grad phi, q0 (q0.grad phi) and q0 phi_dot coefficients
+                // grad phi, q0 (q0.grad phi) and q0 phi_dot coefficients (FDF_EOM_EXACT
+                // takes FDF_EOM_GEODESIC's with q in place of q0)
                 double A = Kpsi, B = q02 * Kphi, C = Kphi, Dt = c.dtau_k;
                 if (a.eom == FDF_EOM_CANONICAL) C = Dt = 0.0;
                 else if (a.eom == FDF_EOM_SR_NEWTON) { A = Kpsi + q02 * Kphi; B = C = Dt = 0.0; }
@@ -513,10 +523,12 @@ __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ P
                 else if (a.eom == FDF_EOM_NEWTONIAN) { A = c.Ka; B = C = Dt = 0.0; }
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
-                    q[d] += -g[d] * A - g[3 + d] * B + q0[d] * (qdphi * C) + q0[d] * (g[6] * Dt);
+                    q[d] += -g[d] * A - g[3 + d] * B + qk[d] * (qdphi * C) + qk[d] * (g[6] * Dt);
+                if (exact) metric = g[7];
                 kicked = true;
             }
         }
+        if (exact && kicked) sd[i] = metric;
         if (moved) {
             xd[i] = x[0];
             xd[n + i] = x[1];
@@ -716,7 +728,7 @@ cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, 
 {
     if (a.n <= 0) return cudaSuccess;
     const unsigned b = grid_for(a.n);
-    if (precision == FDF_PREC_F64) k_push_f64<<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d);
+    if (precision == FDF_PREC_F64) k_push_f64<<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d, st.sd);
     else if (precision == FDF_PREC_F32) {
         if (a.uniform_species) push_split<float, true>(s, b, a, st);
         else push_split<float, false>(s, b, a, st);

@@ -152,10 +152,11 @@ struct alignas(64) SplitRec {   // 64 bytes: a scattered record covers two whole
     double pmag;
     uint32_t pad[4];
 };
-struct alignas(32) PlainRec {   // 96 bytes: three whole sectors
-    double x[3], q[3], q0[3], pmag;
-    uint32_t id, pad[7];
+struct alignas(32) PlainRec {   // 128 bytes: four whole sectors
+    double x[3], q[3], q0[3], pmag, s;   // s: phi + psi of the exact equations of motion
+    uint32_t id, pad[5];
 };
+static_assert(sizeof(PlainRec) == 128, "PlainRec is four sectors");
 
 template <int Prec> struct RecOf { using T = SplitRec; };
 template <> struct RecOf<FDF_PREC_F64> { using T = PlainRec; };
@@ -170,8 +171,9 @@ __device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int6
             r.q0[d] = a.q0d[d * n + i];
         }
         r.pmag = a.pmag[i];
+        r.s = a.sd ? a.sd[i] : 0.0;
         r.id = a.id[i];
-        for (int q = 0; q < 7; ++q) r.pad[q] = 0;
+        for (int q = 0; q < 5; ++q) r.pad[q] = 0;
     } else {
         for (int d = 0; d < 3; ++d) {
             r.X[d] = a.X[d * n + i];
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64
                 b.q0d[d * n + j] = r.q0[d];
             }
             b.pmag[j] = r.pmag;
+            if (b.sd) b.sd[j] = r.s;
             b.id[j] = r.id;
         } else {
             const SplitRec r = reinterpret_cast<const SplitRec*>(recs)[j];

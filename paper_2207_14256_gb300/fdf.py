@@ -19,6 +19,7 @@ FDF_PREC_F64, FDF_PREC_F32, FDF_PREC_BF16 = 0, 1, 2
 FDF_FLAG_FIXED_AMPLITUDE = 1
 FDF_Q_W_EPS, FDF_Q_W, FDF_Q_EPS, FDF_Q_COUNT, FDF_Q_W_QX, FDF_Q_W_QY, FDF_Q_W_QZ = 0, 1, 2, 3, 4, 5, 6
 FDF_EOM_GEODESIC, FDF_EOM_CANONICAL, FDF_EOM_SR_NEWTON, FDF_EOM_Q_SIMPLE, FDF_EOM_NEWTONIAN = 0, 1, 2, 3, 4
+FDF_EOM_EXACT = 5
 FDF_K_PUSH, FDF_K_FIELDS_Z, FDF_K_FIELDS_Y, FDF_K_FIELDS_X, FDF_K_OTHER, FDF_K_SORT = 0, 1, 2, 3, 4, 5
 KERNEL_CLASSES = {"push": 0, "fields_z": 1, "fields_y": 2, "fields_x": 3, "other": 4, "sort": 5}
 

@@ -108,7 +108,8 @@ def test_host_only_calls(fdf, inputs):
     with pytest.raises(fdf.FdfError):
         fdf.fdf_footprint(bad)
     for knob in (dict(interp_order=3), dict(sort_tile=4), dict(sort_cells=-1), dict(steps_per_pass=5),
-                 dict(superstep_tol=-0.1), dict(superstep_tol=float("nan")), dict(eom=5)):
+                 dict(superstep_tol=-0.1), dict(superstep_tol=float("nan")), dict(eom=6), dict(eom=-1),
+                 dict(precision=0, eom=5, steps_per_pass=3)):
         with pytest.raises(fdf.FdfError) as e:
             fdf.fdf_footprint(fdf.make_params(inputs.config("c1_32", **knob)))
         assert e.value.code == fdf.FDF_EINVAL, knob
@@ -117,6 +118,15 @@ def test_host_only_calls(fdf, inputs):
         fdf.fdf_footprint(fdf.make_params(inputs.config("c1_32", precision=1, eom=3)))
     assert e.value.code == fdf.FDF_ENOSYS
     assert fdf.fdf_footprint(fdf.make_params(inputs.config("c1_32", precision=0, eom=3))) > 0
+    with pytest.raises(fdf.FdfError) as e:
+        fdf.fdf_footprint(fdf.make_params(inputs.config("c1_32", precision=1, eom=fdf.FDF_EOM_EXACT)))
+    assert e.value.code == fdf.FDF_ENOSYS
+    # the exact form carries phi + psi per particle (both halves of the sort's double buffer)
+    p = inputs.config("c1_32", precision=0)
+    extra = fdf.fdf_footprint(fdf.make_params(dict(p, eom=fdf.FDF_EOM_EXACT))) - fdf.fdf_footprint(
+        fdf.make_params(p))
+    n = p["n_part"] * p["n_species"]
+    assert abs(extra - 2 * n * 8) <= 4096, extra
 
 
 def test_create_rejects_bad_tables_before_touching_the_device(fdf, inputs, c1_tables):

@@ -13,6 +13,8 @@
 * Super-steps (Sec. 2.1): the same schedule as the oracle's, one transform per
   super-step, and the run against the oracle's super-stepped run.
 * The comparison equations of motion (Sec. 3.2 and 5) in the plain FP64 form.
+* The exact eq:releq and eq:geodesic in the non-symplectic leapfrog (Sec. 3.3) in
+  the plain FP64 form.
 """
 import math
 
@@ -177,3 +179,31 @@ def test_comparison_equations_of_motion_match_the_oracle(F, inputs, c1_tables, e
         assert ex < 1e-9 and eq < 1e-9 and ew < 1e-10, (ex, eq, ew)
     base = O.Oracle(dict(p, eom=0), c1_tables).run(np.arange(p["n_part"]))
     assert np.max(np.abs(base["q"] - res[0][1])) > 1e-3 * np.max(np.abs(base["q"] - base["qs"]))
+
+
+# ---- the exact equations of motion, non-symplectic (Sec. 3.3) ----------------------------------
+@pytest.mark.parametrize("spp,order,ss", [(1, 1, 0.0), (2, 2, 0.0), (2, 1, 0.01)])
+def test_exact_equations_of_motion_match_the_oracle(F, inputs, c1_tables, spp, order, ss):
+    """FDF_EOM_EXACT (eq:releq and eq:geodesic in the non-symplectic leapfrog) in the
+    plain FP64 form against the oracle: two species, one and two steps per pass, CIC and
+    TSC, with super-steps (the phi + psi grids are interpolated too), the run split in
+    two calls; and it differs from the method's separable form."""
+    p = inputs.config("c1_32", n_part=3001, n_species=2, m_ev=[0.05, 0.2], n_grid=16, n_steps=40, precision=0,
+                      seed=161, eom=F.FDF_EOM_EXACT, steps_per_pass=spp, interp_order=order, superstep_tol=ss)
+    o = O.Oracle(p, c1_tables)
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        r.step(17)
+        r.step(p["n_steps"] - 17)
+        res = [r.get(s) for s in range(2)]
+    for s in range(2):
+        g = np.arange(s * p["n_part"], (s + 1) * p["n_part"])
+        ref = o.run(g)
+        ex, eq, ew = errors(*res[s], ref, p["box"])
+        print("exact eom, %d steps per pass, order %d, super-steps %g, species %d: x %.3e L, q %.3e, w %.3e"
+              % (spp, order, ss, s, ex, eq, ew))
+        assert ex < 1e-9 and eq < 1e-9 and ew < 1e-10, (ex, eq, ew)
+    base = O.Oracle(dict(p, eom=0), c1_tables).run(np.arange(p["n_part"]))
+    d = np.max(np.linalg.norm(base["q"] - res[0][1], axis=0) / np.linalg.norm(base["q"], axis=0))
+    print("exact against the separable form: largest |dq| / |q| %.3e" % d)
+    assert d > 1e-9
