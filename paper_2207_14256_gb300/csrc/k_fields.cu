@@ -373,23 +373,26 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
         // one branch per packed grid, so that each reads only the amplitudes it uses
         // (psi; psi and phi; phi; phi_dot and psi) from shared memory
         V v[N1];
-        auto form = [&](auto P) {
+        // Q = 4 is grid 3 with slot 7 = phi + psi (the exact drift's factor)
+        auto form = [&](auto Q) {
+            constexpr int P = Q < 4 ? (int)Q : 3;
             sfor<N1>([&](auto I) {
                 const T kz = kf * (T)sidx(N2 * I + t, N);
                 const int o = I * NT + threadIdx.x;
-                T apsi = (P == 2) ? T(0) : As[0 * N1 * NT + o];
-                const T aphi = (P == 1 || P == 2) ? As[1 * N1 * NT + o] : T(0);
+                const T apsi = (P == 2) ? T(0) : As[0 * N1 * NT + o];
+                const T aphi = (P == 1 || P == 2 || Q == 4) ? As[1 * N1 * NT + o] : T(0);
                 const T adot = (P == 3) ? As[2 * N1 * NT + o] : T(0);
-                // slot 7 (the imaginary part of grid 3) as phi + psi for the exact drift
-                if (P == 3 && a.slot7_sum) apsi += As[1 * N1 * NT + o];
-                v[I] = packed<V>(P, Rv[I], apsi, aphi, adot, kx, ky, kz);
+                v[I] = packed<V>(P, Rv[I], Q == 4 ? apsi + aphi : apsi, aphi, adot, kx, ky, kz);
             });
         };
         switch (p) {
             case 0: form(Idx<0>{}); break;
             case 1: form(Idx<1>{}); break;
             case 2: form(Idx<2>{}); break;
-            default: form(Idx<3>{}); break;
+            default:
+                if (a.slot7_sum) form(Idx<4>{});
+                else form(Idx<3>{});
+                break;
         }
         line_first<V, N>(v, t, s_tw, tr + xo * S::TSZ);
         __syncthreads();
@@ -426,11 +429,16 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fields_y(FieldArgs a, con
 }
 
 // ---- pass x: inverse DFT along x, interleave into G[cell][8] ----------------
-// Block: TL consecutive x-lines (line index = jz * N + jy).  Grids 0..2 are parked
-// in shared memory as they finish; grid 3's results are written together with them,
-// so every cell's 8-slot record goes out in one piece.
+// Block: TL consecutive x-lines (line index = jz * N + jy).  FP64 records go out in
+// two halves: grid 0 is parked in shared memory and written with grid 1, grid 2
+// with grid 3 (one parked grid instead of three doubles the resident blocks).  FP32
+// and BF16 records go out in one piece: grids 0..2 are parked and written with grid 3.
 template <typename Gt, typename V> struct GRec;
+// FP64 records (64 bytes) are written in two halves (grids 0-1, then grids 2-3), each
+// two whole 32-byte sectors; FP32 and BF16 records in one piece, which measured faster
+// for them (FP32 halves: 232 -> 310 us per x pass at 256^3).
 template <> struct GRec<float, float2> {
+    static constexpr bool kHalves = false;
     __device__ static void put(float* G, size_t cell, float2 a, float2 b, float2 c, float2 d)
     {
         float4* g = reinterpret_cast<float4*>(G) + 2 * cell;
@@ -439,16 +447,16 @@ template <> struct GRec<float, float2> {
     }
 };
 template <> struct GRec<double, double2> {
-    __device__ static void put(double* G, size_t cell, double2 a, double2 b, double2 c, double2 d)
+    static constexpr bool kHalves = true;
+    __device__ static void put_half(double* G, size_t cell, int h, double2 a, double2 b)
     {
-        double2* g = reinterpret_cast<double2*>(G) + 4 * cell;
+        double2* g = reinterpret_cast<double2*>(G) + 4 * cell + 2 * h;
         g[0] = a;
         g[1] = b;
-        g[2] = c;
-        g[3] = d;
     }
 };
 template <> struct GRec<__nv_bfloat16, float2> {
+    static constexpr bool kHalves = false;
     __device__ static void put(__nv_bfloat16* G, size_t cell, float2 a, float2 b, float2 c, float2 d)
     {
         const __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y), h1 = __floats2bfloat162_rn(b.x, b.y);
@@ -467,11 +475,12 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_X) k_fields_x(FieldArgs a, c
                                                                   const V* __restrict__ W1, Gt* __restrict__ G)
 {
     using S = Shape<N>;
+    using Rec = GRec<Gt, V>;
     constexpr int TL = S::TL, N1 = S::N1, N2 = S::N2, T = S::T, LS = N + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* tr = s_tw + S::TWS;          // TL * TSX
-    V* park = tr + TL * S::TSX;     // 3 * TL * LS: grids 0..2
+    V* park = tr + TL * S::TSX;     // TL * LS per parked grid (1 for halves, else 3)
     load_line_twiddles<V, N>(s_tw, tw);
     const int t = threadIdx.x % T, lo = threadIdx.x / T;
     const size_t N3 = (size_t)N * N * N;
@@ -490,16 +499,27 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_X) k_fields_x(FieldArgs a, c
         __syncthreads();
         line_first<V, N>(v, t, s_tw, tr + lo * S::TSX);
         __syncthreads();
-        if (p < 3) {
-            V* pk = park + (p * TL + lo) * LS;
-            line_second<V, N>(t, tr + lo * S::TSX, [&](int x, V val) { pk[x] = val; });
+        if constexpr (Rec::kHalves) {
+            // each thread parks and reads back only its own x values: no barrier needed
+            V* pk = park + lo * LS;
+            if ((p & 1) == 0) {
+                line_second<V, N>(t, tr + lo * S::TSX, [&](int x, V val) { pk[x] = val; });
+            } else {
+                const int h = p >> 1;
+                line_second<V, N>(t, tr + lo * S::TSX,
+                                  [&](int x, V val) { Rec::put_half(G, line * N + x, h, pk[x], val); });
+            }
         } else {
-            const V* p0 = park + lo * LS;
-            const V* p1 = park + (TL + lo) * LS;
-            const V* p2 = park + (2 * TL + lo) * LS;
-            line_second<V, N>(t, tr + lo * S::TSX, [&](int x, V val) {
-                GRec<Gt, V>::put(G, line * N + x, p0[x], p1[x], p2[x], val);
-            });
+            if (p < 3) {
+                V* pk = park + (p * TL + lo) * LS;
+                line_second<V, N>(t, tr + lo * S::TSX, [&](int x, V val) { pk[x] = val; });
+            } else {
+                const V* p0 = park + lo * LS;
+                const V* p1 = park + (TL + lo) * LS;
+                const V* p2 = park + (2 * TL + lo) * LS;
+                line_second<V, N>(t, tr + lo * S::TSX,
+                                  [&](int x, V val) { Rec::put(G, line * N + x, p0[x], p1[x], p2[x], val); });
+            }
         }
     }
 }
@@ -562,7 +582,8 @@ template <typename V, typename Gt, int N>
 cudaError_t run_x(cudaStream_t s, const FieldArgs& a, const void* tw, const void* W1, void* G)
 {
     using S = Shape<N>;
-    const size_t sm = (size_t)(S::TWS + S::TL * S::TSX + 3 * S::TL * (N + 1)) * sizeof(V);
+    const int parked = GRec<Gt, V>::kHalves ? 1 : 3;
+    const size_t sm = (size_t)(S::TWS + S::TL * S::TSX + parked * S::TL * (N + 1)) * sizeof(V);
     cudaError_t e = set_smem(k_fields_x<V, Gt, N>, sm);
     if (e != cudaSuccess) return e;
     k_fields_x<V, Gt, N><<<(unsigned)((size_t)N * N / S::TL), S::THREADS_X, sm, s>>>(a, (const V*)tw, (const V*)W1,
