@@ -205,6 +205,23 @@ FDF_API int fdf_sample(fdf_ctx* c);
  * FDF_ESTATE before fdf_sample. */
 FDF_API int fdf_step(fdf_ctx* c, int32_t n);
 
+/* fdf_sample(c) followed by fdf_step(c, n), 0 <= n <= n_steps, replayed as one
+ * CUDA graph.  The paper has no counterpart: this is the launch form of a run
+ * (Sec. 2.1's particles are independent once the metric is known, so a run's
+ * launches and their order are fixed by fdf_params and n alone).  The first call
+ * for a given n records every launch of the run (field builds on the context's
+ * second stream, particle passes, sorts) into a graph held by the context; each
+ * later call with the same n replays it with one launch, without re-issuing the
+ * kernels from the host, and leaves the context in the state the sequential
+ * calls would (step n, the same buffers; the results are bitwise the same).
+ * A call with another n records anew.  Queued on the context's stream (a context
+ * on the legacy default stream, which cannot be recorded, runs its graph on a
+ * private blocking stream that the legacy stream orders); returns
+ * after the run, like fdf_sample, so that the sampler's failure is reported
+ * (FDF_EINVAL).  FDF_ESTATE while fdf_timing is on (per-kernel events are not
+ * recorded inside a graph) or with fdf_set_fields in force. */
+FDF_API int fdf_run_graph(fdf_ctx* c, int32_t n);
+
 /* Weighted CIC density estimate of eq:empirical_rho at the current scale
  * factor: out[n] = sum_k v_k W(x_n - x_k) over the grid nodes n, with v_k
  * chosen by quantity (FDF_Q_*), over one species (0..n_species-1) or all (-1);

@@ -314,6 +314,20 @@ struct fdf_ctx {
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    // the recorded run of fdf_run_graph, and the host state it leaves behind
+    struct RunGraph {
+        int n = -1;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t fork = nullptr;
+        cudaStream_t own = nullptr;      // records and replays a run queued on the legacy stream
+        int gk[kMaxBuf];
+        int ssk[2];
+        bool sum7 = false;
+        int k = 0;
+        double disp = 0;
+        ParticleState st{}, st_alt{};
+        int64_t launches = 0, sorts = 0;
+    } graph;
 
     double hubble(double a) const
     {
@@ -1134,6 +1148,111 @@ int fdf_step(fdf_ctx* c, int32_t n)
     return join_fields(c);
 }
 
+int fdf_run_graph(fdf_ctx* c, int32_t n)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (n < 0 || n > c->p.n_steps) return fail(FDF_EINVAL, "n must be in [0, n_steps]");
+    if (c->timing) return fail(FDF_ESTATE, "fdf_run_graph with fdf_timing on");
+    if (c->frozen) return fail(FDF_ESTATE, "fdf_run_graph with frozen fields");
+    auto& g = c->graph;
+    if (!g.fork) FDF_CUDA(cudaEventCreateWithFlags(&g.fork, cudaEventDisableTiming), "creating an event");
+    // The legacy default stream cannot be captured: a context on it records and
+    // replays its run on a private blocking stream, which the legacy stream orders
+    // with everything else.
+    if (!c->stream && !g.own) FDF_CUDA(cudaStreamCreate(&g.own), "creating the run's stream");
+    struct StreamSwap {
+        fdf_ctx* c;
+        cudaStream_t saved;
+        ~StreamSwap() { c->stream = saved; }
+    } swap_back{c, c->stream};
+    if (!c->stream) c->stream = g.own;
+    if (!g.exec || g.n != n) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            g.n = -1;
+        }
+        // The recorded run depends on nothing outside itself: let everything queued
+        // finish, and forget the release events recorded before the capture.
+        if (!swap_back.saved) FDF_CUDA(cudaStreamSynchronize(nullptr), "fdf_run_graph");
+        FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_run_graph");
+        FDF_CUDA(cudaStreamSynchronize(c->sf), "fdf_run_graph");
+        for (int b = 0; b < kMaxBuf; ++b) c->has_release[b] = false;
+        const int64_t l0 = c->launches, s0 = c->sorts;
+        FDF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "beginning the capture");
+        // the fields stream joins the capture through an event of the main stream
+        cudaError_t e = cudaEventRecord(g.fork, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->sf, g.fork, 0);
+        int rc = e == cudaSuccess ? sample_enqueue(c) : cuda_fail(e, "forking the fields stream");
+        if (rc == FDF_OK && n > 0) rc = fdf_step(c, n);
+        if (rc == FDF_OK) rc = join_fields(c);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(c->stream, &graph);
+        const int64_t captured = c->launches - l0, sorted = c->sorts - s0;
+        c->launches = l0;
+        c->sorts = s0;
+        if (rc == FDF_OK && e != cudaSuccess) rc = cuda_fail(e, "ending the capture");
+        if (rc == FDF_OK) {
+            e = cudaGraphInstantiate(&g.exec, graph, 0);
+            if (e != cudaSuccess) {
+                g.exec = nullptr;
+                rc = cuda_fail(e, "instantiating the run's graph");
+            }
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != FDF_OK) {
+            // the host state describes a run that never executed
+            c->sampled = c->stepped = false;
+            for (int b = 0; b < kMaxBuf; ++b) {
+                c->gk[b] = -1;
+                c->has_release[b] = false;
+            }
+            c->ssk[0] = c->ssk[1] = -1;
+            return rc;
+        }
+        // the host state the run leaves behind, restored after every replay
+        g.n = n;
+        std::memcpy(g.gk, c->gk, sizeof(g.gk));
+        std::memcpy(g.ssk, c->ssk, sizeof(g.ssk));
+        g.sum7 = c->sum7;
+        g.k = c->k;
+        g.disp = c->disp;
+        g.st = c->st;
+        g.st_alt = c->st_alt;
+        g.launches = captured;
+        g.sorts = sorted;
+    }
+    FDF_CUDA(cudaGraphLaunch(g.exec, c->stream), "launching the run's graph");
+    // later work on the fields stream follows the run, and the grids the run left in
+    // its buffers count as built once it ends (the events recorded inside the graph
+    // cannot be waited on from outside it)
+    FDF_CUDA(cudaEventRecord(g.fork, c->stream), "recording the run's end");
+    FDF_CUDA(cudaStreamWaitEvent(c->sf, g.fork, 0), "ordering the fields stream");
+    for (int b = 0; b < c->nbuf; ++b) FDF_CUDA(cudaEventRecord(c->built[b], c->stream), "recording the run's grids");
+    std::memcpy(c->gk, g.gk, sizeof(g.gk));
+    std::memcpy(c->ssk, g.ssk, sizeof(g.ssk));
+    for (int b = 0; b < kMaxBuf; ++b) c->has_release[b] = false;
+    c->sum7 = g.sum7;
+    c->k = g.k;
+    c->disp = g.disp;
+    c->st = g.st;
+    c->st_alt = g.st_alt;
+    c->launches += g.launches;
+    c->sorts += g.sorts;
+    c->noise_ready = true;
+    c->sampled = true;
+    c->stepped = n > 0;
+    // the sampler's failure flag, as fdf_sample reads it
+    int flag = 0;
+    FDF_CUDA(cudaMemcpyAsync(&flag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "reading flags");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_run_graph");
+    if (flag) {
+        c->sampled = false;
+        return fail(FDF_EINVAL, "a direction could not be drawn in 64 attempts");
+    }
+    return FDF_OK;
+}
+
 int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_t out_on_device)
 {
     if (!c) return fail(FDF_EINVAL, "ctx is NULL");
@@ -1387,6 +1506,9 @@ void fdf_destroy(fdf_ctx* c)
         if (c->released[i]) cudaEventDestroy(c->released[i]);
     }
     if (c->joined) cudaEventDestroy(c->joined);
+    if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+    if (c->graph.fork) cudaEventDestroy(c->graph.fork);
+    if (c->graph.own) cudaStreamDestroy(c->graph.own);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->Gfrozen) cudaFree(c->Gfrozen);
     if (c->own_block && c->block) cudaFree(c->block);

@@ -112,6 +112,7 @@ def lib():
             "fdf_create": (C.c_int, [P, T, _V, _V, C.c_size_t, C.POINTER(_V)]),
             "fdf_sample": (C.c_int, [_V]),
             "fdf_step": (C.c_int, [_V, C.c_int32]),
+            "fdf_run_graph": (C.c_int, [_V, C.c_int32]),
             "fdf_deposit": (C.c_int, [_V, C.c_int32, C.c_int32, _V, C.c_int32]),
             "fdf_deposit_subset": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, _V, C.c_int32]),
             "fdf_get": (C.c_int, [_V, C.c_int32, _V, _V, _V, C.c_int32]),
@@ -246,6 +247,11 @@ def fdf_sample(ctx):
 
 def fdf_step(ctx, n):
     _check(lib().fdf_step(ctx, int(n)), "fdf_step")
+
+
+def fdf_run_graph(ctx, n):
+    """fdf_sample + fdf_step(n) as one CUDA graph, recorded on the first call for n."""
+    _check(lib().fdf_run_graph(ctx, int(n)), "fdf_run_graph")
 
 
 def fdf_deposit(ctx, species, quantity, out):
@@ -449,6 +455,9 @@ class Run:
 
     def step(self, n):
         fdf_step(self.ctx, n)
+
+    def run_graph(self, n):
+        fdf_run_graph(self.ctx, n)
 
     def get(self, species=0):
         n = self.n_part
