@@ -222,6 +222,18 @@ FDF_API int fdf_step(fdf_ctx* c, int32_t n);
  * recorded inside a graph) or with fdf_set_fields in force. */
 FDF_API int fdf_run_graph(fdf_ctx* c, int32_t n);
 
+/* The four terms of the exact acceleration eq:releq at the current step, as
+ * Fig. 2 of the paper plots them: with the potentials of the current scale factor
+ * a read at each particle's position (the kernel of order interp_order) and its
+ * momentum q, eps = sqrt(q^2 + m^2 a^2),
+ *   T1 = -eps grad psi,  T2 = -(q^2/eps) grad phi,  T3 = q (q.grad phi)/eps,
+ *   T4 = q phi_dot;
+ * rms[i] = sqrt(mean over the particles of |T_{i+1}|^2), i = 0..3, and rms[4] the
+ * same for T1 + T2 + T3 + T4.  species: 0..n_species-1, or -1 for all.  rms: 5
+ * host doubles.  Sums in FP64 on the device; synchronises the stream.  FDF_ESTATE
+ * before fdf_sample; all zero for an empty species. */
+FDF_API int fdf_accel_terms(fdf_ctx* c, int32_t species, double* rms);
+
 /* Weighted CIC density estimate of eq:empirical_rho at the current scale
  * factor: out[n] = sum_k v_k W(x_n - x_k) over the grid nodes n, with v_k
  * chosen by quantity (FDF_Q_*), over one species (0..n_species-1) or all (-1);

@@ -99,6 +99,8 @@ def lib():
         L.or_integrate.argtypes = [C.POINTER(OrParams), C.POINTER(OrTables), _D, _I64, C.c_int64, C.c_int,
                                    C.c_int, _D, _D, _D]
         L.or_weights.argtypes = [C.POINTER(OrParams), C.c_int64, _D, _D, _D]
+        L.or_accel_terms.argtypes = [C.POINTER(OrParams), C.POINTER(OrTables), _D, _I64, C.c_int64, C.c_int,
+                                     _D, _D, _D]
         L.or_deposit.argtypes = [C.POINTER(OrParams), _I64, C.c_int64, _D, _D, _D, C.c_double, C.c_int, _D]
         L.or_lna.argtypes = [C.POINTER(OrParams), C.c_double]
         L.or_lna.restype = C.c_double
@@ -249,6 +251,23 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("oracle integration failed")
         return x.reshape(3, n), q.reshape(3, n)
+
+    def accel_terms(self, gidx, x, q, k, frozen=None):
+        """RMS over the particles of the four terms of eq:releq (-eps grad psi,
+        -(q^2/eps) grad phi, q (q.grad phi)/eps, q phi_dot) and of their sum, with the
+        fields of step k (Fig. 2)."""
+        g = np.ascontiguousarray(gidx, dtype=np.int64)
+        n = len(g)
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(3 * n)
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(3 * n)
+        fr = None if frozen is None else np.ascontiguousarray(frozen, dtype=np.float64).ravel()
+        out = np.zeros(5)
+        rc = lib().or_accel_terms(C.byref(self._P), C.byref(self._T), None if fr is None else _p(fr, C.c_double),
+                                  _p(g, C.c_int64), n, int(k), _p(x, C.c_double), _p(q, C.c_double),
+                                  _p(out, C.c_double))
+        if rc != 0:
+            raise RuntimeError("oracle acceleration terms failed")
+        return out
 
     def weights(self, q, pmag):
         n = len(pmag)

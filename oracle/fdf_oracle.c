@@ -819,6 +819,54 @@ int or_integrate(const or_params* p, const or_tables* t, const double* frozen, c
 }
 
 /* ------------------------------------------------------------------------ */
+/* The four terms of eq:releq (Sec. 3.2), whose root mean square over the     */
+/* particles Fig. 2 plots from z = 1e9 to 0:                                 */
+/*   T1 = -eps grad psi,  T2 = -(q^2/eps) grad phi,  T3 = q (q.grad phi)/eps, */
+/*   T4 = q phi_dot,      eps = sqrt(q^2 + m^2 a^2),                         */
+/* at each particle's x and q with the fields of step k.  out[i] = sqrt of   */
+/* the mean of |T_{i+1}|^2 over the n particles; out[4] the same for the     */
+/* sum T1 + T2 + T3 + T4 (the whole acceleration).                            */
+/* ------------------------------------------------------------------------ */
+int or_accel_terms(const or_params* p, const or_tables* t, const double* frozen, const int64_t* gidx, int64_t n,
+                   int k, const double* x, const double* q, double* out)
+{
+    const int N = p->n_grid;
+    const size_t N3 = (size_t)N * N * N;
+    field_src fs = {p, t, frozen, NULL, NULL};
+    if (!frozen) {
+        fs.R = (double complex*)malloc(sizeof(double complex) * N3);
+        or_noise(p, fs.R);
+    }
+    field_src_schedule(&fs);
+    const double* F = fields_at(&fs, (double)k, 0x7Fu);
+    const double a = exp(or_lna(p, k));
+    double sum[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i) {
+        double xi[3], qi[3], g[8];
+        for (int d = 0; d < 3; ++d) {
+            xi[d] = x[d * n + i];
+            qi[d] = q[d * n + i];
+        }
+        gather(N, p->box, order_of(p), F, 0x7Fu, xi, g);
+        const double m = mass_of(p, gidx[i]);
+        const double qq = qi[0] * qi[0] + qi[1] * qi[1] + qi[2] * qi[2];
+        const double eps = sqrt(qq + m * m * a * a);
+        const double qdphi = qi[0] * g[3] + qi[1] * g[4] + qi[2] * g[5];
+        for (int d = 0; d < 3; ++d) {
+            const double T[4] = {-eps * g[d], -(qq / eps) * g[3 + d], qi[d] * qdphi / eps, qi[d] * g[6]};
+            for (int j = 0; j < 4; ++j) sum[j] += T[j] * T[j];
+            const double tot = T[0] + T[1] + T[2] + T[3];
+            sum[4] += tot * tot;
+        }
+    }
+    for (int j = 0; j < 5; ++j) out[j] = n > 0 ? sqrt(sum[j] / (double)n) : 0.0;
+    fields_done(&fs, F);
+    free(fs.R);
+    free(fs.is_super);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* delta-f weight (Sec. 2.2): w = 1 - fbar(|q|)/fbar(p), written as          */
 /*   w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)),                            */
 /* which is the same quantity without cancellation or overflow.              */

@@ -1342,6 +1342,40 @@ int fdf_deposit(fdf_ctx* c, int32_t species, int32_t quantity, double* out, int3
     return fdf_deposit_subset(c, species, quantity, -1, out, out_on_device);
 }
 
+int fdf_accel_terms(fdf_ctx* c, int32_t species, double* rms)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!rms) return fail(FDF_EINVAL, "rms is NULL");
+    if (!c->sampled) return fail(FDF_ESTATE, "fdf_accel_terms before fdf_sample");
+    if (species < -1 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
+    for (int j = 0; j < 5; ++j) rms[j] = 0.0;
+    const int64_t np = c->p.n_part;
+    const int64_t begin = species < 0 ? 0 : species * np, count = species < 0 ? c->n : np;
+    if (count == 0) return FDF_OK;
+    // the fields of the current step (a buffer already holding them, or a build)
+    const void* G = nullptr;
+    int b = -1;
+    int rc = ensure_grid(c, c->k, 0u, &G, &b);
+    if (rc) return rc;
+    rc = acquire_grid(c, b);
+    if (rc) return rc;
+    double* sums = c->stage;             // 5 doubles of the staging area (>= 7 n_part doubles)
+    FDF_CUDA(cudaMemsetAsync(sums, 0, 5 * sizeof(double), c->stream), "clearing the sums");
+    rc = timed(c, FDF_K_OTHER, "acceleration terms", [&] {
+        return launch_accel_terms(c->stream, c->p.precision, c->st, c->n, begin, count, np, c->p.m_ev,
+                                  std::exp(c->lna(c->k)), c->p.interp_order == 2 ? 2 : 1, c->p.n_grid,
+                                  c->p.box_mpc, G, sums);
+    });
+    if (rc) return rc;
+    rc = release_grid(c, b);
+    if (rc) return rc;
+    double h[5];
+    FDF_CUDA(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "reading the sums");
+    FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_accel_terms");
+    for (int j = 0; j < 5; ++j) rms[j] = std::sqrt(h[j] / (double)count);
+    return FDF_OK;
+}
+
 int fdf_deposit_subset(fdf_ctx* c, int32_t species, int32_t quantity, int32_t parity, double* out,
                        int32_t out_on_device)
 {

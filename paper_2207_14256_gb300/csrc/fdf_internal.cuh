@@ -175,6 +175,11 @@ cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st
                           int64_t count, double L, double T_ev, double* x, double* q, double* w);
 cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                                   int64_t count, uint32_t* X, double* p);
+// The four terms of eq:releq at particles [begin, begin + count) with the grid G:
+// sums[0..3] += |T_i|^2, sums[4] += |T1 + T2 + T3 + T4|^2 (sums: 5 device doubles).
+cudaError_t launch_accel_terms(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                               int64_t count, int64_t n_part, const double* m_ev, double a, int order, int N,
+                               double L, const void* G, double* sums);
 // parity: -1 every particle, 0 or 1 the particles whose id has that parity (the
 // two halves of the ensemble); order: the kernel order r (1 or 2).
 cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,

@@ -614,6 +614,55 @@ __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, i
     }
 }
 
+// ---- the four terms of eq:releq (Fig. 2) ------------------------------------------
+// At each particle of [begin, begin + count), with the fields G of the current step:
+// T1 = -eps grad psi, T2 = -(q^2/eps) grad phi, T3 = q (q.grad phi)/eps, T4 = q phi_dot,
+// eps = sqrt(q^2 + m^2 a^2).  sums[0..3] accumulate |T_i|^2 and sums[4] |T1+T2+T3+T4|^2
+// (FP64, one atomic addition per warp and quantity).
+template <int Prec, typename Gt>
+__global__ void __launch_bounds__(kThreads) k_accel_terms(ParticleState st, int64_t n, int64_t begin, int64_t count,
+                                                          int64_t n_part, Masses ms, double a, int order, int N,
+                                                          double L, const Gt* __restrict__ G,
+                                                          double* __restrict__ sums)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = begin + j;
+        const double m = ms.m[i / n_part];
+        double x[3], q[3], g[8];
+        load_state<Prec>(st, n, i, L, x, q);
+        if constexpr (Prec == FDF_PREC_F64) {
+            gather_f64_order(order, reinterpret_cast<const double*>(G), N, (double)N / L, x, g);
+        } else {
+            float gf[8];
+            gather_order<Gt>(order, G, (uint32_t)N, st.X[i], st.X[n + i], st.X[2 * n + i], gf);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) g[s] = (double)gf[s];
+        }
+        const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        const double eps = sqrt(qq + m * m * a * a);
+        const double qdphi = q[0] * g[3] + q[1] * g[4] + q[2] * g[5];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double t1 = -eps * g[d], t2 = -(qq / eps) * g[3 + d], t3 = q[d] * qdphi / eps, t4 = q[d] * g[6];
+            acc[0] += t1 * t1;
+            acc[1] += t2 * t2;
+            acc[2] += t3 * t3;
+            acc[3] += t4 * t4;
+            const double tot = t1 + t2 + t3 + t4;
+            acc[4] += tot * tot;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(sums + k, v);
+    }
+}
+
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                       int64_t n_part, Masses ms, double a, double T, int quantity,
@@ -760,6 +809,25 @@ cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleS
         k_export_initial<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p);
     else
         k_export_initial<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accel_terms(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                               int64_t count, int64_t n_part, const double* m_ev, double a, int order, int N,
+                               double L, const void* G, double* sums)
+{
+    if (count <= 0) return cudaSuccess;
+    const unsigned b = grid_for(count);
+    const Masses ms = masses_of(m_ev);
+    if (precision == FDF_PREC_F64)
+        k_accel_terms<FDF_PREC_F64, double><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, order, N, L,
+                                                                       (const double*)G, sums);
+    else if (precision == FDF_PREC_F32)
+        k_accel_terms<FDF_PREC_F32, float><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, order, N, L,
+                                                                     (const float*)G, sums);
+    else
+        k_accel_terms<FDF_PREC_BF16, __nv_bfloat16><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, order,
+                                                                             N, L, (const __nv_bfloat16*)G, sums);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,7 @@ def lib():
             "fdf_sample": (C.c_int, [_V]),
             "fdf_step": (C.c_int, [_V, C.c_int32]),
             "fdf_run_graph": (C.c_int, [_V, C.c_int32]),
+            "fdf_accel_terms": (C.c_int, [_V, C.c_int32, _D]),
             "fdf_deposit": (C.c_int, [_V, C.c_int32, C.c_int32, _V, C.c_int32]),
             "fdf_deposit_subset": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, _V, C.c_int32]),
             "fdf_get": (C.c_int, [_V, C.c_int32, _V, _V, _V, C.c_int32]),
@@ -247,6 +248,13 @@ def fdf_sample(ctx):
 
 def fdf_step(ctx, n):
     _check(lib().fdf_step(ctx, int(n)), "fdf_step")
+
+
+def fdf_accel_terms(ctx, species=-1):
+    """RMS of the four terms of eq:releq and of their sum at the current step (Fig. 2)."""
+    out = np.zeros(5)
+    _check(lib().fdf_accel_terms(ctx, int(species), out.ctypes.data_as(C.POINTER(C.c_double))), "fdf_accel_terms")
+    return out
 
 
 def fdf_run_graph(ctx, n):
@@ -458,6 +466,9 @@ class Run:
 
     def run_graph(self, n):
         fdf_run_graph(self.ctx, n)
+
+    def accel_terms(self, species=-1):
+        return fdf_accel_terms(self.ctx, species)
 
     def get(self, species=0):
         n = self.n_part

@@ -15,6 +15,7 @@
 * The comparison equations of motion (Sec. 3.2 and 5) in the plain FP64 form.
 * The exact eq:releq and eq:geodesic in the non-symplectic leapfrog (Sec. 3.3) in
   the plain FP64 form.
+* The RMS of the four terms of eq:releq (Fig. 2) in every precision form.
 """
 import math
 
@@ -207,3 +208,38 @@ def test_exact_equations_of_motion_match_the_oracle(F, inputs, c1_tables, spp, o
     d = np.max(np.linalg.norm(base["q"] - res[0][1], axis=0) / np.linalg.norm(base["q"], axis=0))
     print("exact against the separable form: largest |dq| / |q| %.3e" % d)
     assert d > 1e-9
+
+
+# ---- the four terms of eq:releq (Fig. 2) --------------------------------------------------------
+@pytest.mark.parametrize("prec,order", [(0, 1), (1, 1), (1, 2), (2, 1)])
+def test_accel_terms_match_the_oracle(F, inputs, c1_tables, prec, order):
+    """fdf_accel_terms against the oracle's on the oracle's own particles, per species and
+    for all, at an early step (relativistic: the first two terms alike) and a late one.
+    The q phi_dot term has its own bound in the split forms: phi_dot shares its packed
+    transform with psi, about 1e4 times larger late in the run, and the FP32 (BF16)
+    rounding of that pair sets phi_dot's error."""
+    p = inputs.config("c1_32", n_part=3001, n_species=2, m_ev=[0.05, 0.2], n_grid=16, n_steps=60, precision=prec,
+                      seed=181, interp_order=order)
+    o = O.Oracle(p, c1_tables)
+    tol = {0: 1e-9, 1: 1e-5, 2: 3e-3}[prec]
+    tol_dot = {0: 1e-9, 1: 1e-3, 2: 1.0}[prec]
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        done = 0
+        for k in (5, 60):
+            r.step(k - done)
+            done = k
+            got = [r.accel_terms(s) for s in (0, 1, -1)]
+            ref = []
+            for s in range(2):
+                g = np.arange(s * p["n_part"], (s + 1) * p["n_part"])
+                st = o.run(g, k_to=k)
+                ref.append(o.accel_terms(g, st["x"], st["q"], k))
+            g = np.arange(2 * p["n_part"])
+            st = o.run(g, k_to=k)
+            ref.append(o.accel_terms(g, st["x"], st["q"], k))
+            for s, gv, rv in zip((0, 1, -1), got, ref):
+                rel = np.abs(gv - rv) / rv
+                print("prec %d order %d step %d species %2d: rms %s  (rel. err %.2e, phi_dot term %.2e)"
+                      % (prec, order, k, s, " ".join("%.3e" % v for v in gv), np.delete(rel, 3).max(), rel[3]))
+                assert np.delete(rel, 3).max() < tol and rel[3] < tol_dot, (s, gv, rv)

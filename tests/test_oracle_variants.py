@@ -330,3 +330,68 @@ def test_phi_plus_psi_slot_is_psi_plus_the_potential_of_grad_phi(inputs, c1_tabl
         ref = plain[3 + d]
         assert np.max(np.abs(grad - ref)) < 1e-10 * np.max(np.abs(ref)), d
     assert np.max(np.abs(phi)) > 0.1 * np.max(np.abs(plain[7]))
+
+
+# ---- the four terms of eq:releq (Fig. 2) ------------------------------------------------------
+def test_accel_terms_exact_cases(inputs, c1_tables):
+    """Closed cases of the RMS of -eps grad psi, -(q^2/eps) grad phi, q (q.grad phi)/eps,
+    q phi_dot and of their sum, under uniform fields:
+    * a momentum parallel to grad phi: the two grad phi terms cancel (the sum has only
+      the grad psi term), a perpendicular one: the third term vanishes;
+    * massless particles (eps = |q|): the first two terms are |q| |grad psi| and
+      |q| |grad phi|;
+    * phi_dot alone: the fourth term is |phi_dot| |q|, the others vanish."""
+    p = inputs.config("c1_32", n_grid=16, n_part=4096, n_steps=40, seed=21, m_ev=[0.05])
+    N = p["n_grid"]
+    o = O.Oracle(p, c1_tables)
+    g = np.arange(64)
+    ic = o.initial(g, frozen=np.zeros((8, N, N, N)))
+    x = ic["x"]
+    qn = np.linalg.norm(ic["q"], axis=0)
+    k = 25
+    a = math.exp(o.lna(k))
+    m = p["m_ev"][0]
+    eps = np.sqrt(qn ** 2 + (m * a) ** 2)
+    gpsi, gphi = np.array([2e-6, -1e-6, 5e-7]), np.array([-3e-7, 4e-7, 1e-6])
+    # parallel to grad phi
+    qpar = np.outer(gphi / np.linalg.norm(gphi), qn)
+    r = o.accel_terms(g, x, qpar, k, frozen=inputs.uniform_fields(N, gpsi, gphi, 0.0, 0.0))
+    assert abs(r[1] - r[2]) <= 1e-14 * r[1] and r[1] > 0
+    assert abs(r[4] - r[0]) <= 1e-14 * r[0]
+    assert math.isclose(r[0], np.linalg.norm(gpsi) * math.sqrt(np.mean(eps ** 2)), rel_tol=1e-13)
+    # perpendicular to grad phi
+    perp = np.cross(gphi, [1.0, 0.0, 0.0])
+    qperp = np.outer(perp / np.linalg.norm(perp), qn)
+    r = o.accel_terms(g, x, qperp, k, frozen=inputs.uniform_fields(N, np.zeros(3), gphi, 0.0, 0.0))
+    assert r[2] <= 1e-14 * r[1] and r[0] == 0.0 and r[3] == 0.0
+    assert math.isclose(r[1], np.linalg.norm(gphi) * math.sqrt(np.mean((qn ** 2 / eps) ** 2)), rel_tol=1e-13)
+    assert abs(r[4] - r[1]) <= 1e-14 * r[1]
+    # massless
+    o0 = O.Oracle(dict(p, m_ev=[0.0]), c1_tables)
+    r = o0.accel_terms(g, x, ic["q"], k, frozen=inputs.uniform_fields(N, gpsi, gphi, 0.0, 0.0))
+    rq = math.sqrt(np.mean(qn ** 2))
+    assert math.isclose(r[0], np.linalg.norm(gpsi) * rq, rel_tol=1e-13)
+    assert math.isclose(r[1], np.linalg.norm(gphi) * rq, rel_tol=1e-13)
+    # phi_dot alone
+    r = o.accel_terms(g, x, ic["q"], k, frozen=inputs.uniform_fields(N, np.zeros(3), np.zeros(3), 3e-9, 0.0))
+    assert r[0] == r[1] == r[2] == 0.0
+    assert math.isclose(r[3], 3e-9 * math.sqrt(np.mean(qn ** 2)), rel_tol=1e-13) and r[4] == r[3]
+
+
+def test_accel_terms_follow_the_paper_trend(inputs, c1_tables):
+    """Fig. 2's reading of eq:releq on a run with built fields: the Newtonian term's share
+    grows as the particles become non-relativistic (eps/|q| grows with a), while the two
+    quadratic terms stay of one order."""
+    p = inputs.config("c1_32", n_grid=16, n_part=4096, n_steps=60, seed=29, m_ev=[0.1])
+    o = O.Oracle(p, c1_tables)
+    g = np.arange(2000)
+    ic = o.initial(g)
+    x, q = ic["x"], ic["q"]
+    ratios = []
+    for k0, k1 in ((0, 5), (5, 60)):
+        x, q = o.integrate(g, x, q, ic["q0"], k0, k1)
+        r = o.accel_terms(g, x, q, k1)
+        print("step %d: rms terms %s" % (k1, " ".join("%.3e" % v for v in r)))
+        assert 0.05 < r[2] / r[1] < 2.0
+        ratios.append(r[0] / r[1])
+    assert ratios[1] > 3 * ratios[0]
