@@ -439,11 +439,13 @@ template <typename Gt, typename V> struct GRec;
 // for them (FP32 halves: 232 -> 310 us per x pass at 256^3).
 template <> struct GRec<float, float2> {
     static constexpr bool kHalves = false;
+    // one 32-byte store per record (the record is 32-byte aligned)
     __device__ static void put(float* G, size_t cell, float2 a, float2 b, float2 c, float2 d)
     {
-        float4* g = reinterpret_cast<float4*>(G) + 2 * cell;
-        g[0] = make_float4(a.x, a.y, b.x, b.y);
-        g[1] = make_float4(c.x, c.y, d.x, d.y);
+        float* g = G + 8 * cell;
+        asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(g), "f"(a.x), "f"(a.y),
+                     "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
+                     : "memory");
     }
 };
 template <> struct GRec<double, double2> {
