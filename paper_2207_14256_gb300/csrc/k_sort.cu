@@ -161,6 +161,44 @@ static_assert(sizeof(PlainRec) == 128, "PlainRec is four sectors");
 template <int Prec> struct RecOf { using T = SplitRec; };
 template <> struct RecOf<FDF_PREC_F64> { using T = PlainRec; };
 
+// A split record moves as two 32-byte vector accesses (the record buffer and each
+// record are 64-byte aligned).
+__device__ __forceinline__ void store_split(void* recs, int64_t j, const SplitRec& r)
+{
+    uint32_t* p = reinterpret_cast<uint32_t*>(recs) + 16 * j;
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(r.X[0]), "r"(r.X[1]),
+                 "r"(r.X[2]), "r"(__float_as_uint(r.q0[0])), "r"(__float_as_uint(r.q0[1])),
+                 "r"(__float_as_uint(r.q0[2])), "r"(__float_as_uint(r.dq[0])), "r"(__float_as_uint(r.dq[1]))
+                 : "memory");
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p + 8),
+                 "r"(__float_as_uint(r.dq[2])), "r"(r.id), "r"((uint32_t)__double2loint(r.pmag)),
+                 "r"((uint32_t)__double2hiint(r.pmag)), "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                 : "memory");
+}
+
+__device__ __forceinline__ SplitRec load_split(const void* recs, int64_t j)
+{
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(recs) + 16 * j;
+    uint32_t w[16];
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                 : "l"(p));
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]),
+                   "=r"(w[15])
+                 : "l"(p + 8));
+    SplitRec r;
+    for (int d = 0; d < 3; ++d) {
+        r.X[d] = w[d];
+        r.q0[d] = __uint_as_float(w[3 + d]);
+        r.dq[d] = __uint_as_float(w[6 + d]);
+    }
+    r.id = w[9];
+    r.pmag = __hiloint2double((int)w[11], (int)w[10]);
+    r.pad[0] = r.pad[1] = r.pad[2] = r.pad[3] = 0;
+    return r;
+}
+
 template <int Prec>
 __device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int64_t i, typename RecOf<Prec>::T& r)
 {
@@ -232,7 +270,8 @@ __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t
             if (!live[u]) continue;
             const uint32_t b = __shfl_sync(peers[u], base[u], leader[u]);
             const int64_t j = (int64_t)b + __popc(peers[u] & ((1u << lane) - 1u));
-            reinterpret_cast<Rec*>(recs)[j] = r[u];
+            if constexpr (Prec == FDF_PREC_F64) reinterpret_cast<Rec*>(recs)[j] = r[u];
+            else store_split(recs, j, r[u]);
         }
     }
 }
@@ -252,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64
             if (b.sd) b.sd[j] = r.s;
             b.id[j] = r.id;
         } else {
-            const SplitRec r = reinterpret_cast<const SplitRec*>(recs)[j];
+            const SplitRec r = load_split(recs, j);
             for (int d = 0; d < 3; ++d) {
                 b.X[d * n + j] = r.X[d];
                 b.q0f[d * n + j] = r.q0[d];
