@@ -140,14 +140,22 @@ template <int N> struct Shape {
     static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, G = N1 / N2;
     static constexpr int T = N2;                               // threads per line
     static constexpr int TS0 = N2 * (N1 + 1);                  // transpose buffer per line (elements)
-    // y and z passes: TX lines (consecutive x) per block, lane = xo + TX t, so the
-    // 32 lanes of a warp cover 32/TX values of t; a line stride TS = 32/TX (mod 16)
-    // spreads them over each pair of banks exactly twice (2 wavefronts per access).
+    // y and z passes: TX lines (consecutive x) per block, lane = xo + TX t.
     static constexpr int TX0 = 128 / T > 16 ? 128 / T : 16;
     static constexpr int TX = TX0 < N ? TX0 : N;
     static constexpr int THREADS = TX * T;
-    static constexpr int SYZ = (32 / TX) % 16;
-    static constexpr int TS = TS0 + ((SYZ - TS0 % 16) + 16) % 16;
+    // Line stride of the y and z passes' transpose buffers, in elements of E bytes.  One
+    // shared-memory wavefront serves 128 bytes: P = 128 / E consecutive lanes over P bank
+    // groups.  Lane xo + TXl t touches element n2 (N1 + 1) + k of the line at xo * stride
+    // (n2 = t, N1 + 1 odd).  With stride = P / TXl (mod P) for TXl < P (a wavefront spans
+    // P / TXl values of t), else 1 (mod P), the P lanes fall in P distinct bank groups.
+    template <int E, int TXl>
+    __host__ __device__ static constexpr int line_stride()
+    {
+        constexpr int P = 128 / E;
+        constexpr int S = TXl < P ? P / TXl : 1;
+        return TS0 + ((S - TS0 % P) % P + P) % P;
+    }
     // x pass: TL lines per block, lane = t + T lo; stride TSX = T (mod 16).
     static constexpr int TL0 = 128 / T;
     static constexpr int TL = TL0 < N ? TL0 : N;
@@ -159,8 +167,6 @@ template <int N> struct Shape {
     static constexpr int TZ0 = 128 / T;
     static constexpr int TZ = TZ0 < N ? TZ0 : N;
     static constexpr int THREADS_Z = TZ * T;
-    static constexpr int SZ = (32 / TZ) % 16;
-    static constexpr int TSZ = TS0 + ((SZ - TS0 % 16) + 16) % 16;
 };
 
 // Twiddles of the first level, w_N^(n2 k1) at [n2 (N1 + 1) + k1]: a thread reads its
@@ -344,10 +350,11 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
     using T = typename Real<V>::T;
     using S = Shape<N>;
     constexpr int TX = S::TZ, N1 = S::N1, N2 = S::N2, NT = S::THREADS_Z;
+    constexpr int TSZ = S::template line_stride<sizeof(V), S::TZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* tr = s_tw + S::TWS;                                  // TX * TSZ
-    T* As = reinterpret_cast<T*>(tr + TX * S::TSZ);         // [3][N1][NT]: each thread's own column
+    T* As = reinterpret_cast<T*>(tr + TX * TSZ);            // [3][N1][NT]: each thread's own column
     load_line_twiddles<V, N>(s_tw, tw);
     const int xo = threadIdx.x % TX, t = threadIdx.x / TX;
     const int x0 = blockIdx.x * TX, jy = blockIdx.y;
@@ -394,10 +401,10 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
                 else form(Idx<3>{});
                 break;
         }
-        line_first<V, N>(v, t, s_tw, tr + xo * S::TSZ);
+        line_first<V, N>(v, t, s_tw, tr + xo * TSZ);
         __syncthreads();
         V* dst = W0 + p * N3 + (size_t)jy * N + x0 + xo;
-        line_second<V, N>(t, tr + xo * S::TSZ, [&](int z, V val) { dst[(size_t)z * NN] = val; });
+        line_second<V, N>(t, tr + xo * TSZ, [&](int z, V val) { dst[(size_t)z * NN] = val; });
         __syncthreads();
     }
 }
@@ -411,6 +418,7 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fields_y(FieldArgs a, con
 {
     using S = Shape<N>;
     constexpr int TX = S::TX, N1 = S::N1, N2 = S::N2;
+    constexpr int TS = S::template line_stride<sizeof(V), S::TX>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* s_tw = reinterpret_cast<V*>(smem_raw);
     V* tr = s_tw + S::TWS;
@@ -422,10 +430,10 @@ __global__ void __launch_bounds__(Shape<N>::THREADS) k_fields_y(FieldArgs a, con
     V v[N1];
     sfor<N1>([&](auto N1i) { v[N1i] = src[(size_t)(N2 * N1i + t) * N]; });
     __syncthreads();
-    line_first<V, N>(v, t, s_tw, tr + xo * S::TS);
+    line_first<V, N>(v, t, s_tw, tr + xo * TS);
     __syncthreads();
     V* dst = W1 + p * N3 + (size_t)jz * N * N + x0 + xo;
-    line_second<V, N>(t, tr + xo * S::TS, [&](int y, V val) { dst[(size_t)y * N] = val; });
+    line_second<V, N>(t, tr + xo * TS, [&](int y, V val) { dst[(size_t)y * N] = val; });
 }
 
 // ---- pass x: inverse DFT along x, interleave into G[cell][8] ----------------
@@ -562,7 +570,8 @@ cudaError_t run_z(cudaStream_t s, const FieldArgs& a, const void* A, const void*
 {
     using S = Shape<N>;
     using T = typename Real<V>::T;
-    const size_t sm = (size_t)(S::TWS + S::TZ * S::TSZ) * sizeof(V) + (size_t)3 * S::N1 * S::THREADS_Z * sizeof(T);
+    constexpr int TSZ = S::template line_stride<sizeof(V), S::TZ>();
+    const size_t sm = (size_t)(S::TWS + S::TZ * TSZ) * sizeof(V) + (size_t)3 * S::N1 * S::THREADS_Z * sizeof(T);
     cudaError_t e = set_smem(k_fields_z<V, N>, sm);
     if (e != cudaSuccess) return e;
     k_fields_z<V, N><<<dim3(N / S::TZ, N), S::THREADS_Z, sm, s>>>(a, (const T*)A, (const V*)R, (const V*)tw, (V*)W0);
@@ -573,7 +582,8 @@ template <typename V, int N>
 cudaError_t run_y(cudaStream_t s, const FieldArgs& a, const void* tw, const void* W0, void* W1)
 {
     using S = Shape<N>;
-    const size_t sm = (size_t)(S::TWS + S::TX * S::TS) * sizeof(V);
+    constexpr int TS = S::template line_stride<sizeof(V), S::TX>();
+    const size_t sm = (size_t)(S::TWS + S::TX * TS) * sizeof(V);
     cudaError_t e = set_smem(k_fields_y<V, N>, sm);
     if (e != cudaSuccess) return e;
     k_fields_y<V, N><<<dim3(N / S::TX, N, 4), S::THREADS, sm, s>>>(a, (const V*)tw, (const V*)W0, (V*)W1);
