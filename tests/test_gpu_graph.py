@@ -100,6 +100,11 @@ def test_refusals(F, inputs, c1_tables):
             r.run_graph(8)
         assert e.value.code == F.FDF_ESTATE
         F.fdf_timing(r.ctx, False)
+        r.set_fields(inputs.uniform_fields(p["n_grid"], np.ones(3) * 1e-6, np.zeros(3), 0.0, 0.0))
+        with pytest.raises(F.FdfError) as e:
+            r.run_graph(8)
+        assert e.value.code == F.FDF_ESTATE
+        r.set_fields(None)
         r.run_graph(0)
         assert r.state()[0] == 0
         r.step(8)
