@@ -213,12 +213,18 @@ def bench_ours(args, rank, world, dist):
             # event pair around every launch (fdf_timing).  The events cost about 10 ms
             # per run, so they stay out of the timed region above.
             fdf.fdf_timing(ctx, True)
-            i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            i0.record(stream)
-            run_once(fdf, ctx, p, dep)
-            i1.record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            fdf.fdf_sample(ctx)
+            ev[1].record(stream)
+            fdf.fdf_step(ctx, p["n_steps"])
+            ev[2].record(stream)
+            fdf.fdf_deposit(ctx, -1, fdf.FDF_Q_W_EPS, dep)
+            ev[3].record(stream)
             barrier()
-            inst_ms = i0.elapsed_time(i1)
+            inst_ms = ev[0].elapsed_time(ev[3])
+            phases = {"sample_ms": ev[0].elapsed_time(ev[1]), "steps_ms": ev[1].elapsed_time(ev[2]),
+                      "deposit_ms": ev[2].elapsed_time(ev[3])}
             ktimes = {k: fdf.fdf_kernel_time(ctx, v) for k, v in fdf.KERNEL_CLASSES.items()}
             fdf.fdf_timing(ctx, False)
             # host time to enqueue the steps of one run while the device works through
@@ -307,7 +313,8 @@ def bench_ours(args, rank, world, dist):
                      "note": "the same workload with the paper's super-steps (not the headline: the headline builds "
                              "every step's fields by transform)"}
 
-    return dict(p=p, ms=ms, units=units, launches=launches, ktimes=ktimes, inst_ms=inst_ms, clocks=clk, e2e_s=e2e_s,
+    return dict(p=p, ms=ms, units=units, launches=launches, ktimes=ktimes, inst_ms=inst_ms, phases=phases,
+                clocks=clk, e2e_s=e2e_s,
                 tune=tune, host_ms=host_ms, superstep=superstep,
                 e2e_steps=e2e_steps, tab_bytes=tab_bytes, d2h=p["n_species"] * np_ * 7 * 8, plain=plain)
 
@@ -535,6 +542,10 @@ def main():
                         "x, q and w of every species into pinned host memory + fdf_destroy, per step"},
         "gpu_launches": r["launches"],
         "host_enqueue_ms_per_step": r["host_ms"],
+        "phases": dict(r["phases"], steps_only_value=whole_job_value(world, r["units"], r["phases"]["steps_ms"] / 1e3),
+                       note="the instrumented run's phases: fdf_sample (sampling, the first grid build, the "
+                            "momentum transform, the first sort), fdf_step(n_steps) and fdf_deposit; "
+                            "steps_only_value = particle-steps / steps_ms"),
         "kernels": per_run,
         "clocks": r["clocks"],
     })
