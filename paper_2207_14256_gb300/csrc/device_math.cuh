@@ -108,4 +108,27 @@ __device__ __forceinline__ void fixed_cell(uint32_t X, uint32_t N, uint32_t& i0,
     i1 = (i0 + 1u == N) ? 0u : i0 + 1u;
 }
 
+// |q| with the sampler's exactly rounded evaluation order, so that an
+// untouched momentum reproduces p = |q_sampled| bit for bit.
+__device__ __forceinline__ double norm3_rn(const double q[3])
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])), __dmul_rn(q[2], q[2])));
+}
+
+// delta-f weight (Sec. 2.2), w = 1 - fbar(|q|)/fbar(p), in the cancellation-free form
+// w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)).
+__device__ __forceinline__ double dfweight(double qm, double p, double T)
+{
+    return -expm1((p - qm) / T) / (1.0 + exp(-qm / T));
+}
+
+// The same weight as the split forms compute it: the small difference p - |q| in
+// FP64 (|q| from norm3_rn), the rest in FP32 (their momenta carry FP32 rounding
+// already, and GB300's FP64 transcendental functions are slow).
+__device__ __forceinline__ float dfweight_split(double qm, double p, double T)
+{
+    const float arg = (float)((p - qm) / T);
+    return -expm1f(arg) / (1.f + expf(-(float)qm / (float)T));
+}
+
 }  // namespace fdf

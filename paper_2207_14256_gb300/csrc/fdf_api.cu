@@ -1264,7 +1264,11 @@ int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_
     double* xs = out_on_device ? x : (x ? c->stage : nullptr);
     double* qs = out_on_device ? q : (q ? c->stage + 3 * np : nullptr);
     double* ws = out_on_device ? w : (w ? c->stage + 6 * np : nullptr);
+    // a sorted state leaves id order: go through the sort's record buffer
     int rc = timed(c, FDF_K_OTHER, "export", [&] {
+        if (c->sorts > 0 && c->recs)
+            return launch_export_records(c->stream, c->p.precision, c->st, c->n, begin, np, c->p.box_mpc, c->T_ev,
+                                         c->recs, xs, qs, ws);
         return launch_export(c->stream, c->p.precision, c->st, c->n, begin, np, c->p.box_mpc, c->T_ev, xs, qs, ws);
     });
     if (rc) return rc;

@@ -175,6 +175,11 @@ cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st
                           int64_t count, double L, double T_ev, double* x, double* q, double* w);
 cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                                   int64_t count, uint32_t* X, double* p);
+// launch_export's outputs for a permuted (sorted) state, through recs (the sort's
+// record buffer, >= count records): one whole record per particle scattered to its
+// id slot, then a streaming pass that writes x, q, w.
+cudaError_t launch_export_records(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                                  int64_t count, double L, double T_ev, void* recs, double* x, double* q, double* w);
 // The four terms of eq:releq at particles [begin, begin + count) with the grid G:
 // sums[0..3] += |T_i|^2, sums[4] += |T1 + T2 + T3 + T4|^2 (sums: 5 device doubles).
 cudaError_t launch_accel_terms(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,

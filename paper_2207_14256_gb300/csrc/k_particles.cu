@@ -246,13 +246,6 @@ __device__ __forceinline__ uint32_t round_mod32(FF d)
     return (uint32_t)i + (uint32_t)i2;
 }
 
-// |q| with the sampler's exactly rounded evaluation order, so that an
-// untouched momentum reproduces p = |q_sampled| bit for bit.
-__device__ __forceinline__ double norm3_rn(const double q[3])
-{
-    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])), __dmul_rn(q[2], q[2])));
-}
-
 struct Masses {
     double m[kMaxSpecies];
 };
@@ -559,13 +552,6 @@ __device__ __forceinline__ void load_state(const ParticleState& st, int64_t n, i
     }
 }
 
-// delta-f weight (Sec. 2.2), w = 1 - fbar(|q|)/fbar(p), in the cancellation-free form
-// w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)).
-__device__ __forceinline__ double dfweight(double qm, double p, double T)
-{
-    return -expm1((p - qm) / T) / (1.0 + exp(-qm / T));
-}
-
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                      double L, double T, double* __restrict__ xo,
@@ -587,7 +573,10 @@ __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n
             qo[count + o] = q[1];
             qo[2 * count + o] = q[2];
         }
-        if (wo) wo[o] = dfweight(norm3_rn(q), st.pmag[i], T);
+        if (wo) {
+            if constexpr (Prec == FDF_PREC_F64) wo[o] = dfweight(norm3_rn(q), st.pmag[i], T);
+            else wo[o] = (double)dfweight_split(norm3_rn(q), st.pmag[i], T);
+        }
     }
 }
 
@@ -692,8 +681,7 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
             const float qf = (float)qm;
             const float ma = (float)(m * a);
             const float eps = sqrtf(fmaf(qf, qf, ma * ma));
-            const float arg = (float)((st.pmag[i] - qm) / T);
-            const float w = -expm1f(arg) / (1.f + expf(-qf / (float)T));
+            const float w = dfweight_split(qm, st.pmag[i], T);
             if (quantity == FDF_Q_W_EPS) v = (double)(w * eps);
             else if (quantity == FDF_Q_W) v = (double)w;
             else if (quantity == FDF_Q_EPS) v = (double)eps;

@@ -303,6 +303,68 @@ __global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64
     }
 }
 
+// ---- export in id order through the record buffer -------------------------------
+// A sorted state holds particle i's outputs at slot id[i] - begin of the caller's
+// arrays.  Writing them there directly scatters seven 8-byte values per particle;
+// instead each particle's record goes whole to that slot (one scattered 64-byte
+// write), and a streaming pass turns the records into positions, momenta and
+// weights.
+template <int Prec>
+__global__ void __launch_bounds__(kThreads) k_export_pack(ParticleState a, int64_t n, int64_t begin, int64_t count,
+                                                          void* __restrict__ recs)
+{
+    using Rec = typename RecOf<Prec>::T;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = begin + j;
+        const int64_t o = (int64_t)a.id[i] - begin;
+        Rec r;
+        make_rec<Prec>(a, n, i, r);
+        if constexpr (Prec == FDF_PREC_F64) reinterpret_cast<Rec*>(recs)[o] = r;
+        else store_split(recs, o, r);
+    }
+}
+
+template <int Prec>
+__global__ void __launch_bounds__(kThreads) k_export_unpack(const void* __restrict__ recs, int64_t count, double L,
+                                                            double T, double* __restrict__ xo,
+                                                            double* __restrict__ qo, double* __restrict__ wo)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < count;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        double x[3], q[3], pm;
+        if constexpr (Prec == FDF_PREC_F64) {
+            const PlainRec r = reinterpret_cast<const PlainRec*>(recs)[o];
+            for (int d = 0; d < 3; ++d) {
+                x[d] = r.x[d];
+                q[d] = r.q[d];
+            }
+            pm = r.pmag;
+        } else {
+            const SplitRec r = load_split(recs, o);
+            for (int d = 0; d < 3; ++d) {
+                x[d] = L * ((double)r.X[d] * 2.3283064365386963e-10);
+                q[d] = (double)r.q0[d] + (double)r.dq[d];
+            }
+            pm = r.pmag;
+        }
+        if (xo) {
+            xo[o] = x[0];
+            xo[count + o] = x[1];
+            xo[2 * count + o] = x[2];
+        }
+        if (qo) {
+            qo[o] = q[0];
+            qo[count + o] = q[1];
+            qo[2 * count + o] = q[2];
+        }
+        if (wo) {
+            if constexpr (Prec == FDF_PREC_F64) wo[o] = dfweight(norm3_rn(q), pm, T);
+            else wo[o] = (double)dfweight_split(norm3_rn(q), pm, T);
+        }
+    }
+}
+
 unsigned grid_for(int64_t n)
 {
     int64_t b = (n + kThreads - 1) / kThreads;
@@ -340,6 +402,21 @@ cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, c
     } else {
         k_sort_pack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, key, hist, recs);
         k_sort_unpack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(b, n, recs);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_records(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
+                                  int64_t count, double L, double T_ev, void* recs, double* x, double* q, double* w)
+{
+    if (count <= 0) return cudaSuccess;
+    const unsigned b = grid_for(count);
+    if (precision == FDF_PREC_F64) {
+        k_export_pack<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, recs);
+        k_export_unpack<FDF_PREC_F64><<<b, kThreads, 0, s>>>(recs, count, L, T_ev, x, q, w);
+    } else {
+        k_export_pack<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, recs);
+        k_export_unpack<FDF_PREC_F32><<<b, kThreads, 0, s>>>(recs, count, L, T_ev, x, q, w);
     }
     return cudaGetLastError();
 }
