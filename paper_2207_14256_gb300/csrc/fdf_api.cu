@@ -707,10 +707,13 @@ int join_fields(fdf_ctx* c)
 
 // Sort by the positions the particles will have halfway through the next pass,
 // which runs in direction dir from the current step.
-int sort_particles(fdf_ctx* c, int dir)
+int sort_particles(fdf_ctx* c, int dir, bool pre_transform = false)
 {
     SortLead lead{};
-    if (c->p.precision != FDF_PREC_F64) {
+    if (pre_transform) {
+        // split forms right after sampling: by position alone, carrying the sampled momenta
+        lead.pre_transform = 1;
+    } else if (c->p.precision != FDF_PREC_F64) {
         const double l1 = c->lna(c->k), l2 = c->lna(c->k + 0.5 * c->spp * dir);
         double W[kMaxGL], a2[kMaxGL];
         nodes(c, std::min(l1, l2), std::max(l1, l2), W, a2);
@@ -988,6 +991,16 @@ int sample_enqueue(fdf_ctx* c)
     c->ssk[0] = c->ssk[1] = -1;
     rc = draw_noise(c);
     if (rc) return rc;
+    // The split forms sort right after sampling, so that the transform's gather of the
+    // step-0 grid runs over spatially ordered particles (at z_start a particle crosses a
+    // negligible part of a cell in the first pass, so no lead is lost).  The plain form
+    // keeps its sampled positions in id order and sorts after the transform.
+    const bool sort0 = c->p.sort_every >= 0 && c->n > 0;
+    const bool split = c->p.precision != FDF_PREC_F64;
+    if (sort0 && split) {
+        rc = sort_particles(c, 1, true);
+        if (rc) return rc;
+    }
     const void* G0 = nullptr;
     int b0 = -1;
     if (c->st.sd) FDF_CUDA(cudaMemsetAsync(c->st.sd, 0, (size_t)c->n * 8, c->stream), "clearing phi + psi");
@@ -1011,7 +1024,7 @@ int sample_enqueue(fdf_ctx* c)
         c->ssk[0] = c->ssk[1] = -1;
     }
     c->k = 0;
-    if (c->p.sort_every >= 0 && c->n > 0) {
+    if (sort0 && !split) {
         rc = sort_particles(c, 1);
         if (rc) return rc;
     }
@@ -1288,22 +1301,20 @@ int fdf_get_initial(fdf_ctx* c, int32_t species, uint32_t* X, double* q_sampled,
     if (species < 0 || species >= c->p.n_species) return fail(FDF_EINVAL, "species out of range");
     const int64_t np = c->p.n_part, n = c->n, begin = species * np;
     if (np == 0) return FDF_OK;
-    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     // positions and |q_sampled| follow the particle permutation: un-permute by id
     uint32_t* Xs = out_on_device ? X : (X ? (uint32_t*)c->stage : nullptr);
     double* ps = out_on_device ? pm : (pm ? c->stage + 2 * np : nullptr);
+    double* qss = out_on_device ? q_sampled : (q_sampled ? c->stage + 3 * np : nullptr);
     int rc = timed(c, FDF_K_OTHER, "export initial", [&] {
-        return launch_export_initial(c->stream, c->p.precision, c->st, n, begin, np, Xs, ps);
+        return launch_export_initial(c->stream, c->p.precision, c->st, n, begin, np, Xs, ps, qss);
     });
     if (rc) return rc;
     if (!out_on_device) {
         if (X) FDF_CUDA(cudaMemcpyAsync(X, Xs, 3 * np * 4, cudaMemcpyDeviceToHost, c->stream), "copy X");
         if (pm) FDF_CUDA(cudaMemcpyAsync(pm, ps, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy p");
+        if (q_sampled)
+            FDF_CUDA(cudaMemcpyAsync(q_sampled, qss, 3 * np * 8, cudaMemcpyDeviceToHost, c->stream), "copy q_sampled");
     }
-    // the sampled momenta are not permuted
-    for (int d = 0; d < 3 && q_sampled; ++d)
-        FDF_CUDA(cudaMemcpyAsync(q_sampled + d * np, c->st.qs + d * n + begin, np * 8, kind, c->stream),
-                 "copy q_sampled");
     FDF_CUDA(cudaStreamSynchronize(c->stream), "fdf_get_initial");
     return FDF_OK;
 }

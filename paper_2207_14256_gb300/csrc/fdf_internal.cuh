@@ -143,7 +143,8 @@ struct ParticleState {
     double* qd;
     double* q0d;
     double* sd;         // [n] phi + psi from the last kick (the exact equations of motion), or NULL
-    double* qs;         // [3][n] sampled momenta
+    double* qs;         // [3][n] sampled momenta (one array for both halves: id order in the plain form;
+                        // the split forms carry it through their sort before the transform only)
     double* pmag;       // [n]
     uint32_t* id;       // [n]
 };
@@ -163,6 +164,9 @@ struct SortLead {
     int on;
     float dtau_q32[kMaxSpecies];  // conformal time of the lead, times 2^32 / L
     float m2a2[kMaxSpecies];      // m^2 a^2 at the middle of the lead
+    // split forms, before the momentum transform: q0/dq do not exist yet; the keys
+    // use the positions alone and the sampled momenta qs travel with the particles
+    int pre_transform;
 };
 inline int sort_tile_shift(const fdf_params& p) { return p.sort_tile; }
 size_t sort_record_bytes(int precision);
@@ -174,7 +178,7 @@ cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, c
 cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                           int64_t count, double L, double T_ev, double* x, double* q, double* w);
 cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
-                                  int64_t count, uint32_t* X, double* p);
+                                  int64_t count, uint32_t* X, double* p, double* qs);
 // launch_export's outputs for a permuted (sorted) state, through recs (the sort's
 // record buffer, >= count records): one whole record per particle scattered to its
 // id slot, then a streaming pass that writes x, q, w.

@@ -581,12 +581,13 @@ __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n
 }
 
 // The pre-initial draw in particle-index order.  The split form's fixed-point
-// positions are the live state and follow the permutation; the plain form keeps
-// them in id order.  |q_sampled| follows the permutation in both forms.
+// positions and sampled momenta are the live state and follow the permutation (it
+// sorts before the momentum transform); the plain form keeps them in id order.
+// |q_sampled| follows the permutation in both forms.
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, int64_t n, int64_t begin,
                                                              int64_t count, uint32_t* __restrict__ Xo,
-                                                             double* __restrict__ po)
+                                                             double* __restrict__ po, double* __restrict__ qso)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -600,6 +601,13 @@ __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, i
             }
         }
         if (po) po[o] = st.pmag[i];
+        if (qso) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if constexpr (Prec == FDF_PREC_F64) qso[d * count + j] = st.qs[d * n + i];
+                else qso[d * count + o] = st.qs[d * n + i];
+            }
+        }
     }
 }
 
@@ -789,14 +797,14 @@ cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st
 }
 
 cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
-                                  int64_t count, uint32_t* X, double* p)
+                                  int64_t count, uint32_t* X, double* p, double* qs)
 {
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
     if (precision == FDF_PREC_F64)
-        k_export_initial<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p);
+        k_export_initial<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p, qs);
     else
-        k_export_initial<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p);
+        k_export_initial<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p, qs);
     return cudaGetLastError();
 }
 

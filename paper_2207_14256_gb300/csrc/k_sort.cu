@@ -54,14 +54,17 @@ __global__ void __launch_bounds__(kThreads) k_sort_keys(ParticleState st, int64_
                 c[d] = (uint32_t)ci >> tile_shift;
             }
         } else {
-            float q[3];
-            float q2 = 0.f;
+            float q[3] = {0.f, 0.f, 0.f};
+            float k = 0.f;
+            if (lead.on) {   // without a lead the momenta are not read (they may not exist yet)
+                float q2 = 0.f;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                q[d] = st.q0f[d * n + i] + st.dqf[d * n + i];
-                q2 = fmaf(q[d], q[d], q2);
+                for (int d = 0; d < 3; ++d) {
+                    q[d] = st.q0f[d * n + i] + st.dqf[d * n + i];
+                    q2 = fmaf(q[d], q[d], q2);
+                }
+                k = lead.dtau_q32[s] * rsqrtf(q2 + lead.m2a2[s]);
             }
-            const float k = lead.on ? lead.dtau_q32[s] * rsqrtf(q2 + lead.m2a2[s]) : 0.f;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 // a saturated shift only makes the bucket a poor guess, never wrong
@@ -200,7 +203,8 @@ __device__ __forceinline__ SplitRec load_split(const void* recs, int64_t j)
 }
 
 template <int Prec>
-__device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int64_t i, typename RecOf<Prec>::T& r)
+__device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int64_t i, typename RecOf<Prec>::T& r,
+                                         bool pre_transform = false)
 {
     if constexpr (Prec == FDF_PREC_F64) {
         for (int d = 0; d < 3; ++d) {
@@ -213,10 +217,24 @@ __device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int6
         r.id = a.id[i];
         for (int q = 0; q < 5; ++q) r.pad[q] = 0;
     } else {
-        for (int d = 0; d < 3; ++d) {
-            r.X[d] = a.X[d * n + i];
-            r.q0[d] = a.q0f[d * n + i];
-            r.dq[d] = a.dqf[d * n + i];
+        for (int d = 0; d < 3; ++d) r.X[d] = a.X[d * n + i];
+        if (pre_transform) {
+            // the three FP64 sampled momenta, bit for bit, in the six 32-bit momentum slots
+            uint32_t w[6];
+            for (int d = 0; d < 3; ++d) {
+                const double v = a.qs[d * n + i];
+                w[2 * d] = (uint32_t)__double2loint(v);
+                w[2 * d + 1] = (uint32_t)__double2hiint(v);
+            }
+            for (int d = 0; d < 3; ++d) {
+                r.q0[d] = __uint_as_float(w[d]);
+                r.dq[d] = __uint_as_float(w[3 + d]);
+            }
+        } else {
+            for (int d = 0; d < 3; ++d) {
+                r.q0[d] = a.q0f[d * n + i];
+                r.dq[d] = a.dqf[d * n + i];
+            }
         }
         r.id = a.id[i];
         r.pmag = a.pmag[i];
@@ -231,7 +249,8 @@ constexpr int kPackU = 2;
 
 template <int Prec>
 __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t n, const uint32_t* __restrict__ key,
-                                                        uint32_t* __restrict__ offset, void* __restrict__ recs)
+                                                        uint32_t* __restrict__ offset, void* __restrict__ recs,
+                                                        int pre_transform)
 {
     using Rec = typename RecOf<Prec>::T;
     // Grid-stride loop with a warp-uniform trip count, so that every lane can take
@@ -252,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t
             live[u] = idx[u] < n;
             k[u] = live[u] ? key[idx[u]] : 0u;
             base[u] = 0u;
-            if (live[u]) make_rec<Prec>(a, n, idx[u], r[u]);
+            if (live[u]) make_rec<Prec>(a, n, idx[u], r[u], pre_transform != 0);
         }
 #pragma unroll
         for (int u = 0; u < kPackU; ++u) {
@@ -277,7 +296,8 @@ __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t
 }
 
 template <int Prec>
-__global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64_t n, const void* __restrict__ recs)
+__global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64_t n, const void* __restrict__ recs,
+                                                          int pre_transform)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         if constexpr (Prec == FDF_PREC_F64) {
@@ -292,10 +312,21 @@ __global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64
             b.id[j] = r.id;
         } else {
             const SplitRec r = load_split(recs, j);
-            for (int d = 0; d < 3; ++d) {
-                b.X[d * n + j] = r.X[d];
-                b.q0f[d * n + j] = r.q0[d];
-                b.dqf[d * n + j] = r.dq[d];
+            for (int d = 0; d < 3; ++d) b.X[d * n + j] = r.X[d];
+            if (pre_transform) {
+                // the sampled momenta (one array shared by both halves: the pack kernel
+                // has read all of it before this kernel writes)
+                uint32_t w[6];
+                for (int d = 0; d < 3; ++d) {
+                    w[d] = __float_as_uint(r.q0[d]);
+                    w[3 + d] = __float_as_uint(r.dq[d]);
+                }
+                for (int d = 0; d < 3; ++d) b.qs[d * n + j] = __hiloint2double((int)w[2 * d + 1], (int)w[2 * d]);
+            } else {
+                for (int d = 0; d < 3; ++d) {
+                    b.q0f[d * n + j] = r.q0[d];
+                    b.dqf[d * n + j] = r.dq[d];
+                }
             }
             b.id[j] = r.id;
             b.pmag[j] = r.pmag;
@@ -397,11 +428,11 @@ cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, c
     e = scan_exclusive(s, hist, bins, bsum);
     if (e != cudaSuccess) return e;
     if (precision == FDF_PREC_F64) {
-        k_sort_pack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, key, hist, recs);
-        k_sort_unpack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(b, n, recs);
+        k_sort_pack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, key, hist, recs, 0);
+        k_sort_unpack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(b, n, recs, 0);
     } else {
-        k_sort_pack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, key, hist, recs);
-        k_sort_unpack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(b, n, recs);
+        k_sort_pack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, key, hist, recs, lead.pre_transform);
+        k_sort_unpack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(b, n, recs, lead.pre_transform);
     }
     return cudaGetLastError();
 }
