@@ -321,7 +321,8 @@ FDF_API void fdf_destroy(fdf_ctx* c);
  * stated tolerances): sort_cells, sort_tile and steps_per_pass.  It times whole
  * runs (fdf_sample + fdf_step(n_steps)) of p on the device, one knob at a time
  * (coordinate descent over sort_cells in {2, 4, 8}, sort_tile in {0, 1, 2},
- * steps_per_pass in {2, 3, 4}), starting from the automatic choices, and writes
+ * steps_per_pass in {2, 3, 4}, then sort_cells again in {3, 5, 6}), starting from
+ * the automatic choices, and writes
  * the fastest parameter set to *out (p with the three knobs set).  The paper
  * has no counterpart.  stream: a cudaStream_t or NULL; every trial allocates
  * and frees its own context.  ms (may be NULL) receives the best run time;
