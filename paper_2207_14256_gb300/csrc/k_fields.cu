@@ -363,16 +363,31 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
     const T kx = kf * (T)nx, ky = kf * (T)ny;
     const size_t NN = (size_t)N * N;
     V Rv[N1];
-    sfor<N1>([&](auto I) {
-        const int z = N2 * I + t;
-        const int nz = sidx(z, N);
-        Rv[I] = R[(size_t)z * NN + (size_t)jy * N + x0 + xo];
-        T ap = T(0), af = T(0), ad = T(0);
-        if (nx != h && ny != h && nz != h) amp_entry(A, nx * nx + ny * ny + nz * nz, ap, af, ad);
-        As[(0 * N1 + I) * NT + threadIdx.x] = ap;
-        As[(1 * N1 + I) * NT + threadIdx.x] = af;
-        As[(2 * N1 + I) * NT + threadIdx.x] = ad;
-    });
+    sfor<N1>([&](auto I) { Rv[I] = R[(size_t)(N2 * I + t) * NN + (size_t)jy * N + x0 + xo]; });
+    // The amplitudes depend on |n|^2 only, so the modes nz and -nz of a column share
+    // them.  Mode z = N2 I + t mirrors to z' = N - z: for t > 0 that is thread N2 - t,
+    // index N1 - 1 - I; for t = 0 it is thread 0, index (N1 - I) mod N1.  Each thread
+    // looks up the first half of its modes (t = 0 also I = N1/2) and writes the
+    // amplitudes into its own column and into its mirror partner's.
+    {
+        const int tp = t == 0 ? 0 : N2 - t;
+        const int partner = xo + TX * tp;
+        sfor<N1 / 2 + 1>([&](auto I) {
+            if (I < N1 / 2 || t == 0) {
+                const int z = N2 * I + t;
+                const int nz = sidx(z, N);
+                const int Ip = t == 0 ? (N1 - I) % N1 : N1 - 1 - I;
+                T ap = T(0), af = T(0), ad = T(0);
+                if (nx != h && ny != h && nz != h) amp_entry(A, nx * nx + ny * ny + nz * nz, ap, af, ad);
+                As[(0 * N1 + I) * NT + threadIdx.x] = ap;
+                As[(1 * N1 + I) * NT + threadIdx.x] = af;
+                As[(2 * N1 + I) * NT + threadIdx.x] = ad;
+                As[(0 * N1 + Ip) * NT + partner] = ap;
+                As[(1 * N1 + Ip) * NT + partner] = af;
+                As[(2 * N1 + Ip) * NT + partner] = ad;
+            }
+        });
+    }
     __syncthreads();
     const size_t N3 = NN * N;
 #pragma unroll 1
