@@ -139,3 +139,25 @@ def test_create_rejects_bad_tables_before_touching_the_device(fdf, inputs, c1_ta
     with pytest.raises(fdf.FdfError) as e:
         fdf.fdf_create(P, T)
     assert e.value.code == fdf.FDF_EINVAL
+
+
+def test_binding_constants_match_the_header(fdf):
+    """Every integer #define of include/fdf.h that the binding defines has the same
+    value there, and every entry point the header declares is bound with that name."""
+    src = open(os.path.join(ROOT, "include", "fdf.h")).read()
+    defines = {}
+    for name, val in re.findall(r"^#define (FDF_\w+)\s+\(?(-?\d+)\)?", src, re.M):
+        defines[name] = int(val)
+    assert len(defines) >= 30
+    checked = 0
+    for name, val in defines.items():
+        if hasattr(fdf, name):
+            assert getattr(fdf, name) == val, name
+            checked += 1
+    # the codes, forms, quantities, equations of motion and kernel classes are all mirrored
+    for prefix in ("FDF_E", "FDF_PREC_", "FDF_Q_", "FDF_EOM_", "FDF_K_PUSH", "FDF_REQ_"):
+        names = [n for n in defines if n.startswith(prefix)]
+        assert names and all(hasattr(fdf, n) for n in names), prefix
+    assert checked >= 30
+    for name in declared_symbols():
+        assert hasattr(fdf, name), name
