@@ -250,8 +250,10 @@ FDF_API int fdf_deposit_subset(fdf_ctx* c, int32_t species, int32_t quantity, in
                                int32_t out_on_device);
 
 /* Current state of one species in particle-index order: x[3][n_part] (Mpc,
- * in [0, L)), q[3][n_part] (eV), w[n_part] (delta-f weight, Sec. 2.2).  Any
- * output pointer may be NULL.  Device or host memory per out_on_device. */
+ * in [0, L)), q[3][n_part] (eV), w[n_part] (delta-f weight, Sec. 2.2:
+ * w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)); the split forms take p - |q| in
+ * FP64 and the rest in FP32, as their deposit does).  Any output pointer may be
+ * NULL.  Device or host memory per out_on_device; synchronises the stream. */
 FDF_API int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_t out_on_device);
 
 /* The pre-initial draw of one species before the momentum transform:
