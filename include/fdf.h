@@ -70,6 +70,11 @@ extern "C" {
 
 /* ---- flags (fdf_params.flags) -------------------------------------------- */
 #define FDF_FLAG_FIXED_AMPLITUDE 1  /* |R_k| = sqrt(P(k)/V), random phase ("fixed" ICs, Sec. 4) */
+/* The dipole term of eq:transform times 3, the factor 2l+1 of the paper's Legendre
+ * convention (eq:def2) that eq:pre_int and eq:transform do not print.  As printed
+ * (the default) the transform's delta-f energy flux is (rho + P) theta / 3 with
+ * theta = k^2 tau psi / 2; with this flag it is (rho + P) theta. */
+#define FDF_FLAG_LEGENDRE_DIPOLE 2
 
 /* ---- deposit quantities (fdf_deposit) ------------------------------------ */
 #define FDF_Q_W_EPS 0  /* w_k eps_k: the delta-f energy density of eq:empirical_rho */

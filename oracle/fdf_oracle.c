@@ -716,6 +716,12 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
     const double a0 = exp(or_lna(p, 0.0));
     const double tau0 = or_tau(p, a0);
     const double L = p->box;
+    /* eq:transform with nu = 4, omega = 4/3: 1 + delta/nu = 1 - psi/2 and
+     * (omega eps/nu) grad(nabla^-2 theta) = (eps/3)(-tau0/2) grad psi = -(eps tau0/6) grad psi.
+     * The paper expands Psi in Legendre terms with the factor 2l+1 (eq:def2), which
+     * puts a factor 3 on the dipole that eq:pre_int and eq:transform do not print;
+     * flag bit 1 takes that reading (the dipole then carries the flux theta). */
+    const double dip = (p->flags & OR_FLAG_LEGENDRE_DIPOLE) ? 3.0 : 1.0;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double xi[3], g[8];
@@ -724,7 +730,7 @@ int or_initial(const or_params* p, const or_tables* t, const double* frozen, con
         double m = mass_of(p, gidx[i]);
         double eps = sqrt(pmag[i] * pmag[i] + m * m * a0 * a0);
         for (int d = 0; d < 3; ++d) {
-            double qd = qs[d * n + i] * (1.0 - g[7] / 2.0) - (eps * tau0 / 6.0) * g[d];
+            double qd = qs[d * n + i] * (1.0 - g[7] / 2.0) - dip * (eps * tau0 / 6.0) * g[d];
             x[d * n + i] = xi[d];
             q[d * n + i] = qd;
             q0[d * n + i] = qd;

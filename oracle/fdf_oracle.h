@@ -26,7 +26,8 @@ typedef struct {
     double   T_K;          /* present-day neutrino temperature, K (paper: 1.95) */
     double   z_start, z_end;
     int32_t  n_steps;
-    int32_t  flags;        /* bit 0: fixed amplitudes (|R| = sqrt(P/V)) */
+    int32_t  flags;        /* bit 0: fixed amplitudes (|R| = sqrt(P/V)); bit 1: the dipole term of
+                              eq:transform with the factor 2l+1 = 3 of eq:def2 */
     uint64_t seed;
     double   h, omega_m, omega_r;   /* Omega_Lambda = 1 - omega_m - omega_r */
     double   A_s, n_s, k_pivot;
@@ -57,5 +58,6 @@ typedef struct {
 } or_tables;
 
 #define OR_FLAG_FIXED_AMPLITUDE 1
+#define OR_FLAG_LEGENDRE_DIPOLE 2
 
 #endif

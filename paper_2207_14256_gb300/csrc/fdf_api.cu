@@ -219,6 +219,7 @@ int fdf::validate_params(const fdf_params* p)
     const double a0 = 1.0 / (1.0 + p->z_start);
     if (!(p->omega_r / (a0 * a0 * a0 * a0) + p->omega_m / (a0 * a0 * a0) + ol > 0))
         return fail(FDF_EINVAL, "H^2 <= 0 at z_start");
+    if (p->flags & ~(FDF_FLAG_FIXED_AMPLITUDE | FDF_FLAG_LEGENDRE_DIPOLE)) return fail(FDF_EINVAL, "unknown flags");
     if (p->sort_every < -1) return fail(FDF_EINVAL, "sort_every must be -1, 0 or a step count");
     if (p->steps_per_pass < 0 || p->steps_per_pass > kMaxSub - 1)
         return fail(FDF_EINVAL, "steps_per_pass must be 0 (automatic) or 1..4");
@@ -1009,9 +1010,11 @@ int sample_enqueue(fdf_ctx* c)
     if (rc) return rc;
     rc = acquire_grid(c, b0);
     if (rc) return rc;
+    // the dipole term's factor: tau0 as printed, 3 tau0 with the Legendre convention's 2l+1
+    const double tau_dip = (c->p.flags & FDF_FLAG_LEGENDRE_DIPOLE) ? 3.0 * c->tau0 : c->tau0;
     rc = timed(c, FDF_K_OTHER, "initial transform", [&] {
         return launch_initial(c->stream, c->p.precision, c->st, c->n, c->p.n_part > 0 ? c->p.n_part : 1,
-                              c->p.m_ev, c->a0, c->tau0, c->p.interp_order == 2 ? 2 : 1, c->p.n_grid,
+                              c->p.m_ev, c->a0, tau_dip, c->p.interp_order == 2 ? 2 : 1, c->p.n_grid,
                               c->p.box_mpc, G0);
     });
     if (rc) return rc;

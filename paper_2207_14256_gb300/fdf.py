@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfdf.so")
 
 FDF_OK, FDF_EINVAL, FDF_ENOMEM, FDF_ECUDA, FDF_ESTATE, FDF_ETIMEOUT, FDF_ENAN, FDF_ENOSYS = 0, -1, -2, -3, -4, -5, -6, -7
 FDF_PREC_F64, FDF_PREC_F32, FDF_PREC_BF16 = 0, 1, 2
-FDF_FLAG_FIXED_AMPLITUDE = 1
+FDF_FLAG_FIXED_AMPLITUDE, FDF_FLAG_LEGENDRE_DIPOLE = 1, 2
 FDF_Q_W_EPS, FDF_Q_W, FDF_Q_EPS, FDF_Q_COUNT, FDF_Q_W_QX, FDF_Q_W_QY, FDF_Q_W_QZ = 0, 1, 2, 3, 4, 5, 6
 FDF_EOM_GEODESIC, FDF_EOM_CANONICAL, FDF_EOM_SR_NEWTON, FDF_EOM_Q_SIMPLE, FDF_EOM_NEWTONIAN = 0, 1, 2, 3, 4
 FDF_EOM_EXACT = 5
