@@ -57,16 +57,32 @@ extern "C" {
 /* ---- precision forms (fdf_params.precision) ------------------------------ */
 /* FDF_PREC_F64: the plain form.  Grids, FFTs, positions, momenta and all
  *   arithmetic in FP64 (positions as FP64 Mpc, wrapped with floor).
- * FDF_PREC_F32: the split form.  Grid build, FFT and gradient storage in FP32;
- *   positions as 32-bit fixed-point fractions of the box (resolution
- *   L / 2^32, periodic wrap exact by integer overflow); momenta as
- *   q = q_0 + dq with q_0 and dq in FP32 (|dq| << |q|); the per-step drift
- *   integral evaluated in float-float (about 44-bit mantissa) on the FP32
- *   pipe; kick integrals in FP32.
- * FDF_PREC_BF16: the split form with BF16 gradient-grid storage. */
-#define FDF_PREC_F64  0
-#define FDF_PREC_F32  1
-#define FDF_PREC_BF16 2
+ * FDF_PREC_F32: FP32 grid build, FFT and gradient storage with FP32
+ *   interpolation, and an FP64 phase-space state: positions (Mpc) and momenta
+ *   (eV) are stored and accumulated in FP64, and the step integrals are
+ *   evaluated in FP64 -- the drift's int dtau / eps and the kick's
+ *   int eps_0 dtau and int dtau / eps_0 (eq:discrete_drift, eq:releq_approx).
+ *   Each integral is r_c sum_k C_k t^k, a series about the interval's centre in
+ *   t = m^2 a_c^2 r_c^2 with r_c = (|q|^2 + m^2 a_c^2)^(-1/2) and FP64
+ *   coefficients from the host; r_c, t and the leading terms (six for the drift,
+ *   three for a kick) are FP64, and the terms beyond them, which add less than
+ *   1e-7 of the integral at the workloads' step sizes, are FP32.  The kick
+ *   itself (a change of at most ~1e-3 of |q| per step) is formed in FP32 from
+ *   the FP32 gradients and q_0 (stored in FP32) and added to q in FP64.
+ * FDF_PREC_BF16: FDF_PREC_F32 with BF16 gradient-grid storage (FP32
+ *   interpolation, the same FP64 state and integrals).
+ * FDF_PREC_F32_FIXED: the split-state form.  FP32 grids as FDF_PREC_F32;
+ *   positions as 32-bit fixed-point fractions of the box (resolution L / 2^32,
+ *   periodic wrap exact by integer overflow); momenta as q = q_0 + dq with q_0
+ *   and dq in FP32 (|dq| << |q|); the drift integral in float-float (about
+ *   44-bit mantissa) on the FP32 pipe; kick integrals in FP32.  No FP64
+ *   instruction runs in its particle pass.
+ * FDF_PREC_BF16_FIXED: the split-state form with BF16 gradient-grid storage. */
+#define FDF_PREC_F64        0
+#define FDF_PREC_F32        1
+#define FDF_PREC_BF16       2
+#define FDF_PREC_F32_FIXED  3
+#define FDF_PREC_BF16_FIXED 4
 
 /* ---- flags (fdf_params.flags) -------------------------------------------- */
 #define FDF_FLAG_FIXED_AMPLITUDE 1  /* |R_k| = sqrt(P(k)/V), random phase ("fixed" ICs, Sec. 4) */
@@ -123,8 +139,8 @@ typedef struct fdf_params {
                                   sort exceeds sort_cells cells; k > 0 = every k steps; -1 = never
                                   (always after sampling unless -1) */
     int32_t  steps_per_pass;   /* leapfrog steps per particle pass, 1..4: the particle state is
-                                  read and written once per pass (0 = 4 for the split forms,
-                                  1 for the plain FP64 form) */
+                                  read and written once per pass (0 = 4 for the FP32/BF16-grid
+                                  forms, 1 for the plain FP64 form) */
     int32_t  sort_tile;        /* sort buckets are cubes of 2^sort_tile cells per axis, 0..3
                                   (0 = single cells) */
     int32_t  sort_cells;       /* with sort_every = 0: re-bucket when the typical particle has
@@ -256,8 +272,8 @@ FDF_API int fdf_deposit_subset(fdf_ctx* c, int32_t species, int32_t quantity, in
 
 /* Current state of one species in particle-index order: x[3][n_part] (Mpc,
  * in [0, L)), q[3][n_part] (eV), w[n_part] (delta-f weight, Sec. 2.2:
- * w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)); the split forms take p - |q| in
- * FP64 and the rest in FP32, as their deposit does).  Any output pointer may be
+ * w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)); the FP32/BF16-grid forms take
+ * p - |q| in FP64 and the rest in FP32, as their deposit does).  Any output pointer may be
  * NULL.  Device or host memory per out_on_device; synchronises the stream. */
 FDF_API int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_t out_on_device);
 
@@ -315,6 +331,16 @@ FDF_API int fdf_state(fdf_ctx* c, int32_t* step, double* lna);
 FDF_API int fdf_timing(fdf_ctx* c, int32_t enable);
 FDF_API int fdf_kernel_time(fdf_ctx* c, int32_t which, double* ms, int64_t* launches);
 
+/* Issue rates of the arithmetic pipes the particle pass uses, measured on the
+ * current device (the denominators of the passes' FP64-pipe roofline): dependent
+ * FP64 fused multiply-adds per second (*dfma_per_s; 2 flops each), FP32 fused
+ * multiply-adds per second (*ffma_per_s), and FP64 -> FP32 -> FP64 conversion
+ * round trips per second (*cvt_per_s, two conversions each).  Each is the best of
+ * five timed launches (CUDA events on stream, a cudaStream_t or NULL) of every SM
+ * holding 64 warps with 8 independent chains per thread.  The paper has no
+ * counterpart.  Any pointer may be NULL; changes no device setting. */
+FDF_API int fdf_pipe_rates(void* stream, double* dfma_per_s, double* ffma_per_s, double* cvt_per_s);
+
 /* Number of kernels this context has launched since creation. */
 FDF_API int64_t fdf_launch_count(const fdf_ctx* c);
 
@@ -333,7 +359,7 @@ FDF_API void fdf_destroy(fdf_ctx* c);
  * the fastest parameter set to *out (p with the three knobs set).  The paper
  * has no counterpart.  stream: a cudaStream_t or NULL; every trial allocates
  * and frees its own context.  ms (may be NULL) receives the best run time;
- * trials (may be NULL) the number of timed runs.  Only split forms are tuned;
+ * trials (may be NULL) the number of timed runs.  Only the FP32/BF16-grid forms are tuned;
  * for FDF_PREC_F64 *out = *p. */
 FDF_API int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, fdf_params* out, double* ms,
                      int32_t* trials);

@@ -76,6 +76,52 @@ __device__ __forceinline__ FF ff_rsqrt(FF s)
     return r;
 }
 
+// ---- FP64 <-> FP32 on the integer pipe ---------------------------------------
+// GB300 converts between FP64 and FP32 at its FP64 rate (two per clock per SM, the
+// rate of its FMAs), so the FP64-state particle pass converts with bit operations,
+// which run on the integer pipe.  Both follow the IEEE-754 binary64 and binary32
+// layouts (sign, biased exponent, fraction; the biases differ by 1023 - 127 = 896).
+//
+// d2f_bits: a double in the FP32 normal range (or a value below 2^-126 in
+// magnitude, returned as a signed zero) to the nearest float, ties away from zero.
+__device__ __forceinline__ float d2f_bits(double d)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const uint32_t sign = hi & 0x80000000u, mag = hi & 0x7FFFFFFFu;
+    // exponent rebias (896 << 20 in the high word, then << 3 into binary32's field),
+    // the top 23 fraction bits, and the next bit to round; a carry out of the fraction
+    // moves into the exponent, as it must
+    uint32_t f = (((mag - 0x38000000u) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+    f = mag < 0x38100000u ? 0u : f;
+    return __uint_as_float(sign | f);
+}
+
+// f2d_bits: a float (normal or zero; subnormals flush to zero) to the equal double.
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t mag = b & 0x7FFFFFFFu;
+    const uint32_t hi = mag < 0x00800000u ? (b & 0x80000000u) : (((mag >> 3) + 0x38000000u) | (b & 0x80000000u));
+    const uint32_t lo = mag < 0x00800000u ? 0u : (b << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// 1/sqrt(u) for u > 0 in the FP32 normal range, to FP64 accuracy with four FP64
+// instructions: the FP32 hardware estimate y (relative error below ~2^-21) and one
+// Newton-Raphson step for u^(-1/2) taken to second order,
+//   r = y (1 + e/2 + 3 e^2 / 8),  e = 1 - u y^2,
+// whose error is 5 e^3 / 16 (below 2^-62).  e/2 = 1/2 - u y (y/2) is formed with one
+// fused multiply-add in FP64; 3 e^2 / 8 (below 2^-40) is formed in FP32.
+__device__ __forceinline__ double rsqrt_fp64(double u)
+{
+    const float yf = rsqrtf(d2f_bits(u));
+    const double y = f2d_bits(yf), yh = f2d_bits(0.5f * yf);
+    const double eh = fma(-(u * y), yh, 0.5);                 // e/2
+    const float ehf = d2f_bits(eh);
+    const double s = eh + f2d_bits(1.5f * ehf * ehf);         // e/2 + 3 e^2 / 8
+    return fma(y, s, y);
+}
+
 // ---- complex ----
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {

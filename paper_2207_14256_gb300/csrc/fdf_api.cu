@@ -15,6 +15,8 @@
 #include <cstring>
 #include <algorithm>
 #include <climits>
+#include <map>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -45,9 +47,15 @@ int ilog2(int v)
     return r;
 }
 
-size_t grid_bytes_per_cell(int prec) { return prec == FDF_PREC_F64 ? 64 : (prec == FDF_PREC_F32 ? 32 : 16); }
-size_t complex_bytes(int prec) { return prec == FDF_PREC_F64 ? 16 : 8; }
-size_t real_bytes(int prec) { return prec == FDF_PREC_F64 ? 8 : 4; }
+// storage of the grids by precision setting (the FP64-state and split-state forms
+// share their grids' storage)
+size_t grid_bytes_per_cell(int prec)
+{
+    const int g = grid_prec(prec);
+    return g == FDF_PREC_F64 ? 64 : (g == FDF_PREC_F32 ? 32 : 16);
+}
+size_t complex_bytes(int prec) { return grid_prec(prec) == FDF_PREC_F64 ? 16 : 8; }
+size_t real_bytes(int prec) { return grid_prec(prec) == FDF_PREC_F64 ? 8 : 4; }
 
 // Gauss-Legendre rule on [-1, 1] by Newton's method on P_n, with
 // P_n' = n (x P_n - P_{n-1}) / (x^2 - 1).
@@ -93,6 +101,81 @@ int auto_nodes(double dlna)
     return n;
 }
 
+// ---- the FP64-state form's step integrals as polynomials (WideCoef) ---------------
+// g(t) = sum_j W_j (1 + e_j t)^power on t in [0, 1] (power -1/2 or +1/2), interpolated at
+// the Chebyshev points of [0, 1] and written as monomial coefficients in t.  The degree
+// is the smallest in [max(nf64, 3), kWideDeg] for which the polynomial agrees with the sum
+// within `tol` of max |g| at 65 points of [0, 1] after the device's split (the first
+// nf64 coefficients in FP64, the rest rounded to FP32), with the FP32 Horner sum's
+// rounding bounded by sum_{k >= nf64} |a_k| 4 2^-24 added.  Returns false (the pass
+// then integrates node by node) if no degree does.
+bool fit_wide_poly(const double* W, const double* e, int n, double power, int nf64, double tol, WidePoly& P)
+{
+    std::memset(&P, 0, sizeof(P));
+    auto g = [&](long double t) {
+        long double v = 0;
+        for (int j = 0; j < n; ++j) {
+            const double b = std::sqrt(1.0 + e[j] * (double)t);
+            v += (long double)W[j] * (power < 0 ? 1.0L / b : (long double)b);
+        }
+        return v;
+    };
+    constexpr int kCheck = 64;   // check points t = i / kCheck
+    long double gmax = 0;
+    for (int i = 0; i <= kCheck; ++i) gmax = std::max(gmax, std::fabs(g((long double)i / kCheck)));
+    if (gmax == 0) return true;
+    for (int K = std::max(nf64, 3); K <= kWideDeg; ++K) {
+        // Chebyshev coefficients of g(t(s)), s = 2t - 1, from its values at the K + 1 points
+        long double cc[kWideDeg + 1] = {};
+        long double gv[kWideDeg + 1];
+        for (int i = 0; i <= K; ++i) {
+            const long double th = 3.14159265358979323846264338327950288L * (i + 0.5L) / (K + 1);
+            gv[i] = g((1.0L + std::cos(th)) / 2);
+        }
+        for (int m = 0; m <= K; ++m) {
+            long double acc = 0;
+            for (int i = 0; i <= K; ++i)
+                acc += gv[i] * std::cos(3.14159265358979323846264338327950288L * m * (i + 0.5L) / (K + 1));
+            cc[m] = acc * 2 / (K + 1);
+        }
+        cc[0] /= 2;
+        // T_m(2t - 1) as polynomials in t: T_0 = 1, T_1 = 2t - 1, T_{m+1} = 2 (2t - 1) T_m - T_{m-1}
+        long double Tm1[kWideDeg + 2] = {}, Tm[kWideDeg + 2] = {}, a[kWideDeg + 1] = {};
+        Tm1[0] = 1;
+        Tm[0] = -1;
+        Tm[1] = 2;
+        a[0] += cc[0];
+        for (int m = 1; m <= K; ++m) {
+            for (int k = 0; k <= m; ++k) a[k] += cc[m] * Tm[k];
+            long double Tn[kWideDeg + 2] = {};
+            for (int k = 0; k <= m; ++k) {
+                Tn[k + 1] += 4 * Tm[k];
+                Tn[k] -= 2 * Tm[k];
+            }
+            for (int k = 0; k <= m + 1; ++k) Tn[k] -= Tm1[k];
+            std::memcpy(Tm1, Tm, sizeof(Tm));
+            std::memcpy(Tm, Tn, sizeof(Tn));
+        }
+        // the device's evaluation: FP64 coefficients below nf64, FP32 ones above
+        long double tail = 0;
+        for (int k = nf64; k <= K; ++k) tail += std::fabs(a[k]);
+        const long double tail_bound = tail * 4 * 5.9604644775390625e-8L;
+        long double err = 0;
+        for (int i = 0; i <= kCheck; ++i) {
+            const long double t = (long double)i / kCheck;
+            long double pt = 0;
+            for (int k = K; k >= 0; --k) pt = pt * t + (k < nf64 ? (long double)(double)a[k] : (long double)(float)a[k]);
+            err = std::max(err, std::fabs(pt - g(t)));
+        }
+        if ((err + tail_bound) <= tol * gmax) {
+            for (int k = 0; k < nf64; ++k) P.c64[k] = (double)a[k];
+            for (int k = nf64; k <= K; ++k) P.c32[k - nf64] = (float)a[k];
+            return true;
+        }
+    }
+    return false;
+}
+
 FF split_ff(double v)
 {
     FF r;
@@ -110,7 +193,7 @@ struct StateLayout {
 int steps_per_pass(const fdf_params& p)
 {
     if (p.steps_per_pass > 0) return p.steps_per_pass;
-    return p.precision == FDF_PREC_F64 ? 1 : kMaxSub - 1;
+    return form_of(p.precision) == kPlain ? 1 : kMaxSub - 1;
 }
 
 // Grids held at once: the current pass's (its steps plus the opening kick's) and
@@ -155,7 +238,8 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     for (int b = 0; b < L.nbuf; ++b) L.G[b] = take(N3 * grid_bytes_per_cell(prec));
     // the two super-step grids an interpolated step reads (super-steps only)
     for (int b = 0; b < 2; ++b) L.Gss[b] = take(p.superstep_tol > 0 ? N3 * grid_bytes_per_cell(prec) : 0);
-    const bool split = prec != FDF_PREC_F64;
+    const int form = form_of(prec);
+    const bool split = form != kPlain;     // sorts the sampler's output before the transform
     const bool sorts = p.sort_every >= 0;
     for (int h = 0; h < (sorts ? 2 : 1); ++h) {
         StateLayout& S = L.s[h];
@@ -163,10 +247,10 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
         // positions are written once and never permuted, so they are not doubled
         S.X = (h == 0 || split) ? take(3 * n * 4) : L.s[0].X;
         S.q0f = take(split ? 3 * n * 4 : 0);
-        S.dqf = take(split ? 3 * n * 4 : 0);
-        S.xd = take(split ? 0 : 3 * n * 8);
-        S.qd = take(split ? 0 : 3 * n * 8);
-        S.q0d = take(split ? 0 : 3 * n * 8);
+        S.dqf = take(form == kFixed ? 3 * n * 4 : 0);
+        S.xd = take(form != kFixed ? 3 * n * 8 : 0);
+        S.qd = take(form != kFixed ? 3 * n * 8 : 0);
+        S.q0d = take(form == kPlain ? 3 * n * 8 : 0);
         // 1 + phi + psi's phi + psi at each particle, carried from a kick to the next
         // drift (the exact equations of motion only)
         S.sd = take(p.eom == FDF_EOM_EXACT ? n * 8 : 0);
@@ -210,7 +294,7 @@ int fdf::validate_params(const fdf_params* p)
     if (!(p->z_start > p->z_end) || !(p->z_end > -1.0) || !std::isfinite(p->z_start))
         return fail(FDF_EINVAL, "need z_start > z_end > -1");
     if (p->n_steps < 1) return fail(FDF_EINVAL, "n_steps must be >= 1");
-    if (p->precision < FDF_PREC_F64 || p->precision > FDF_PREC_BF16) return fail(FDF_EINVAL, "unknown precision");
+    if (p->precision < FDF_PREC_F64 || p->precision > FDF_PREC_BF16_FIXED) return fail(FDF_EINVAL, "unknown precision");
     if (p->n_gl != 0 && (p->n_gl < 2 || p->n_gl > kMaxGL)) return fail(FDF_EINVAL, "n_gl must be 0 or 2..8");
     if (!(p->h > 0) || !(p->omega_m >= 0) || !(p->omega_r >= 0) || !(p->A_s > 0) || !(p->k_pivot > 0) ||
         !std::isfinite(p->n_s))
@@ -237,6 +321,14 @@ int fdf::validate_params(const fdf_params* p)
     if (p->eom == FDF_EOM_EXACT && p->steps_per_pass > 2)
         return fail(FDF_EINVAL, "steps_per_pass must be 0, 1 or 2 with FDF_EOM_EXACT");
     return FDF_OK;
+}
+
+void fdf::twiddle_table(int N, double* cs)
+{
+    for (int j = 0; j < N; ++j) {
+        cs[2 * j] = std::cos(2.0 * kPi * j / N);
+        cs[2 * j + 1] = std::sin(2.0 * kPi * j / N);
+    }
 }
 
 bool fdf::uniform_grid(const double* v, int n, double* v0, double* dv)
@@ -272,6 +364,9 @@ struct fdf_ctx {
     void* Gss[2] = {nullptr, nullptr};
     int ssk[2] = {-1, -1};            // the step each super-step grid holds
     double lnk0 = 0, dlnk = 0, lnat0 = 0, dlnat = 0;
+    // fitted integral polynomials of the FP64-state form by interval (ln a ends) and
+    // kind (0 drift, 1 kick 1/eps, 2 kick eps), with whether the fit passed
+    std::map<std::tuple<double, double, int>, std::pair<bool, WidePoly>> wide_fits;
     Layout lay{};
     char* block = nullptr;
     bool own_block = false;
@@ -429,6 +524,8 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.uniform_species = c->uniform;
     a.order = c->p.interp_order == 2 ? 2 : 1;
     a.eom = c->p.eom;
+    a.wide_series = 1;
+    for (int s = 0; s < kMaxSpecies; ++s) a.m2[s] = c->p.m_ev[s] * c->p.m_ev[s];
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
     a.invL = 1.0 / c->p.box_mpc;
@@ -436,9 +533,47 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.fx_scale = split_ff(4294967296.0 / c->p.box_mpc);
 }
 
+// The FP64-state form's coefficients of a sub-step (WideCoef): for each interval, the
+// centre a_c (midpoint in ln a), e_j = a_j^2 / a_c^2 - 1 and the fitted polynomials.
+// Drift integrals are fitted to 2e-13 of their size, kick integrals (which only scale a
+// kick of at most ~1e-3 of |q|) to 1e-9.  u.wide_ok = 0 if a fit failed.
+void fill_wide(fdf_ctx* c, bool drift, double d1, double d2, const double* Wd, const double* ad, bool kick,
+               double k1, double k2, const double* Wk, const double* ak, SubStep& u)
+{
+    WideCoef& w = u.wide;
+    u.wide_ok = 1;
+    auto fit = [&](double l1, double l2, int kind, const double* W, const double* a2, int n, WidePoly& P) {
+        const auto key = std::make_tuple(l1, l2, kind);
+        auto it = c->wide_fits.find(key);
+        if (it == c->wide_fits.end()) {
+            const double a2c = std::exp(l1 + l2);       // a_c^2 at the midpoint in ln a
+            double e[kMaxGL];
+            for (int j = 0; j < n; ++j) e[j] = a2[j] / a2c - 1.0;
+            WidePoly Q;
+            const bool ok = kind == 0 ? fit_wide_poly(W, e, n, -0.5, kWideD64, 2e-13, Q)
+                                      : fit_wide_poly(W, e, n, kind == 1 ? -0.5 : 0.5, kWideK64, 1e-9, Q);
+            it = c->wide_fits.emplace(key, std::make_pair(ok, Q)).first;
+        }
+        P = it->second.second;
+        if (!it->second.first) u.wide_ok = 0;
+    };
+    if (drift) {
+        w.a2c = std::exp(d1 + d2);
+        fit(d1, d2, 0, Wd, ad, c->ngl, w.drift);
+    }
+    if (kick) {
+        w.a2k = std::exp(k1 + k2);
+        fit(k1, k2, 1, Wk, ak, c->nkick, w.kphi);
+        fit(k1, k2, 2, Wk, ak, c->nkick, w.kpsi);
+        double dt = 0;
+        for (int j = 0; j < c->nkick; ++j) dt += Wk[j];
+        w.dtau_k = (float)dt;
+    }
+}
+
 // Coefficients of one sub-step: drift over [d1, d2] (if any), kick over [k1, k2] (if any).
 // The split form's drift weights carry the factor 2^32/L (position quanta per Mpc).
-void fill_substep(const fdf_ctx* c, bool drift, double d1, double d2, bool kick, double k1, double k2, SubStep& u)
+void fill_substep(fdf_ctx* c, bool drift, double d1, double d2, bool kick, double k1, double k2, SubStep& u)
 {
     std::memset(&u, 0, sizeof(u));
     u.do_drift = drift;
@@ -493,6 +628,7 @@ void fill_substep(const fdf_ctx* c, bool drift, double d1, double d2, bool kick,
             sc.dtau_k_f = (float)dt;
         }
     }
+    if (form_of(c->p.precision) == kWide) fill_wide(c, drift, d1, d2, Wd, ad, kick, k1, k2, Wk, ak, u);
 }
 
 // The unit Gaussian field of the run (a function of the seed and the mesh only),
@@ -501,7 +637,7 @@ int draw_noise(fdf_ctx* c)
 {
     const FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, c->lna0);
     int rc = timed_on(c, c->sf, FDF_K_FIELDS_Z, "noise",
-                      [&] { return launch_noise(c->sf, c->p.precision, a, c->noise); });
+                      [&] { return launch_noise(c->sf, grid_prec(c->p.precision), a, c->noise); });
     if (rc == FDF_OK) c->noise_ready = true;
     return rc;
 }
@@ -517,7 +653,7 @@ int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s, bool sum7)
     }
     FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
     a.slot7_sum = sum7 ? 1 : 0;
-    const int prec = c->p.precision;
+    const int prec = grid_prec(c->p.precision);
     int rc = timed_on(c, s, FDF_K_FIELDS_Z, "mode table",
                       [&] { return launch_mode_table(s, prec, a, c->tabs, c->modeA); });
     if (rc) return rc;
@@ -636,7 +772,8 @@ int produce_grid(fdf_ctx* c, int k, void* G)
     }
     const double w = s == e ? 0.0 : (c->lna(k) - c->lna(s)) / (c->lna(e) - c->lna(s));
     return timed_on(c, c->sf, FDF_K_FIELDS_X, "super-step interpolation", [&] {
-        return launch_interp_grid(c->sf, c->p.precision, c->p.n_grid, c->Gss[slot[0]], c->Gss[slot[1]], w, G);
+        return launch_interp_grid(c->sf, grid_prec(c->p.precision), c->p.n_grid, c->Gss[slot[0]], c->Gss[slot[1]], w,
+                                  G);
     });
 }
 
@@ -714,7 +851,7 @@ int sort_particles(fdf_ctx* c, int dir, bool pre_transform = false)
     if (pre_transform) {
         // split forms right after sampling: by position alone, carrying the sampled momenta
         lead.pre_transform = 1;
-    } else if (c->p.precision != FDF_PREC_F64) {
+    } else if (form_of(c->p.precision) != kPlain) {
         const double l1 = c->lna(c->k), l2 = c->lna(c->k + 0.5 * c->spp * dir);
         double W[kMaxGL], a2[kMaxGL];
         nodes(c, std::min(l1, l2), std::max(l1, l2), W, a2);
@@ -846,7 +983,7 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     c->dlna = (c->lnaN - c->lna0) / p->n_steps;
     if (c->p.n_gl == 0) c->p.n_gl = auto_nodes(c->dlna);
     c->ngl = c->p.n_gl;
-    if (c->p.precision != FDF_PREC_F64) {
+    if (form_of(c->p.precision) == kFixed) {
         // the split form's kick (needed to ~1e-7) takes half the drift's nodes (2 to 4):
         // the error of an n-point rule falls like rho^(-2n), so ceil(n/2) nodes give
         // about the square root of the drift's
@@ -935,10 +1072,7 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     c->Gss[1] = b + L.Gss[1];
     superstep_schedule(c);
     std::vector<double> twd(2 * (size_t)N);
-    for (int j = 0; j < N; ++j) {
-        twd[2 * j] = std::cos(2.0 * kPi * j / N);
-        twd[2 * j + 1] = std::sin(2.0 * kPi * j / N);
-    }
+    twiddle_table(N, twd.data());
     // uploads on the context's stream (not the legacy default stream, which would wait
     // for every other blocking stream of the device), then waited for, since the host
     // buffers belong to the caller
@@ -946,7 +1080,8 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     cudaStream_t s0 = c->stream;
     cudaError_t e = cudaMemcpyAsync(c->tabs, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s0);
     if (e == cudaSuccess) {
-        if (p->precision == FDF_PREC_F64) e = cudaMemcpyAsync(c->tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, s0);
+        if (grid_prec(p->precision) == FDF_PREC_F64)
+            e = cudaMemcpyAsync(c->tw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, s0);
         else e = cudaMemcpyAsync(c->tw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, s0);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->cdf_t, t->cdf_t, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice, s0);
@@ -997,7 +1132,7 @@ int sample_enqueue(fdf_ctx* c)
     // negligible part of a cell in the first pass, so no lead is lost).  The plain form
     // keeps its sampled positions in id order and sorts after the transform.
     const bool sort0 = c->p.sort_every >= 0 && c->n > 0;
-    const bool split = c->p.precision != FDF_PREC_F64;
+    const bool split = form_of(c->p.precision) != kPlain;
     if (sort0 && split) {
         rc = sort_particles(c, 1, true);
         if (rc) return rc;
@@ -1142,8 +1277,10 @@ int fdf_step(fdf_ctx* c, int32_t n)
             c->disp += typical_displacement(c, c->lna(k0), c->lna(k1));
         }
         a.drift_series = 1;
-        for (int u = 0; u < a.nsub; ++u)
+        for (int u = 0; u < a.nsub; ++u) {
             if (a.sub[u].emax > kSeriesMaxE) a.drift_series = 0;
+            if (!a.sub[u].wide_ok) a.wide_series = 0;
+        }
         for (int b : bufs_cur) {
             rc = acquire_grid(c, b);
             if (rc) return rc;
@@ -1427,7 +1564,7 @@ int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device)
     double* dst = out;
     if (!out_on_device) FDF_CUDA(cudaMalloc(&dst, 8 * N3 * 8), "allocating the field copy");
     rc = timed(c, FDF_K_OTHER, "field export",
-               [&] { return launch_fields_to_f64(c->stream, c->p.precision, N, c->G[buf], dst); });
+               [&] { return launch_fields_to_f64(c->stream, grid_prec(c->p.precision), N, c->G[buf], dst); });
     if (!rc && !out_on_device) {
         cudaError_t e = cudaMemcpyAsync(out, dst, 8 * N3 * 8, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1463,7 +1600,7 @@ int fdf_set_fields(fdf_ctx* c, const double* fields, int32_t on_device)
         src = tmp;
     }
     int rc = timed(c, FDF_K_OTHER, "field import",
-                   [&] { return launch_fields_from_f64(c->stream, c->p.precision, N, src, c->Gfrozen); });
+                   [&] { return launch_fields_from_f64(c->stream, grid_prec(c->p.precision), N, src, c->Gfrozen); });
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (tmp) cudaFree(tmp);
     if (rc) return rc;

@@ -9,6 +9,20 @@
 
 namespace fdf {
 
+// The three state forms of the precision settings (FDF_PREC_*): the plain FP64 form,
+// the FP64-state form with FP32 or BF16 grids, and the split-state form with
+// fixed-point positions.
+enum Form { kPlain = 0, kWide = 1, kFixed = 2 };
+__host__ __device__ constexpr int form_of(int prec)
+{
+    return prec == FDF_PREC_F64 ? kPlain : (prec == FDF_PREC_F32 || prec == FDF_PREC_BF16) ? kWide : kFixed;
+}
+// The grid storage of a precision setting: FDF_PREC_F64, FDF_PREC_F32 or FDF_PREC_BF16.
+__host__ __device__ constexpr int grid_prec(int prec)
+{
+    return prec == FDF_PREC_F32_FIXED ? FDF_PREC_F32 : prec == FDF_PREC_BF16_FIXED ? FDF_PREC_BF16 : prec;
+}
+
 constexpr int kMaxGL = 8;       // Gauss-Legendre nodes per step integral
 constexpr int kMaxSpecies = 4;
 constexpr int kSlots = 8;       // d psi (3), d phi (3), phi_dot, psi
@@ -44,13 +58,43 @@ struct SpeciesCoef {
     float dtau_k_f;
 };
 
+// The FP64-state form's step integrals as polynomials.  Over an interval with
+// Gauss-Legendre nodes a_j and weights W_j, centre a_c (the midpoint in ln a) and
+// e_j = a_j^2 / a_c^2 - 1,
+//   sum_j W_j (s + m^2 a_j^2)^(-1/2) = r gm(t),   sum_j W_j (s + m^2 a_j^2)^(1/2) = (u r) gp(t),
+// with u = s + m^2 a_c^2, r = u^(-1/2), t = m^2 a_c^2 / u in [0, 1] and
+// gm(t) = sum_j W_j (1 + e_j t)^(-1/2), gp(t) = sum_j W_j (1 + e_j t)^(1/2).  gm and gp
+// depend on the interval only (not on the mass); the host fits each by a polynomial
+// in t (Chebyshev interpolation on [0, 1], turned into monomial coefficients) and
+// checks it against the sum.  The device takes the first kWideD64 (drift) or
+// kWideK64 (kick) coefficients in FP64 and the rest in FP32.
+constexpr int kWideDeg = 10;    // highest degree of a fitted polynomial
+constexpr int kWideD64 = 5;     // drift terms evaluated in FP64
+constexpr int kWideK64 = 2;     // kick terms evaluated in FP64
+
+struct WidePoly {
+    double c64[kWideD64];       // coefficients 0..kWideD64-1 (FP64)
+    float c32[kWideDeg + 1];    // coefficients kWideD64.. (kick: kWideK64..), FP32, zero-padded
+};
+
+struct WideCoef {
+    double a2c;                 // a_c^2 of the drift interval (m^2 a_c^2 = m^2 a2c)
+    double a2k;                 // a_c^2 of the kick interval
+    WidePoly drift;             // gm of the drift interval
+    WidePoly kphi;              // gm of the kick interval: K_phi = r gm(t)
+    WidePoly kpsi;              // gp of the kick interval: K_psi = u r gp(t)
+    float dtau_k;               // conformal time of the kick interval
+};
+
 // One sub-step of a particle pass: an optional drift over [ln a_k, ln a_k+1] and an
 // optional kick with the grid of the sub-step's end point.
 struct SubStep {
     int do_drift;
     int do_kick;
     double emax;                // largest |e_j| of any species (the series converges for <= 1/4)
+    int wide_ok;                // the FP64-state form's fits of this sub-step passed
     SpeciesCoef sp[kMaxSpecies];
+    WideCoef wide;              // the FP64-state form (species enter through m^2 only)
 };
 
 constexpr double kSeriesMaxE = 0.25;
@@ -67,6 +111,9 @@ struct PushArgs {
     int drift_series;           // the drift corrections of this pass converge as a series
     int order;                  // interpolation order r: 1 cloud-in-cell, 2 TSC
     int eom;                    // FDF_EOM_* (the plain FP64 form)
+    int wide_series;            // the FP64-state form: every fitted polynomial of this pass passed
+                                // its check (else the integrals loop over the nodes)
+    double m2[kMaxSpecies];     // m^2 per species (eV^2)
     int N;                      // grid side
     int nsub;                   // sub-steps in this pass, 1..kMaxSub
     double L, invL, invh;
@@ -103,6 +150,9 @@ inline int ilog2_host(int v)
 int set_error(int code, const char* msg);       // records the message fdf_last_error() returns
 int validate_params(const fdf_params* p);       // FDF_OK or FDF_EINVAL with a message
 bool uniform_grid(const double* v, int n, double* v0, double* dv);
+// The FFT twiddles tw[j] = exp(2 pi i j / N), j < N, as (cos, sin) pairs in FP64 on the
+// host; both field-build entry points upload this one table (FP32 copies for FP32 grids).
+void twiddle_table(int N, double* cs);
 FieldArgs make_field_args(const fdf_params& p, int nk, int na, double lnk0, double dlnk, double lnat0,
                           double dlnat, double lna);
 
@@ -137,11 +187,11 @@ cudaError_t launch_fields_from_f64(cudaStream_t s, int precision, int N, const d
 // Particle passes.
 struct ParticleState {
     uint32_t* X;        // [3][n] fixed-point positions (split forms; sampler output in all forms)
-    float* q0f;         // [3][n] (split)
-    float* dqf;         // [3][n] (split)
-    double* xd;         // [3][n] (plain FP64 form)
-    double* qd;
-    double* q0d;
+    float* q0f;         // [3][n] (split-state and FP64-state forms)
+    float* dqf;         // [3][n] (split-state form)
+    double* xd;         // [3][n] (plain and FP64-state forms)
+    double* qd;         // [3][n] (plain and FP64-state forms)
+    double* q0d;        // [3][n] (plain form)
     double* sd;         // [n] phi + psi from the last kick (the exact equations of motion), or NULL
     double* qs;         // [3][n] sampled momenta (one array for both halves: id order in the plain form;
                         // the split forms carry it through their sort before the transform only)

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "device_math.cuh"
 
@@ -49,17 +50,6 @@ int scratch_address(unsigned char** out)
     return FDF_OK;
 }
 
-// tw[j] = exp(2 pi i j / N)
-template <typename V>
-__global__ void k_twiddles(int N, V* __restrict__ tw)
-{
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-        double s, c;
-        sincospi(2.0 * j / N, &s, &c);
-        tw[j] = mk<V>((typename Real<V>::T)c, (typename Real<V>::T)s);
-    }
-}
-
 }  // namespace
 }  // namespace fdf
 
@@ -77,7 +67,8 @@ extern "C" int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t
     double lnk0, dlnk, lnat0, dlnat;
     if (!uniform_grid(t->lnk, t->nk, &lnk0, &dlnk) || !uniform_grid(t->lna, t->na, &lnat0, &dlnat))
         return set_error(FDF_EINVAL, "lnk and lna must be uniform ascending grids");
-    const bool f64 = p->precision == FDF_PREC_F64;
+    const int gp = grid_prec(p->precision);
+    const bool f64 = gp == FDF_PREC_F64;
     const size_t N = (size_t)p->n_grid, N3 = N * N * N;
     const size_t csz = f64 ? 16 : 8, rsz = f64 ? 8 : 4;
     const size_t ntab = 3 * (size_t)t->na * t->nk;
@@ -104,19 +95,24 @@ extern "C" int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t
     cudaError_t e = cudaMemcpyAsync(T64, t->T_psi, nt * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T64 + nt, t->T_phi, nt * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T64 + 2 * nt, t->dTphi_dlna, nt * 8, cudaMemcpyHostToDevice, st);
+    // the twiddles fdf_create uploads, from the same host table; the copies are from
+    // pageable host memory, so the stream is synchronised before the vectors go
+    std::vector<double> twd(2 * N);
+    twiddle_table((int)N, twd.data());
+    const std::vector<float> twf(twd.begin(), twd.end());
+    if (e == cudaSuccess)
+        e = f64 ? cudaMemcpyAsync(s + oTw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, st)
+                : cudaMemcpyAsync(s + oTw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(FDF_ECUDA, (std::string("table upload: ") + cudaGetErrorString(e)).c_str());
-    if (!f64) k_twiddles<float2><<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int)N, (float2*)(s + oTw));
-    else k_twiddles<double2><<<(unsigned)((N + 255) / 256), 256, 0, st>>>((int)N, (double2*)(s + oTw));
-    e = cudaGetLastError();
     const FieldArgs a = make_field_args(*p, t->nk, t->na, lnk0, dlnk, lnat0, dlnat, lna);
     void* W0 = s + oW0;
     void* W1 = s + oW1;
-    if (e == cudaSuccess) e = launch_noise(st, p->precision, a, s + oR);
-    if (e == cudaSuccess) e = launch_mode_table(st, p->precision, a, T64, s + oA);
-    if (e == cudaSuccess) e = launch_fields_z(st, p->precision, a, s + oA, s + oR, s + oTw, W0);
-    if (e == cudaSuccess) e = launch_fields_y(st, p->precision, a, s + oTw, W0, W1);
-    if (e == cudaSuccess) e = launch_fields_x(st, p->precision, a, s + oTw, W1, W0);
-    if (e == cudaSuccess) e = launch_fields_to_f64(st, p->precision, p->n_grid, W0, out);
+    if (e == cudaSuccess) e = launch_noise(st, gp, a, s + oR);
+    if (e == cudaSuccess) e = launch_mode_table(st, gp, a, T64, s + oA);
+    if (e == cudaSuccess) e = launch_fields_z(st, gp, a, s + oA, s + oR, s + oTw, W0);
+    if (e == cudaSuccess) e = launch_fields_y(st, gp, a, s + oTw, W0, W1);
+    if (e == cudaSuccess) e = launch_fields_x(st, gp, a, s + oTw, W1, W0);
+    if (e == cudaSuccess) e = launch_fields_to_f64(st, gp, p->n_grid, W0, out);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return set_error(FDF_ECUDA, (std::string("fdf_build_fields_noalloc: ") + cudaGetErrorString(e)).c_str());

@@ -87,14 +87,12 @@ __device__ __forceinline__ void gather_fixed(const Gt* __restrict__ G, uint32_t 
 }
 
 // One axis of the order-2 kernel (Sec. 4, r = 2: the quadratic B-spline, or
-// triangular-shaped cloud) at a fixed-point coordinate: the nearest node c and
-// its neighbours, with d = u - c in [-1/2, 1/2) and weights (1/2 - d)^2/2,
-// 3/4 - d^2, (1/2 + d)^2/2.
-__device__ __forceinline__ void tsc_axis(uint32_t X, uint32_t N, uint32_t idx[3], float w[3])
+// triangular-shaped cloud) from a coordinate's cell i0, next node i1 and fraction f:
+// the nearest node c and its neighbours, with d = u - c in [-1/2, 1/2) and weights
+// (1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2.
+__device__ __forceinline__ void tsc_from_cell(uint32_t i0, uint32_t i1, float f, uint32_t N, uint32_t idx[3],
+                                              float w[3])
 {
-    uint32_t i0, i1;
-    float f;
-    fixed_cell(X, N, i0, i1, f);
     const bool up = f >= 0.5f;
     const uint32_t c = up ? i1 : i0;
     const float d = up ? f - 1.f : f;
@@ -105,6 +103,15 @@ __device__ __forceinline__ void tsc_axis(uint32_t X, uint32_t N, uint32_t idx[3]
     w[0] = 0.5f * l * l;
     w[1] = 0.75f - d * d;
     w[2] = 0.5f * r * r;
+}
+
+// The same at a fixed-point coordinate.
+__device__ __forceinline__ void tsc_axis(uint32_t X, uint32_t N, uint32_t idx[3], float w[3])
+{
+    uint32_t i0, i1;
+    float f;
+    fixed_cell(X, N, i0, i1, f);
+    tsc_from_cell(i0, i1, f, N, idx, w);
 }
 
 template <typename Gt>
@@ -143,6 +150,70 @@ __device__ __forceinline__ void gather_order(int order, const Gt* __restrict__ G
 {
     if (order == 2) gather_fixed_tsc<Gt>(G, N, X0, X1, X2, g);
     else gather_fixed<Gt>(G, N, X0, X1, X2, g);
+}
+
+// ---- reads of an FP32 or BF16 grid at an FP64 position (the FP64-state form) ----
+// The position goes to FP32 on the integer pipe; u = x N / L in FP32 then locates the
+// cell to ~2^-24 N of a cell, far below what moves a trilinear read of the fields.
+__device__ __forceinline__ void float_cell(double x, float invh, uint32_t N, uint32_t& i0, uint32_t& i1, float& f)
+{
+    const float u = d2f_bits(x) * invh;       // x in [0, L): u in [0, N]
+    uint32_t i = (uint32_t)u;
+    f = u - (float)i;
+    i = i >= N ? i - N : i;                    // u rounded up to N: node 0
+    i = i < N ? i : N - 1u;                    // (never taken for x in [0, L); keeps reads in the grid)
+    i0 = i;
+    i1 = i + 1u == N ? 0u : i + 1u;
+}
+
+template <typename Gt>
+__device__ __forceinline__ void gather_wide(int order, const Gt* __restrict__ G, uint32_t N, float invh,
+                                            const double x[3], float g[8])
+{
+    uint32_t ix[3], iy[3], iz[3];
+    float wx[3], wy[3], wz[3];
+    uint32_t i0, i1;
+    float f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) g[s] = 0.f;
+    if (order == 2) {
+        float_cell(x[0], invh, N, i0, i1, f);
+        tsc_from_cell(i0, i1, f, N, ix, wx);
+        float_cell(x[1], invh, N, i0, i1, f);
+        tsc_from_cell(i0, i1, f, N, iy, wy);
+        float_cell(x[2], invh, N, i0, i1, f);
+        tsc_from_cell(i0, i1, f, N, iz, wz);
+#pragma unroll 1
+        for (int cz = 0; cz < 3; ++cz) {
+#pragma unroll
+            for (int cy = 0; cy < 3; ++cy) {
+                const uint32_t row = (iz[cz] * N + iy[cy]) * N;
+                const float wzy = wz[cz] * wy[cy];
+#pragma unroll
+                for (int cx = 0; cx < 3; ++cx) {
+                    const float w = wx[cx] * wzy;
+                    float v[8];
+                    Cell<Gt>::load(G, row + ix[cx], v);
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) g[s] = fmaf(w, v[s], g[s]);
+                }
+            }
+        }
+        return;
+    }
+    float fx, fy, fz;
+    float_cell(x[0], invh, N, ix[0], ix[1], fx);
+    float_cell(x[1], invh, N, iy[0], iy[1], fy);
+    float_cell(x[2], invh, N, iz[0], iz[1], fz);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+        const float w = (cx ? fx : 1.f - fx) * (cy ? fy : 1.f - fy) * (cz ? fz : 1.f - fz);
+        float v[8];
+        Cell<Gt>::load(G, (iz[cz] * N + iy[cy]) * N + ix[cx], v);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) g[s] = fmaf(w, v[s], g[s]);
+    }
 }
 
 // FP64 read at an FP64 position in [0, L).
@@ -253,7 +324,9 @@ struct Masses {
 // ---- initial transform -----------------------------------------------------
 // q_i <- q_i (1 - psi/2) - (eps tau_0 / 6) d_i psi  (eq:transform with delta = -2 psi,
 // theta = k^2 tau psi / 2, nu = 4, omega = 4/3), eps = sqrt(p^2 + m^2 a_0^2).
-template <int Prec, typename Gt>
+// F: the state form (kPlain, kWide, kFixed).  The transform reads the fields at the
+// sampled fixed-point positions in every form.
+template <int F, typename Gt>
 __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t n, int64_t n_part, Masses ms,
                                                       double a0, double tau0, int order, int N, double L,
                                                       const Gt* __restrict__ G)
@@ -267,7 +340,7 @@ __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t 
         x[0] = L * ((double)X0 * 2.3283064365386963e-10);
         x[1] = L * ((double)X1 * 2.3283064365386963e-10);
         x[2] = L * ((double)X2 * 2.3283064365386963e-10);
-        if constexpr (Prec == FDF_PREC_F64) {
+        if constexpr (F == kPlain) {
             gather_f64_order(order, reinterpret_cast<const double*>(G), N, (double)N / L, x, g);
         } else {
             float gf[8];
@@ -282,10 +355,14 @@ __global__ void __launch_bounds__(kThreads) k_initial(ParticleState st, int64_t 
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double q = st.qs[d * n + i] * r - c * g[d];
-            if constexpr (Prec == FDF_PREC_F64) {
+            if constexpr (F == kPlain) {
                 st.xd[d * n + i] = x[d];
                 st.qd[d * n + i] = q;
                 st.q0d[d * n + i] = q;
+            } else if constexpr (F == kWide) {
+                st.xd[d * n + i] = x[d];
+                st.qd[d * n + i] = q;
+                st.q0f[d * n + i] = (float)q;     // q_0 of the kick, stored in FP32
             } else {
                 const float hi = (float)q;
                 st.q0f[d * n + i] = hi;
@@ -464,6 +541,144 @@ void push_split(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleSta
     else push_split_nk<Gt, false, UNI>(s, b, a, st);
 }
 
+// ---- the fused leapfrog pass, FP64-state form --------------------------------------
+// x and q are FP64 in HBM and in registers and are accumulated in FP64; q_0 is FP32.
+// Every step integral is evaluated in FP64 (WideCoef):
+//   drift  D = int dtau / sqrt(q^2 + m^2 a^2) = r gm(t),  r = (q^2 + m^2 a_c^2)^(-1/2),
+//   kick   K_phi = int dtau / eps_0 = r0 gm(t0),  K_psi = int eps_0 dtau = (u0 r0) gp(t0),
+// with the polynomial's leading terms in FP64 and the rest in FP32 (they add less
+// than 1e-7 of the integral).  The kick, at most ~1e-3 of |q| per step, is formed in
+// FP32 from the FP32 gradients and added to q in FP64.  GB300 runs FP64 arithmetic
+// and FP64 <-> FP32 conversions at 1/64 of its FP32 rate, so every conversion goes
+// through the integer pipe (d2f_bits, f2d_bits).
+
+// p(t) = sum_k c_k t^k: the terms from k = NF64 up in FP32 (Horner), then the terms
+// below NF64 in FP64
+template <int NF64>
+__device__ __forceinline__ double wide_poly(const WidePoly& P, double t)
+{
+    const float tf = d2f_bits(t);
+    float tail = P.c32[kWideDeg - NF64];
+#pragma unroll
+    for (int k = kWideDeg - NF64 - 1; k >= 0; --k) tail = fmaf(tail, tf, P.c32[k]);
+    double acc = f2d_bits(tail);
+#pragma unroll
+    for (int k = NF64 - 1; k >= 0; --k) acc = fma(acc, t, P.c64[k]);
+    return acc;
+}
+
+// Periodic wrap into [0, L) (wrap_f64, a result equal to L mapping to 0), taken only
+// when x left the box.  The test runs on the bit patterns (IEEE doubles order like
+// integers when positive; a negative value has the sign bit), so only a warp with a
+// wrapping particle spends FP64 instructions on it.
+__device__ __forceinline__ double wrap_rare(double x, double L, double invL, long long Lbits)
+{
+    const long long b = __double_as_longlong(x);
+    if (b >= Lbits || b < 0) x = wrap_f64(x, L, invL);
+    return x;
+}
+
+template <typename Gt, bool SERIES, bool UNI>
+__global__ void __launch_bounds__(kThreads, 2) k_push_wide(const __grid_constant__ PushArgs a,
+                                                           double* __restrict__ xd, double* __restrict__ qd,
+                                                           const float* __restrict__ q0f)
+{
+    const int64_t n = a.n;
+    const uint32_t N = (uint32_t)a.N;
+    const float invh = (float)a.invh;
+    const long long Lbits = __double_as_longlong(a.L);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        if (i >= n) continue;
+        const int s = UNI ? 0 : species_of(a, i);
+        const double m2 = a.m2[s];
+        double x[3] = {__ldcs(xd + i), __ldcs(xd + n + i), __ldcs(xd + 2 * n + i)};
+        double q[3] = {__ldcs(qd + i), __ldcs(qd + n + i), __ldcs(qd + 2 * n + i)};
+        const float qa = __ldcs(q0f + i), qb = __ldcs(q0f + n + i), qc = __ldcs(q0f + 2 * n + i);
+        // |q0|^2: exact products of the FP32 components, summed in FP64 (once per pass)
+        const double da = f2d_bits(qa), db = f2d_bits(qb), dc = f2d_bits(qc);
+        const double s0 = fma(da, da, fma(db, db, dc * dc));
+        const float q02 = d2f_bits(s0);
+        bool moved = false, kicked = false;
+        for (int u = 0; u < a.nsub; ++u) {
+            const SubStep& st = a.sub[u];
+            const WideCoef& c = st.wide;
+            if (st.do_drift) {
+                const double qq = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
+                double D;
+                if constexpr (SERIES) {
+                    const double muc = m2 * c.a2c;
+                    const double uc = qq + muc;
+                    const double r = rsqrt_fp64(uc);
+                    const double t = (muc * r) * r;
+                    D = r * wide_poly<kWideD64>(c.drift, t);
+                } else {
+                    const SpeciesCoef& sc = st.sp[s];
+                    D = 0.0;
+                    for (int j = 0; j < a.n_gl; ++j) D = fma(sc.Wd[j], rsqrt_fp64(qq + sc.mud[j]), D);
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) x[d] = wrap_rare(fma(q[d], D, x[d]), a.L, a.invL, Lbits);
+                moved = true;
+            }
+            if (st.do_kick) {
+                float g[8];
+                gather_wide<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, invh, x, g);
+                double Kpsi, Kphi;
+                if constexpr (SERIES) {
+                    const double muk = m2 * c.a2k;
+                    const double u0 = s0 + muk;
+                    const double r0 = rsqrt_fp64(u0);
+                    const double t0 = (muk * r0) * r0;
+                    Kphi = r0 * wide_poly<kWideK64>(c.kphi, t0);
+                    Kpsi = (u0 * r0) * wide_poly<kWideK64>(c.kpsi, t0);
+                } else {
+                    const SpeciesCoef& sc = st.sp[s];
+                    Kpsi = 0.0;
+                    Kphi = 0.0;
+                    for (int j = 0; j < a.n_kick; ++j) {
+                        const double e2 = s0 + sc.muk[j];
+                        const double ie = rsqrt_fp64(e2);
+                        Kpsi = fma(sc.Wk[j], e2 * ie, Kpsi);
+                        Kphi = fma(sc.Wk[j], ie, Kphi);
+                    }
+                }
+                const float Kpsif = d2f_bits(Kpsi), Kphif = d2f_bits(Kphi);
+                const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
+                const float b = qdphi * Kphif + g[6] * c.dtau_k;
+                const float a2 = q02 * Kphif;
+                q[0] += f2d_bits(-g[0] * Kpsif - g[3] * a2 + qa * b);
+                q[1] += f2d_bits(-g[1] * Kpsif - g[4] * a2 + qb * b);
+                q[2] += f2d_bits(-g[2] * Kpsif - g[5] * a2 + qc * b);
+                kicked = true;
+            }
+        }
+        if (moved) {
+            __stcs(xd + i, x[0]);
+            __stcs(xd + n + i, x[1]);
+            __stcs(xd + 2 * n + i, x[2]);
+        }
+        if (kicked) {
+            __stcs(qd + i, q[0]);
+            __stcs(qd + n + i, q[1]);
+            __stcs(qd + 2 * n + i, q[2]);
+        }
+    }
+}
+
+template <typename Gt>
+void push_wide(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
+{
+    if (a.wide_series) {
+        if (a.uniform_species) k_push_wide<Gt, true, true><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
+        else k_push_wide<Gt, true, false><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
+    } else {
+        if (a.uniform_species) k_push_wide<Gt, false, true><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
+        else k_push_wide<Gt, false, false><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
+    }
+}
+
 // ---- the fused leapfrog pass, plain FP64 form --------------------------------
 // FDF_EOM_EXACT (eq:releq and eq:geodesic, not symplectic): each kick holds q at its
 // own start in place of q0, and each drift is scaled by 1 + phi + psi, the slot 7 of
@@ -536,13 +751,13 @@ __global__ void __launch_bounds__(kThreads) k_push_f64(const __grid_constant__ P
 }
 
 // ---- state read-back ------------------------------------------------------------
-template <int Prec>
+template <int F>
 __device__ __forceinline__ void load_state(const ParticleState& st, int64_t n, int64_t i, double L, double x[3],
                                            double q[3])
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        if constexpr (Prec == FDF_PREC_F64) {
+        if constexpr (F != kFixed) {
             x[d] = st.xd[d * n + i];
             q[d] = st.qd[d * n + i];
         } else {
@@ -552,7 +767,7 @@ __device__ __forceinline__ void load_state(const ParticleState& st, int64_t n, i
     }
 }
 
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                      double L, double T, double* __restrict__ xo,
                                                      double* __restrict__ qo, double* __restrict__ wo)
@@ -562,7 +777,7 @@ __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n
         const int64_t i = begin + j;
         const int64_t o = (int64_t)st.id[i] - begin;
         double x[3], q[3];
-        load_state<Prec>(st, n, i, L, x, q);
+        load_state<F>(st, n, i, L, x, q);
         if (xo) {
             xo[o] = x[0];
             xo[count + o] = x[1];
@@ -574,7 +789,7 @@ __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n
             qo[2 * count + o] = q[2];
         }
         if (wo) {
-            if constexpr (Prec == FDF_PREC_F64) wo[o] = dfweight(norm3_rn(q), st.pmag[i], T);
+            if constexpr (F == kPlain) wo[o] = dfweight(norm3_rn(q), st.pmag[i], T);
             else wo[o] = (double)dfweight_split(norm3_rn(q), st.pmag[i], T);
         }
     }
@@ -584,7 +799,7 @@ __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n
 // positions and sampled momenta are the live state and follow the permutation (it
 // sorts before the momentum transform); the plain form keeps them in id order.
 // |q_sampled| follows the permutation in both forms.
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, int64_t n, int64_t begin,
                                                              int64_t count, uint32_t* __restrict__ Xo,
                                                              double* __restrict__ po, double* __restrict__ qso)
@@ -596,7 +811,7 @@ __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, i
         if (Xo) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if constexpr (Prec == FDF_PREC_F64) Xo[d * count + j] = st.X[d * n + i];
+                if constexpr (F == kPlain) Xo[d * count + j] = st.X[d * n + i];
                 else Xo[d * count + o] = st.X[d * n + i];
             }
         }
@@ -604,7 +819,7 @@ __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, i
         if (qso) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if constexpr (Prec == FDF_PREC_F64) qso[d * count + j] = st.qs[d * n + i];
+                if constexpr (F == kPlain) qso[d * count + j] = st.qs[d * n + i];
                 else qso[d * count + o] = st.qs[d * n + i];
             }
         }
@@ -616,7 +831,7 @@ __global__ void __launch_bounds__(kThreads) k_export_initial(ParticleState st, i
 // T1 = -eps grad psi, T2 = -(q^2/eps) grad phi, T3 = q (q.grad phi)/eps, T4 = q phi_dot,
 // eps = sqrt(q^2 + m^2 a^2).  sums[0..3] accumulate |T_i|^2 and sums[4] |T1+T2+T3+T4|^2
 // (FP64, one atomic addition per warp and quantity).
-template <int Prec, typename Gt>
+template <int F, typename Gt>
 __global__ void __launch_bounds__(kThreads) k_accel_terms(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                           int64_t n_part, Masses ms, double a, int order, int N,
                                                           double L, const Gt* __restrict__ G,
@@ -628,9 +843,14 @@ __global__ void __launch_bounds__(kThreads) k_accel_terms(ParticleState st, int6
         const int64_t i = begin + j;
         const double m = ms.m[i / n_part];
         double x[3], q[3], g[8];
-        load_state<Prec>(st, n, i, L, x, q);
-        if constexpr (Prec == FDF_PREC_F64) {
+        load_state<F>(st, n, i, L, x, q);
+        if constexpr (F == kPlain) {
             gather_f64_order(order, reinterpret_cast<const double*>(G), N, (double)N / L, x, g);
+        } else if constexpr (F == kWide) {
+            float gf[8];
+            gather_wide<Gt>(order, G, (uint32_t)N, (float)((double)N / L), x, gf);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) g[s] = (double)gf[s];
         } else {
             float gf[8];
             gather_order<Gt>(order, G, (uint32_t)N, st.X[i], st.X[n + i], st.X[2 * n + i], gf);
@@ -660,7 +880,7 @@ __global__ void __launch_bounds__(kThreads) k_accel_terms(ParticleState st, int6
     }
 }
 
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                       int64_t n_part, Masses ms, double a, double T, int quantity,
                                                       int parity, int order, int N, double L,
@@ -673,19 +893,19 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
         if (parity >= 0 && (int)(st.id[i] & 1u) != parity) continue;
         const double m = ms.m[i / n_part];
         double x[3], q[3];
-        load_state<Prec>(st, n, i, L, x, q);
+        load_state<F>(st, n, i, L, x, q);
         const double qm = norm3_rn(q);
         double v = 1.0;
-        if constexpr (Prec == FDF_PREC_F64) {
+        if constexpr (F == kPlain) {
             const double eps = sqrt(qm * qm + m * m * a * a);
             if (quantity == FDF_Q_W_EPS) v = dfweight(qm, st.pmag[i], T) * eps;
             else if (quantity == FDF_Q_W) v = dfweight(qm, st.pmag[i], T);
             else if (quantity == FDF_Q_EPS) v = eps;
             else if (quantity >= FDF_Q_W_QX) v = dfweight(qm, st.pmag[i], T) * q[quantity - FDF_Q_W_QX];
         } else {
-            // The split form deposits in FP32 arithmetic (FP64 sums): its momenta carry
-            // FP32 rounding already.  The weight's argument p - |q| (a small difference)
-            // is formed in FP64 first.
+            // The FP32-grid forms deposit in FP32 arithmetic (FP64 sums): the weight's
+            // argument p - |q| (a small difference) is formed in FP64 first, and the
+            // kernel weights of an FP64 position take its fraction from FP64.
             const float qf = (float)qm;
             const float ma = (float)(m * a);
             const float eps = sqrtf(fmaf(qf, qf, ma * ma));
@@ -697,13 +917,13 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
         }
         // per axis: the kernel's nodes and weights (order 1: 2 nodes, order 2: 3), in the
         // form's deposit precision
-        using Wt = typename std::conditional<Prec == FDF_PREC_F64, double, float>::type;
+        using Wt = typename std::conditional<F == kPlain, double, float>::type;
         int idx[3][3];
         Wt w[3][3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             double u;
-            if constexpr (Prec == FDF_PREC_F64) {
+            if constexpr (F != kFixed) {
                 u = x[d] * invh;
             } else {
                 const uint32_t Xd = st.X[d * n + i];
@@ -757,29 +977,38 @@ cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& s
     if (n <= 0) return cudaSuccess;
     const unsigned b = grid_for(n);
     const Masses ms = masses_of(m_ev);
-    if (precision == FDF_PREC_F64)
-        k_initial<FDF_PREC_F64, double><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, order, N, L,
-                                                                   (const double*)G);
-    else if (precision == FDF_PREC_F32)
-        k_initial<FDF_PREC_F32, float><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, order, N, L,
-                                                                 (const float*)G);
-    else
-        k_initial<FDF_PREC_BF16, __nv_bfloat16>
-            <<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, order, N, L, (const __nv_bfloat16*)G);
+    const int f = form_of(precision), gp = grid_prec(precision);
+#define FDF_INITIAL(F_, Gt_) \
+    k_initial<F_, Gt_><<<b, kThreads, 0, s>>>(st, n, n_part, ms, a0, tau0, order, N, L, (const Gt_*)G)
+    if (f == kPlain) FDF_INITIAL(kPlain, double);
+    else if (f == kWide && gp == FDF_PREC_F32) FDF_INITIAL(kWide, float);
+    else if (f == kWide) FDF_INITIAL(kWide, __nv_bfloat16);
+    else if (gp == FDF_PREC_F32) FDF_INITIAL(kFixed, float);
+    else FDF_INITIAL(kFixed, __nv_bfloat16);
+#undef FDF_INITIAL
     return cudaGetLastError();
 }
 
 cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a)
 {
     if (a.n <= 0) return cudaSuccess;
-    const unsigned b = grid_for(a.n);
-    if (precision == FDF_PREC_F64) k_push_f64<<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d, st.sd);
-    else if (precision == FDF_PREC_F32) {
-        if (a.uniform_species) push_split<float, true>(s, b, a, st);
-        else push_split<float, false>(s, b, a, st);
+    const int f = form_of(precision), gp = grid_prec(precision);
+    if (f == kPlain) {
+        k_push_f64<<<grid_for(a.n), kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d, st.sd);
+    } else if (f == kWide) {
+        // two resident blocks per SM (the FP64 pipe, not occupancy, bounds the pass)
+        const unsigned b = grid_for(a.n);
+        if (gp == FDF_PREC_F32) push_wide<float>(s, b, a, st);
+        else push_wide<__nv_bfloat16>(s, b, a, st);
     } else {
-        if (a.uniform_species) push_split<__nv_bfloat16, true>(s, b, a, st);
-        else push_split<__nv_bfloat16, false>(s, b, a, st);
+        const unsigned b = grid_for(a.n);
+        if (gp == FDF_PREC_F32) {
+            if (a.uniform_species) push_split<float, true>(s, b, a, st);
+            else push_split<float, false>(s, b, a, st);
+        } else {
+            if (a.uniform_species) push_split<__nv_bfloat16, true>(s, b, a, st);
+            else push_split<__nv_bfloat16, false>(s, b, a, st);
+        }
     }
     return cudaGetLastError();
 }
@@ -789,10 +1018,10 @@ cudaError_t launch_export(cudaStream_t s, int precision, const ParticleState& st
 {
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
-    if (precision == FDF_PREC_F64)
-        k_export<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
-    else
-        k_export<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
+    const int f = form_of(precision);
+    if (f == kPlain) k_export<kPlain><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
+    else if (f == kWide) k_export<kWide><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
+    else k_export<kFixed><<<b, kThreads, 0, s>>>(st, n, begin, count, L, T_ev, x, q, w);
     return cudaGetLastError();
 }
 
@@ -801,10 +1030,11 @@ cudaError_t launch_export_initial(cudaStream_t s, int precision, const ParticleS
 {
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
-    if (precision == FDF_PREC_F64)
-        k_export_initial<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p, qs);
+    // the FP64-state and split-state forms both sort before the transform
+    if (form_of(precision) == kPlain)
+        k_export_initial<kPlain><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p, qs);
     else
-        k_export_initial<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p, qs);
+        k_export_initial<kFixed><<<b, kThreads, 0, s>>>(st, n, begin, count, X, p, qs);
     return cudaGetLastError();
 }
 
@@ -815,15 +1045,15 @@ cudaError_t launch_accel_terms(cudaStream_t s, int precision, const ParticleStat
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
     const Masses ms = masses_of(m_ev);
-    if (precision == FDF_PREC_F64)
-        k_accel_terms<FDF_PREC_F64, double><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, order, N, L,
-                                                                       (const double*)G, sums);
-    else if (precision == FDF_PREC_F32)
-        k_accel_terms<FDF_PREC_F32, float><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, order, N, L,
-                                                                     (const float*)G, sums);
-    else
-        k_accel_terms<FDF_PREC_BF16, __nv_bfloat16><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, order,
-                                                                             N, L, (const __nv_bfloat16*)G, sums);
+    const int f = form_of(precision), gp = grid_prec(precision);
+#define FDF_TERMS(F_, Gt_) \
+    k_accel_terms<F_, Gt_><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, order, N, L, (const Gt_*)G, sums)
+    if (f == kPlain) FDF_TERMS(kPlain, double);
+    else if (f == kWide && gp == FDF_PREC_F32) FDF_TERMS(kWide, float);
+    else if (f == kWide) FDF_TERMS(kWide, __nv_bfloat16);
+    else if (gp == FDF_PREC_F32) FDF_TERMS(kFixed, float);
+    else FDF_TERMS(kFixed, __nv_bfloat16);
+#undef FDF_TERMS
     return cudaGetLastError();
 }
 
@@ -834,12 +1064,13 @@ cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& s
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
     const Masses ms = masses_of(m_ev);
-    if (precision == FDF_PREC_F64)
-        k_deposit<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, parity,
-                                                        order, N, L, grid);
-    else
-        k_deposit<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, parity,
-                                                        order, N, L, grid);
+    const int f = form_of(precision);
+#define FDF_DEPOSIT(F_) \
+    k_deposit<F_><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, parity, order, N, L, grid)
+    if (f == kPlain) FDF_DEPOSIT(kPlain);
+    else if (f == kWide) FDF_DEPOSIT(kWide);
+    else FDF_DEPOSIT(kFixed);
+#undef FDF_DEPOSIT
     return cudaGetLastError();
 }
 

@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v)  // 10 bits -> every thi
     return v;
 }
 
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_sort_keys(ParticleState st, int64_t n, int64_t n_part, uint32_t N,
                                                         int tile_shift, uint32_t tiles_per_species, double invh,
                                                         SortLead lead, uint32_t* __restrict__ key,
@@ -46,11 +46,30 @@ __global__ void __launch_bounds__(kThreads) k_sort_keys(ParticleState st, int64_
         if (!live) continue;
         const uint32_t s = (uint32_t)(i / n_part);
         uint32_t c[3];
-        if constexpr (Prec == FDF_PREC_F64) {
+        if constexpr (F == kPlain) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 int ci = (int)floor(st.xd[d * n + i] * invh);
                 ci = ci < 0 ? 0 : (ci >= (int)N ? (int)N - 1 : ci);
+                c[d] = (uint32_t)ci >> tile_shift;
+            }
+        } else if constexpr (F == kWide) {
+            // the cell of x + q dtau / sqrt(q^2 + m^2 a^2) (the lead in cells), wrapped
+            float q[3], q2 = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                q[d] = (float)st.qd[d * n + i];
+                q2 = fmaf(q[d], q[d], q2);
+            }
+            const float k = lead.on ? lead.dtau_q32[s] * ((float)N * 2.3283064365386963e-10f) *
+                                          rsqrtf(q2 + lead.m2a2[s])
+                                    : 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float u = (float)st.xd[d * n + i] * (float)invh + q[d] * k;
+                u = fminf(fmaxf(u, -1.0e6f), 1.0e6f);      // a saturated lead is only a poor guess
+                int ci = (int)floorf(u) % (int)N;
+                ci = ci < 0 ? ci + (int)N : ci;
                 c[d] = (uint32_t)ci >> tile_shift;
             }
         } else {
@@ -161,8 +180,45 @@ struct alignas(32) PlainRec {   // 128 bytes: four whole sectors
 };
 static_assert(sizeof(PlainRec) == 128, "PlainRec is four sectors");
 
-template <int Prec> struct RecOf { using T = SplitRec; };
-template <> struct RecOf<FDF_PREC_F64> { using T = PlainRec; };
+struct alignas(32) WideRec {    // 96 bytes: three whole sectors
+    double x[3], q[3];
+    float q0[3];
+    uint32_t id;
+    double pmag;
+    uint32_t pad[4];
+};
+static_assert(sizeof(WideRec) == 96, "WideRec is three sectors");
+
+template <int F> struct RecOf { using T = SplitRec; };
+template <> struct RecOf<kPlain> { using T = PlainRec; };
+template <> struct RecOf<kWide> { using T = WideRec; };
+
+// A wide record moves as three 32-byte vector accesses (records are 32-byte aligned).
+__device__ __forceinline__ void store_wide(void* recs, int64_t j, const WideRec& r)
+{
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(&r);
+    uint32_t* p = reinterpret_cast<uint32_t*>(recs) + 24 * j;
+#pragma unroll
+    for (int h = 0; h < 3; ++h)
+        asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p + 8 * h), "r"(w[8 * h]),
+                     "r"(w[8 * h + 1]), "r"(w[8 * h + 2]), "r"(w[8 * h + 3]), "r"(w[8 * h + 4]), "r"(w[8 * h + 5]),
+                     "r"(w[8 * h + 6]), "r"(w[8 * h + 7])
+                     : "memory");
+}
+
+__device__ __forceinline__ WideRec load_wide(const void* recs, int64_t j)
+{
+    WideRec r;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&r);
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(recs) + 24 * j;
+#pragma unroll
+    for (int h = 0; h < 3; ++h)
+        asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(w[8 * h]), "=r"(w[8 * h + 1]), "=r"(w[8 * h + 2]), "=r"(w[8 * h + 3]), "=r"(w[8 * h + 4]),
+                       "=r"(w[8 * h + 5]), "=r"(w[8 * h + 6]), "=r"(w[8 * h + 7])
+                     : "l"(p + 8 * h));
+    return r;
+}
 
 // A split record moves as two 32-byte vector accesses (the record buffer and each
 // record are 64-byte aligned).
@@ -202,11 +258,20 @@ __device__ __forceinline__ SplitRec load_split(const void* recs, int64_t j)
     return r;
 }
 
-template <int Prec>
-__device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int64_t i, typename RecOf<Prec>::T& r,
+template <int F>
+__device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int64_t i, typename RecOf<F>::T& r,
                                          bool pre_transform = false)
 {
-    if constexpr (Prec == FDF_PREC_F64) {
+    if constexpr (F == kWide) {
+        for (int d = 0; d < 3; ++d) {
+            r.x[d] = a.xd[d * n + i];
+            r.q[d] = a.qd[d * n + i];
+            r.q0[d] = a.q0f[d * n + i];
+        }
+        r.id = a.id[i];
+        r.pmag = a.pmag[i];
+        for (int q = 0; q < 4; ++q) r.pad[q] = 0;
+    } else if constexpr (F == kPlain) {
         for (int d = 0; d < 3; ++d) {
             r.x[d] = a.xd[d * n + i];
             r.q[d] = a.qd[d * n + i];
@@ -247,12 +312,12 @@ __device__ __forceinline__ void make_rec(const ParticleState& a, int64_t n, int6
 // round trip to L2 is what a particle waits for, and kPackU of them overlap.
 constexpr int kPackU = 2;
 
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t n, const uint32_t* __restrict__ key,
                                                         uint32_t* __restrict__ offset, void* __restrict__ recs,
                                                         int pre_transform)
 {
-    using Rec = typename RecOf<Prec>::T;
+    using Rec = typename RecOf<F>::T;
     // Grid-stride loop with a warp-uniform trip count, so that every lane can take
     // part in the warp-aggregated atomics: lanes sharing a key take one atomicAdd
     // through their leader.
@@ -271,7 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t
             live[u] = idx[u] < n;
             k[u] = live[u] ? key[idx[u]] : 0u;
             base[u] = 0u;
-            if (live[u]) make_rec<Prec>(a, n, idx[u], r[u], pre_transform != 0);
+            if (live[u]) make_rec<F>(a, n, idx[u], r[u], pre_transform != 0);
         }
 #pragma unroll
         for (int u = 0; u < kPackU; ++u) {
@@ -289,18 +354,28 @@ __global__ void __launch_bounds__(kThreads) k_sort_pack(ParticleState a, int64_t
             if (!live[u]) continue;
             const uint32_t b = __shfl_sync(peers[u], base[u], leader[u]);
             const int64_t j = (int64_t)b + __popc(peers[u] & ((1u << lane) - 1u));
-            if constexpr (Prec == FDF_PREC_F64) reinterpret_cast<Rec*>(recs)[j] = r[u];
+            if constexpr (F == kPlain) reinterpret_cast<Rec*>(recs)[j] = r[u];
+            else if constexpr (F == kWide) store_wide(recs, j, r[u]);
             else store_split(recs, j, r[u]);
         }
     }
 }
 
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64_t n, const void* __restrict__ recs,
                                                           int pre_transform)
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        if constexpr (Prec == FDF_PREC_F64) {
+        if constexpr (F == kWide) {
+            const WideRec r = load_wide(recs, j);
+            for (int d = 0; d < 3; ++d) {
+                b.xd[d * n + j] = r.x[d];
+                b.qd[d * n + j] = r.q[d];
+                b.q0f[d * n + j] = r.q0[d];
+            }
+            b.pmag[j] = r.pmag;
+            b.id[j] = r.id;
+        } else if constexpr (F == kPlain) {
             const PlainRec r = reinterpret_cast<const PlainRec*>(recs)[j];
             for (int d = 0; d < 3; ++d) {
                 b.xd[d * n + j] = r.x[d];
@@ -340,23 +415,24 @@ __global__ void __launch_bounds__(kThreads) k_sort_unpack(ParticleState b, int64
 // instead each particle's record goes whole to that slot (one scattered 64-byte
 // write), and a streaming pass turns the records into positions, momenta and
 // weights.
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_export_pack(ParticleState a, int64_t n, int64_t begin, int64_t count,
                                                           void* __restrict__ recs)
 {
-    using Rec = typename RecOf<Prec>::T;
+    using Rec = typename RecOf<F>::T;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = begin + j;
         const int64_t o = (int64_t)a.id[i] - begin;
         Rec r;
-        make_rec<Prec>(a, n, i, r);
-        if constexpr (Prec == FDF_PREC_F64) reinterpret_cast<Rec*>(recs)[o] = r;
+        make_rec<F>(a, n, i, r);
+        if constexpr (F == kPlain) reinterpret_cast<Rec*>(recs)[o] = r;
+        else if constexpr (F == kWide) store_wide(recs, o, r);
         else store_split(recs, o, r);
     }
 }
 
-template <int Prec>
+template <int F>
 __global__ void __launch_bounds__(kThreads) k_export_unpack(const void* __restrict__ recs, int64_t count, double L,
                                                             double T, double* __restrict__ xo,
                                                             double* __restrict__ qo, double* __restrict__ wo)
@@ -364,7 +440,14 @@ __global__ void __launch_bounds__(kThreads) k_export_unpack(const void* __restri
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < count;
          o += (int64_t)gridDim.x * blockDim.x) {
         double x[3], q[3], pm;
-        if constexpr (Prec == FDF_PREC_F64) {
+        if constexpr (F == kWide) {
+            const WideRec r = load_wide(recs, o);
+            for (int d = 0; d < 3; ++d) {
+                x[d] = r.x[d];
+                q[d] = r.q[d];
+            }
+            pm = r.pmag;
+        } else if constexpr (F == kPlain) {
             const PlainRec r = reinterpret_cast<const PlainRec*>(recs)[o];
             for (int d = 0; d < 3; ++d) {
                 x[d] = r.x[d];
@@ -390,7 +473,7 @@ __global__ void __launch_bounds__(kThreads) k_export_unpack(const void* __restri
             qo[2 * count + o] = q[2];
         }
         if (wo) {
-            if constexpr (Prec == FDF_PREC_F64) wo[o] = dfweight(norm3_rn(q), pm, T);
+            if constexpr (F == kPlain) wo[o] = dfweight(norm3_rn(q), pm, T);
             else wo[o] = (double)dfweight_split(norm3_rn(q), pm, T);
         }
     }
@@ -405,7 +488,12 @@ unsigned grid_for(int64_t n)
 
 }  // namespace
 
-size_t sort_record_bytes(int precision) { return precision == FDF_PREC_F64 ? sizeof(PlainRec) : sizeof(SplitRec); }
+size_t sort_record_bytes(int precision)
+{
+    const int f = form_of(precision);
+    // the FP64-state form also sorts once before the transform, with split records
+    return f == kPlain ? sizeof(PlainRec) : f == kWide ? sizeof(WideRec) : sizeof(SplitRec);
+}
 
 cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, const ParticleState& b, int64_t n,
                         int64_t n_part, int n_species, int N, int tile_shift, double L, const SortLead& lead,
@@ -419,21 +507,23 @@ cudaError_t launch_sort(cudaStream_t s, int precision, const ParticleState& a, c
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)bins * 4, s);
     if (e != cudaSuccess) return e;
     const unsigned g = grid_for(n);
-    if (precision == FDF_PREC_F64)
-        k_sort_keys<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, lead, key,
-                                                         hist);
-    else
-        k_sort_keys<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, lead, key,
-                                                         hist);
-    e = scan_exclusive(s, hist, bins, bsum);
-    if (e != cudaSuccess) return e;
-    if (precision == FDF_PREC_F64) {
-        k_sort_pack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(a, n, key, hist, recs, 0);
-        k_sort_unpack<FDF_PREC_F64><<<g, kThreads, 0, s>>>(b, n, recs, 0);
-    } else {
-        k_sort_pack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(a, n, key, hist, recs, lead.pre_transform);
-        k_sort_unpack<FDF_PREC_F32><<<g, kThreads, 0, s>>>(b, n, recs, lead.pre_transform);
-    }
+    // Before the momentum transform the FP64-state and split-state forms hold the
+    // sampler's output only (fixed-point positions, sampled momenta): both sort it as
+    // the split-state form does.
+    int f = form_of(precision);
+    if (lead.pre_transform) f = kFixed;
+#define FDF_SORT(F_)                                                                                                  \
+    do {                                                                                                              \
+        k_sort_keys<F_><<<g, kThreads, 0, s>>>(a, n, n_part, (uint32_t)N, shift, tiles, N / L, lead, key, hist);     \
+        e = scan_exclusive(s, hist, bins, bsum);                                                                      \
+        if (e != cudaSuccess) return e;                                                                               \
+        k_sort_pack<F_><<<g, kThreads, 0, s>>>(a, n, key, hist, recs, lead.pre_transform);                           \
+        k_sort_unpack<F_><<<g, kThreads, 0, s>>>(b, n, recs, lead.pre_transform);                                    \
+    } while (0)
+    if (f == kPlain) FDF_SORT(kPlain);
+    else if (f == kWide) FDF_SORT(kWide);
+    else FDF_SORT(kFixed);
+#undef FDF_SORT
     return cudaGetLastError();
 }
 
@@ -442,13 +532,16 @@ cudaError_t launch_export_records(cudaStream_t s, int precision, const ParticleS
 {
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
-    if (precision == FDF_PREC_F64) {
-        k_export_pack<FDF_PREC_F64><<<b, kThreads, 0, s>>>(st, n, begin, count, recs);
-        k_export_unpack<FDF_PREC_F64><<<b, kThreads, 0, s>>>(recs, count, L, T_ev, x, q, w);
-    } else {
-        k_export_pack<FDF_PREC_F32><<<b, kThreads, 0, s>>>(st, n, begin, count, recs);
-        k_export_unpack<FDF_PREC_F32><<<b, kThreads, 0, s>>>(recs, count, L, T_ev, x, q, w);
-    }
+    const int f = form_of(precision);
+#define FDF_EXPORT(F_)                                                                                                \
+    do {                                                                                                              \
+        k_export_pack<F_><<<b, kThreads, 0, s>>>(st, n, begin, count, recs);                                          \
+        k_export_unpack<F_><<<b, kThreads, 0, s>>>(recs, count, L, T_ev, x, q, w);                                    \
+    } while (0)
+    if (f == kPlain) FDF_EXPORT(kPlain);
+    else if (f == kWide) FDF_EXPORT(kWide);
+    else FDF_EXPORT(kFixed);
+#undef FDF_EXPORT
     return cudaGetLastError();
 }
 

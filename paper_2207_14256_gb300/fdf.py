@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfdf.so")
 
 FDF_OK, FDF_EINVAL, FDF_ENOMEM, FDF_ECUDA, FDF_ESTATE, FDF_ETIMEOUT, FDF_ENAN, FDF_ENOSYS = 0, -1, -2, -3, -4, -5, -6, -7
-FDF_PREC_F64, FDF_PREC_F32, FDF_PREC_BF16 = 0, 1, 2
+FDF_PREC_F64, FDF_PREC_F32, FDF_PREC_BF16, FDF_PREC_F32_FIXED, FDF_PREC_BF16_FIXED = 0, 1, 2, 3, 4
 FDF_FLAG_FIXED_AMPLITUDE, FDF_FLAG_LEGENDRE_DIPOLE = 1, 2
 FDF_Q_W_EPS, FDF_Q_W, FDF_Q_EPS, FDF_Q_COUNT, FDF_Q_W_QX, FDF_Q_W_QY, FDF_Q_W_QZ = 0, 1, 2, 3, 4, 5, 6
 FDF_EOM_GEODESIC, FDF_EOM_CANONICAL, FDF_EOM_SR_NEWTON, FDF_EOM_Q_SIMPLE, FDF_EOM_NEWTONIAN = 0, 1, 2, 3, 4
@@ -126,6 +126,7 @@ def lib():
             "fdf_timing": (C.c_int, [_V, C.c_int32]),
             "fdf_kernel_time": (C.c_int, [_V, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "fdf_launch_count": (C.c_int64, [_V]),
+            "fdf_pipe_rates": (C.c_int, [_V, _D, _D, _D]),
             "fdf_error_string": (C.c_char_p, [C.c_int]),
             "fdf_last_error": (C.c_char_p, []),
             "fdf_destroy": (None, [_V]),
@@ -295,10 +296,26 @@ def fdf_build_fields(ctx, lna, out):
 
 
 def fdf_build_fields_noalloc(params, tables, lna, out, stream=None):
-    """out: a CUDA tensor of 8 N^3 float64 (the entry point allocates nothing)."""
-    p, dev = _ptr(out)
-    if not dev:
+    """out: a contiguous float64 CUDA tensor of 8 N^3 elements on the current device (the
+    entry point allocates nothing and writes all of it).  Anything else raises before the
+    library is called."""
+    if not (hasattr(out, "data_ptr") and hasattr(out, "is_cuda")):
+        raise TypeError("fdf_build_fields_noalloc writes device memory: pass a torch tensor")
+    if str(out.dtype) != "torch.float64":
+        raise ValueError("out must be float64, got %s" % out.dtype)
+    N = int(params.n_grid)
+    if out.numel() != 8 * N ** 3:
+        raise ValueError("out must hold 8 n_grid^3 = %d doubles, got %d" % (8 * N ** 3, out.numel()))
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    if not out.is_cuda:
         raise ValueError("fdf_build_fields_noalloc writes device memory: pass a CUDA tensor")
+    import torch
+
+    if out.device.index != torch.cuda.current_device():
+        raise ValueError("out is on cuda:%d but the current device is cuda:%d"
+                         % (out.device.index, torch.cuda.current_device()))
+    p = out.data_ptr()
     s = getattr(stream, "cuda_stream", stream)
     _check(lib().fdf_build_fields_noalloc(C.byref(params), C.byref(tables), float(lna), p, s),
            "fdf_build_fields_noalloc")
@@ -340,6 +357,14 @@ def fdf_kernel_time(ctx, which):
     n = C.c_int64(0)
     _check(lib().fdf_kernel_time(ctx, which, C.byref(ms), C.byref(n)), "fdf_kernel_time")
     return ms.value, n.value
+
+
+def fdf_pipe_rates(stream=None):
+    """(FP64 FMA/s, FP32 FMA/s, FP64->FP32->FP64 round trips/s) measured on the current device."""
+    s = getattr(stream, "cuda_stream", stream)
+    d, f, c = C.c_double(0), C.c_double(0), C.c_double(0)
+    _check(lib().fdf_pipe_rates(s, C.byref(d), C.byref(f), C.byref(c)), "fdf_pipe_rates")
+    return d.value, f.value, c.value
 
 
 def fdf_launch_count(ctx):

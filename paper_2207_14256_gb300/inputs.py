@@ -37,7 +37,9 @@ def base_params(**over) -> dict:
     return p
 
 
-PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
+#: Precision settings (include/fdf.h FDF_PREC_*): FP64 everywhere; FP32 or BF16 grids with
+#: an FP64 phase-space state; FP32 or BF16 grids with the split (fixed-point) state.
+PREC_F64, PREC_F32, PREC_BF16, PREC_F32_FIXED, PREC_BF16_FIXED = 0, 1, 2, 3, 4
 
 #: The four measured workloads.  The first is small enough for the oracle to
 #: run in full in seconds; the third (three species of 256^3 particles on a

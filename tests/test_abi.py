@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -91,9 +92,14 @@ def test_struct_layout_matches_c(fdf):
 def test_host_only_calls(fdf, inputs):
     assert fdf.fdf_error_string(0) == "ok"
     assert fdf.fdf_error_string(-4) == "call out of order"
-    p = fdf.make_params(inputs.config("c3_3x256"))
-    b = fdf.fdf_footprint(p)
     n = 3 * 256 ** 3
+    # FP64 state (x, q FP64, q0 FP32, p, id, and the sampler's fixed-point positions) in
+    # both halves of the sort's double buffer, plus 96-byte sort records
+    b = fdf.fdf_footprint(fdf.make_params(inputs.config("c3_3x256")))
+    assert b > n * 2 * (24 + 24 + 12 + 12 + 8 + 4)
+    assert b < 24 * 2 ** 30
+    # the split state: 36 bytes of positions and momenta per particle
+    b = fdf.fdf_footprint(fdf.make_params(inputs.config("c3_3x256", precision=fdf.FDF_PREC_F32_FIXED)))
     assert b > n * (12 + 12 + 12 + 24 + 8 + 4)
     assert b < 16 * 2 ** 30
     bad = fdf.make_params(inputs.config("c1_32", n_grid=48))
@@ -109,7 +115,8 @@ def test_host_only_calls(fdf, inputs):
         fdf.fdf_footprint(bad)
     for knob in (dict(interp_order=3), dict(sort_tile=4), dict(sort_cells=-1), dict(steps_per_pass=5),
                  dict(superstep_tol=-0.1), dict(superstep_tol=float("nan")), dict(eom=6), dict(eom=-1),
-                 dict(precision=0, eom=5, steps_per_pass=3)):
+                 dict(precision=0, eom=5, steps_per_pass=3), dict(precision=5), dict(precision=-1),
+                 dict(flags=4)):
         with pytest.raises(fdf.FdfError) as e:
             fdf.fdf_footprint(fdf.make_params(inputs.config("c1_32", **knob)))
         assert e.value.code == fdf.FDF_EINVAL, knob
@@ -161,3 +168,23 @@ def test_binding_constants_match_the_header(fdf):
     assert checked >= 30
     for name in declared_symbols():
         assert hasattr(fdf, name), name
+
+
+def test_noalloc_binding_refuses_bad_outputs_without_a_kernel(fdf, inputs, c1_tables):
+    """The binding checks fdf_build_fields_noalloc's output tensor before the library is
+    called: a wrong dtype, size or device would let the kernels write past it."""
+    torch = pytest.importorskip("torch")
+    p = inputs.config("c1_32", n_grid=16, precision=1)
+    P = fdf.make_params(p)
+    T, keep = fdf.make_tables(c1_tables)
+    N = p["n_grid"]
+    with pytest.raises(TypeError):
+        fdf.fdf_build_fields_noalloc(P, T, -10.0, np.zeros(8 * N ** 3))
+    with pytest.raises(ValueError, match="float64"):
+        fdf.fdf_build_fields_noalloc(P, T, -10.0, torch.zeros(8 * N ** 3, dtype=torch.float32))
+    with pytest.raises(ValueError, match="8 n_grid"):
+        fdf.fdf_build_fields_noalloc(P, T, -10.0, torch.zeros(8, dtype=torch.float64))
+    with pytest.raises(ValueError, match="contiguous"):
+        fdf.fdf_build_fields_noalloc(P, T, -10.0, torch.zeros(16 * N ** 3, dtype=torch.float64)[::2])
+    with pytest.raises(ValueError, match="device memory"):
+        fdf.fdf_build_fields_noalloc(P, T, -10.0, torch.zeros(8 * N ** 3, dtype=torch.float64))

@@ -35,11 +35,12 @@ def _same(a, b):
     assert np.max(np.abs(da - db)) <= 1e-12 * np.max(np.abs(db))
 
 
-CASES = [dict(precision=1), dict(precision=1, superstep_tol=0.01), dict(precision=2), dict(precision=0),
-         dict(precision=0, eom=5)]
+CASES = [dict(precision=1), dict(precision=1, superstep_tol=0.01), dict(precision=2), dict(precision=3),
+         dict(precision=4), dict(precision=0), dict(precision=0, eom=5)]
 
 
-@pytest.mark.parametrize("over", CASES, ids=["f32", "f32-supersteps", "bf16", "f64", "f64-exact"])
+@pytest.mark.parametrize("over", CASES, ids=["f32", "f32-supersteps", "bf16", "f32-fixed", "bf16-fixed", "f64",
+                                             "f64-exact"])
 def test_replay_equals_the_sequential_run(F, inputs, c1_tables, over):
     p = inputs.config("c1_32", n_part=9001, n_species=2, m_ev=[0.05, 0.2], n_grid=32, n_steps=37, seed=171,
                       **over)

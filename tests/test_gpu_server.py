@@ -42,6 +42,8 @@ def _mix(inputs):
                       precision=1),
         inputs.config("c2_128", n_part=5000, n_grid=16, n_species=3, m_ev=[0.02, 0.1, 0.3], n_steps=31, seed=73,
                       precision=2),
+        inputs.config("c2_128", n_part=7001, n_grid=16, n_species=2, m_ev=[0.04, 0.15], n_steps=19, seed=75,
+                      precision=3),
         inputs.config("c2_128", n_part=4096, n_grid=32, n_species=1, m_ev=[0.08], n_steps=12, seed=74,
                       precision=0),
     ]
@@ -66,11 +68,11 @@ def test_each_request_is_the_same_alone_and_in_the_mix(F, inputs):
             assert info.status == F.FDF_REQ_DONE, info.message
             alone.append(_results(F, srv, rid))
             srv.release(rid)
-    with F.Server(4 * GiB, max_active=4, slice_steps=5) as srv:
-        ids = [srv.submit(p, tables) for p in reqs[:3]]
+    with F.Server(4 * GiB, max_active=5, slice_steps=5) as srv:
+        ids = [srv.submit(p, tables) for p in reqs[:-1]]
         # one request arrives while the others are on the GPU
         got = srv.wait(120000)
-        ids.append(srv.submit(reqs[3], tables))
+        ids.append(srv.submit(reqs[-1], tables))
         finished = {got}
         while len(finished) < len(ids):
             r = srv.wait(120000)
