@@ -32,18 +32,30 @@ from paper_2207_14256_gb300 import inputs as I  # noqa: E402
 METRIC = "neutrino particle-steps/s at 256^3 vs plain FP64 GPU form; served p99 latency"
 UNIT = "particle-steps/s"
 WORKLOAD = "c3_3x256"
-# Algorithmic bytes of the method per unit of work, by precision form (0 FP64, 1 FP32,
-# 2 BF16 grids): a particle-step reads and writes x and q at FP64 and reads q0 at FP32
-# (108 B; 120 B with q0 at FP64), and a kick reads the seven gradient fields of every
-# cell once (28 B per cell at FP32, 14 B at BF16, 56 B at FP64).
-PARTICLE_STEP_BYTES = {1: 108, 2: 108, 0: 120}
-GRID_READ_BYTES_PER_CELL = {1: 28, 2: 14, 0: 56}
+# Algorithmic bytes of the method per unit of work, by precision setting (0 FP64; 1, 2 FP32/BF16
+# grids with the FP64 state; 3, 4 the split state with FP32/BF16 grids): a particle-step reads
+# and writes x and q at FP64 and reads q0 at FP32 (108 B; 120 B with q0 at FP64), and a kick
+# reads the seven gradient fields of every cell once (28 B per cell at FP32, 14 B at BF16, 56 B
+# at FP64).
+PARTICLE_STEP_BYTES = {0: 120, 1: 108, 2: 108, 3: 108, 4: 108}
+GRID_READ_BYTES_PER_CELL = {0: 56, 1: 28, 2: 14, 3: 28, 4: 14}
+FORM_NAMES = {0: "FP64 grids and state", 1: "FP32 grids, FP64 state", 2: "BF16 grids, FP64 state",
+              3: "FP32 grids, split state (fixed-point x, FP32 q0 + dq)",
+              4: "BF16 grids, split state (fixed-point x, FP32 q0 + dq)"}
+# FP64-pipe instructions of the FP64-state pass (k_push_wide), counted in its source: a drift
+# takes 19 (|q|^2 3, the centre's argument 1, the inverse square root 4, t 2, five FP64 terms
+# of the polynomial 5, D 1, x += q D 3) and a kick 17 (argument 1, inverse square root 4, t 2,
+# two FP64 terms of each of two polynomials 4, K_phi 1, K_psi 2, q += dq 3); |q0|^2 takes 3
+# per particle and pass.  Conversions run on the integer pipe.  ncu's count of FP64-pipe
+# instructions (profiles/) checks these figures.
+WIDE_FP64_PER_STEP = 36
+WIDE_FP64_PER_PASS = 3
 
-# DRAM bytes per particle pass of the FP32 split form, from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean over the 50 passes of a one-species 256^3 run, profiles/
-# k_push_split_1x256.md; schedule of the autotuner, sort_tile = 1 and sort_cells = 3), per particle of the launch.  Valid only for the kernel sources
-# it was measured on: their hash is checked and the figure dropped if they changed.
-PUSH_TRAFFIC = {"bytes_per_particle": 3.832e9 / 256 ** 3, "sources_sha256": "592657e412cf2c27:d27dd9ad17a7f14f:bac8a9f67003931c"}
+# DRAM bytes per particle pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# over the passes of a run; profiles/), per particle of the launch, by precision setting.  Valid
+# only for the kernel sources they were measured on: their hash is checked and the figure
+# dropped if they changed.
+PUSH_TRAFFIC = {3: {"bytes_per_particle": 3.832e9 / 256 ** 3, "sources_sha256": "592657e412cf2c27:d27dd9ad17a7f14f:bac8a9f67003931c"}}
 PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
 
 
@@ -56,9 +68,9 @@ def push_sources_hash():
 
 def describe(p):
     return ("%d species x %d^3 particles on a %d^3 grid, box %g Mpc, m = %s eV, %d steps in log a from z = %g "
-            "to %g, %s grids" % (p["n_species"], round(p["n_part"] ** (1 / 3)), p["n_grid"], p["box"],
-                                 "/".join("%g" % m for m in p["m_ev"]), p["n_steps"], p["z_start"], p["z_end"],
-                                 {0: "FP64", 1: "FP32", 2: "BF16"}[p["precision"]]))
+            "to %g, %s" % (p["n_species"], round(p["n_part"] ** (1 / 3)), p["n_grid"], p["box"],
+                           "/".join("%g" % m for m in p["m_ev"]), p["n_steps"], p["z_start"], p["z_end"],
+                           FORM_NAMES[p["precision"]]))
 
 
 # ----------------------------------------------------------------------------------------------
@@ -159,6 +171,76 @@ def run_graph_once(fdf, ctx, p, out_dev):
     fdf.fdf_deposit(ctx, -1, fdf.FDF_Q_W_EPS, out_dev)
 
 
+def time_form(fdf, torch, P, T, stream, p, dep, runs, warmup, barrier):
+    """ms per whole run (fdf_run_graph replays + deposit, CUDA events on the context's
+    stream) and the per-kernel times of one instrumented run after them."""
+    ctx = fdf.fdf_create(P, T, stream)
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                run_graph_once(fdf, ctx, p, dep)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(runs):
+                run_graph_once(fdf, ctx, p, dep)
+            e1.record(stream)
+            barrier()
+            ms = e0.elapsed_time(e1) / runs
+            fdf.fdf_timing(ctx, True)
+            run_once(fdf, ctx, p, dep)
+            barrier()
+            ktimes = {k: fdf.fdf_kernel_time(ctx, v) for k, v in fdf.KERNEL_CLASSES.items()}
+            fdf.fdf_timing(ctx, False)
+    finally:
+        fdf.fdf_destroy(ctx)
+    return ms, ktimes
+
+
+def hbm_roofline(p, ktimes, hbm):
+    """The particle pass against HBM: the method's algorithmic bytes per launch (SURVEY's
+    108 B per particle-step + 28 B per cell per kick at FP32) over its mean launch time."""
+    prec = p["precision"]
+    push_ms, push_n = ktimes["push"]
+    push_avg = push_ms / max(push_n, 1)
+    n_total = p["n_species"] * p["n_part"]
+    N3 = p["n_grid"] ** 3
+    # a run takes n_steps particle-steps per particle and n_steps + 1 grid reads (the opening
+    # half kick and one merged kick per step), over push_n launches
+    alg = (p["n_steps"] * n_total * PARTICLE_STEP_BYTES[prec] +
+           (p["n_steps"] + 1) * N3 * GRID_READ_BYTES_PER_CELL[prec]) / max(push_n, 1)
+    achieved = alg / (push_avg / 1e3) / 1e9
+    tr = PUSH_TRAFFIC.get(prec)
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if hbm else None,
+            "traffic": (tr["bytes_per_particle"] * n_total if tr and push_sources_hash() == tr["sources_sha256"]
+                        else None),
+            "traffic_note": "ncu DRAM bytes per pass (profiles/), per particle of the launch, scaled to the "
+                            "launch; null when the kernel sources changed since the capture",
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800",
+            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": push_avg,
+            "steps_per_launch": p["n_steps"] / max(push_n, 1),
+            "per_unit": "%d B per particle-step + %d B per cell per kick" % (PARTICLE_STEP_BYTES[prec],
+                                                                           GRID_READ_BYTES_PER_CELL[prec])}
+
+
+def fp64_roofline(p, ktimes, dfma_per_s):
+    """The FP64-state pass against the FP64 pipe: FP64-pipe instructions per launch (counted
+    in k_push_wide's source) over its mean launch time, against the measured DFMA issue rate."""
+    push_ms, push_n = ktimes["push"]
+    push_avg = push_ms / max(push_n, 1)
+    n_total = p["n_species"] * p["n_part"]
+    ops = (WIDE_FP64_PER_STEP * p["n_steps"] * n_total + WIDE_FP64_PER_PASS * n_total * push_n) / max(push_n, 1)
+    achieved = ops / (push_avg / 1e3) / 1e9
+    peak = dfma_per_s / 1e9 if dfma_per_s else None
+    return {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak,
+            "unit": "G FP64-pipe instructions/s", "frac": achieved / peak if peak else None,
+            "peak_source": "measured in this run: fdf_pipe_rates (dependent DFMA chains on every SM, CUDA events)",
+            "per_unit": "%d FP64-pipe instructions per particle-step + %d per particle per pass (k_push_wide's "
+                        "source; ncu's count in profiles/)" % (WIDE_FP64_PER_STEP, WIDE_FP64_PER_PASS),
+            "instructions_per_launch": ops, "avg_launch_ms": push_avg}
+
+
 def bench_ours(args, rank, world, dist):
     import torch
 
@@ -183,6 +265,13 @@ def bench_ours(args, rank, world, dist):
     N = p["n_grid"]
     dep = torch.zeros((N, N, N), dtype=torch.float64, device=dev)
     units = p["n_species"] * p["n_part"] * p["n_steps"]
+    # the issue rates of the FP64 pipe (the denominator of the FP64-state pass's roofline),
+    # the FP32 pipe and FP64 <-> FP32 conversions on this GPU
+    d_rate, f_rate, c_rate = fdf.fdf_pipe_rates(stream)
+    pipes = {"dfma_per_s": d_rate, "fp64_tflops": 2 * d_rate / 1e12, "ffma_per_s": f_rate,
+             "cvt_round_trips_per_s": c_rate,
+             "note": "fdf_pipe_rates: best of five launches of 64 warps per SM running 8 independent chains "
+                     "per thread; a conversion round trip is FP64 -> FP32 -> FP64"}
 
     def barrier():
         torch.cuda.synchronize()
@@ -284,7 +373,8 @@ def bench_ours(args, rank, world, dist):
                 push64 = fdf.fdf_kernel_time(c3, fdf.FDF_K_PUSH)
         finally:
             fdf.fdf_destroy(c3)
-        plain = {"value": units / (pms / 1e3), "ms_per_step": pms, "push_ms_per_launch": push64[0] / push64[1]}
+        plain = {"value": units / (pms / 1e3), "ms_per_step": pms, "push_ms_per_launch": push64[0] / push64[1],
+                 "push_launches": push64[1]}
 
     # the paper's super-steps (Sec. 2.1: fields built only where the transfer functions
     # changed by more than 1%, interpolated in between), same workload and schedule
@@ -313,9 +403,42 @@ def bench_ours(args, rank, world, dist):
                      "note": "the same workload with the paper's super-steps (not the headline: the headline builds "
                              "every step's fields by transform)"}
 
+    # the split-state form (fixed-point positions, FP32 q0 + dq) on the same workload and
+    # schedule knobs: not the configured precision, reported beside it
+    split = None
+    if not args.no_split:
+        psp = dict(p, precision=I.PREC_F32_FIXED)
+        Psp = fdf.make_params(psp)
+        for k, v in fdf.knobs(P).items():
+            if k != "n_gl":
+                setattr(Psp, k, v)
+        sms, skt = time_form(fdf, torch, Psp, T, stream, psp, dep, 2, 1, barrier)
+        split = {"value": units / (sms / 1e3), "ms_per_step": sms, "precision": FORM_NAMES[psp["precision"]],
+                 "kernels": {k: {"ms_per_step": v[0], "launches_per_step": v[1]} for k, v in skt.items()},
+                 "roofline_hbm": hbm_roofline(psp, skt, peaks().get("hbm_gbs"))}
+
+    # the reduced-precision workload (BF16 gradient grids, FP64 state; 512^3 particles on 256^3, 300 steps)
+    c4 = None
+    if not args.no_c4:
+        p4 = rank_params("c4_512_bf16", rank)
+        P4 = fdf.make_params(p4)
+        for k, v in fdf.knobs(P).items():
+            if k != "n_gl":
+                setattr(P4, k, v)
+        T4, keep4 = fdf.make_tables(I.transfer_tables(p4))
+        N4 = p4["n_grid"]
+        dep4 = torch.zeros((N4, N4, N4), dtype=torch.float64, device=dev)
+        ms4, kt4 = time_form(fdf, torch, P4, T4, stream, p4, dep4, 1, 1, barrier)
+        units4 = p4["n_species"] * p4["n_part"] * p4["n_steps"]
+        c4 = {"workload": "c4_512_bf16", "description": describe(p4), "value": units4 / (ms4 / 1e3),
+              "ms_per_step": ms4, "schedule": fdf.knobs(P4),
+              "kernels": {k: {"ms_per_step": v[0], "launches_per_step": v[1]} for k, v in kt4.items()},
+              "roofline_hbm": hbm_roofline(p4, kt4, peaks().get("hbm_gbs"))}
+        del dep4
+
     return dict(p=p, ms=ms, units=units, launches=launches, ktimes=ktimes, inst_ms=inst_ms, phases=phases,
-                clocks=clk, e2e_s=e2e_s,
-                tune=tune, host_ms=host_ms, superstep=superstep,
+                clocks=clk, e2e_s=e2e_s, pipes=pipes,
+                tune=tune, host_ms=host_ms, superstep=superstep, split=split, c4=c4,
                 e2e_steps=e2e_steps, tab_bytes=tab_bytes, d2h=p["n_species"] * np_ * 7 * 8, plain=plain)
 
 
@@ -446,6 +569,8 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served stream")
     ap.add_argument("--no-tune", action="store_true", help="use the automatic schedule knobs")
     ap.add_argument("--no-superstep", action="store_true", help="skip the super-step variant")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-state form")
+    ap.add_argument("--no-c4", action="store_true", help="skip the reduced-precision workload")
     ap.add_argument("--schedule", default="", help='schedule knobs as JSON, e.g. {"sort_tile": 1} (no tuning)')
     ap.add_argument("--served-requests", type=int, default=64)
     ap.add_argument("--n-species", type=int, default=0,
@@ -496,46 +621,30 @@ def main():
             dist.destroy_process_group()
         return
 
-    prec = r["p"]["precision"]
     pk = peaks()
     hbm = pk.get("hbm_gbs")
-    push_ms, push_n = r["ktimes"]["push"]
-    push_avg = push_ms / max(push_n, 1)
+    roof = fp64_roofline(r["p"], r["ktimes"], r["pipes"]["dfma_per_s"])
+    roof["kernel"] = "k_push_wide (fused drift + wrap + gather + kick over a pass of leapfrog steps, FP64 state)"
+    roof["launch_timing"] = ("CUDA events around every launch of one run on the context's stream, right after the "
+                             "timed region")
+    roof_hbm = hbm_roofline(r["p"], r["ktimes"], hbm)
+    roof_hbm["kernel"] = roof["kernel"]
     n_total = r["p"]["n_species"] * r["p"]["n_part"]
-    N3 = r["p"]["n_grid"] ** 3
-    # the instrumented run takes n_steps particle-steps per particle and n_steps + 1 grid
-    # reads (the opening half kick and one merged kick per step), over push_n launches
-    steps = r["p"]["n_steps"]
-    kicks = r["p"]["n_steps"] + 1
-    alg_total = steps * n_total * PARTICLE_STEP_BYTES[prec] + kicks * N3 * GRID_READ_BYTES_PER_CELL[prec]
-    alg = alg_total / max(push_n, 1)
-    achieved = alg / (push_avg / 1e3) / 1e9
-    roof = {"kernel": "k_push_split (fused drift + wrap + gather + kick over a pass of leapfrog steps)",
-            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm if hbm else None,
-            "traffic": (PUSH_TRAFFIC["bytes_per_particle"] * n_total
-                        if prec == 1 and push_sources_hash() == PUSH_TRAFFIC["sources_sha256"] else None),
-            "traffic_note": "ncu DRAM bytes per pass, mean over a run, one species scaled to all by particles",
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800",
-            "algorithmic_bytes_per_launch": alg, "avg_launch_ms": push_avg,
-            "launch_timing": "CUDA events around every launch of one run on the context's stream, right after "
-                             "the timed region",
-            "steps_per_launch": steps / max(push_n, 1),
-            "per_unit": "%d B per particle-step + %d B per cell per kick" % (PARTICLE_STEP_BYTES[prec],
-                                                                           GRID_READ_BYTES_PER_CELL[prec])}
     per_run = {k: {"ms_per_step": v[0], "launches_per_step": v[1]} for k, v in r["ktimes"].items()}
     per_run["note"] = ("one instrumented run after the timed region (sequential calls, an event pair per launch: "
                        "%.1f ms for the run)" % r["inst_ms"])
     out = line_base(args, world)
     out.update({
-        "value": value, "ms_per_step": ms_per_step, "dtype": "f32",
+        "value": value, "ms_per_step": ms_per_step, "dtype": "f64 state, f32 grids",
         "config": {"workload": args.workload, "description": describe(r["p"]),
-                   "l2": "inputs larger than L2 (%.1f GB particle state)" % (n_total * 48 / 1e9),
+                   "l2": "inputs larger than L2 (%.1f GB particle state: x, q FP64, q0 FP32)" % (n_total * 60 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single",
                    "schedule": r["tune"] or "automatic",
                    "timed_call": "fdf_run_graph (sample + steps replayed as one recorded CUDA graph) + fdf_deposit "
                                  "per step"},
         "roofline": roof,
+        "roofline_hbm": roof_hbm,
+        "pipe_rates": r["pipes"],
         "e2e": {"value": whole_job_value(world, r["units"], e2e_s), "unit": UNIT, "h2d_bytes_per_step": r["tab_bytes"],
                 "d2h_bytes_per_step": r["d2h"],
                 "note": "fdf_create on a caller-held device arena (table upload) + sample + steps + fdf_get of "
@@ -555,6 +664,14 @@ def main():
         out["plain_f64"] = dict(r["plain"], value=world * r["plain"]["value"],
                                 note="the plain FP64 form (FP64 grids, FFT, state and arithmetic), same workload")
         out["speedup_vs_plain_f64"] = value / out["plain_f64"]["value"]
+    if r["split"]:
+        out["split_state"] = dict(r["split"], value=world * r["split"]["value"],
+                                  note="the split-state form (FDF_PREC_F32_FIXED) on the same workload and schedule: "
+                                       "positions as 32-bit fixed point, momenta as FP32 q0 + dq, float-float drift "
+                                       "and FP32 kick integrals; not the configured precision")
+    if r["c4"]:
+        out["c4"] = dict(r["c4"], value=world * r["c4"]["value"],
+                         note="the reduced-precision workload, timed as the headline (graph replays + deposit)")
     if not args.no_served and world == 1:
         out["served"] = bench_served(args.served_requests)
     if not args.no_cpu and world == 1:

@@ -284,9 +284,12 @@ FDF_API int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w
 FDF_API int fdf_get_initial(fdf_ctx* c, int32_t species, uint32_t* X, double* q_sampled, double* p, int32_t out_on_device);
 
 /* Test and inspection hook: the eight real fields at ln a, as built on the
- * device for the particle pass, converted to FP64: out[8][N^3] in the slot
- * order (d_x psi, d_y psi, d_z psi, d_x phi, d_y phi, d_z phi, phi_dot, psi),
- * phi_dot = a H d phi / d ln a.  Field convention f(x) = sum_n f_n e^{i k.x}. */
+ * device, converted to FP64: out[8][N^3] in the slot order (d_x psi, d_y psi,
+ * d_z psi, d_x phi, d_y phi, d_z phi, phi_dot, psi), phi_dot = a H d phi / d ln a.
+ * Field convention f(x) = sum_n f_n e^{i k.x}.  Slots 0-6 come from a build as the
+ * steps' particle passes read it (phi_dot, packed with slot 7 in one complex
+ * transform, is transformed alone there); slot 7 (psi, which the initial transform
+ * reads) from a second build. */
 FDF_API int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device);
 
 /* fdf_build_fields without a context and without allocating: for callers that
@@ -295,10 +298,11 @@ FDF_API int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on
  * forbids cudaMalloc/cudaFree after start-up because those calls synchronise
  * the device and fragment its memory.  The paper has no counterpart; this is
  * an interface convenience.
- *  p, t: as for fdf_create (host memory; t's arrays are uploaded on each call,
- *  cdf_t and cdf_F are not used).  lna: ln a of the fields.  out: DEVICE memory
- *  of 8 N^3 doubles, written as by fdf_build_fields.  stream: a cudaStream_t or
- *  NULL.  The call synchronises that stream before returning.
+ *  p, t: as for fdf_create (host memory; cdf_t and cdf_F are not used).  lna:
+ *  ln a of the fields.  out: DEVICE memory of 8 N^3 doubles on the current
+ *  device, written as by fdf_build_fields.  stream: a cudaStream_t or NULL.
+ *  Every call copies t's transfer tables and the FFT twiddles from host memory
+ *  into the array, and synchronises stream before returning.
  *  Work arrays live in one static device array of FDF_NOALLOC_SCRATCH_BYTES
  *  that every GPU loading the library holds until the process exits; the call
  *  performs no cudaMalloc or cudaFree.  FDF_EINVAL, with a message naming both
@@ -320,6 +324,15 @@ FDF_API int fdf_set_fields(fdf_ctx* c, const double* fields, int32_t on_device);
  * by transform (every step when superstep_tol = 0), for j = 0..min(len, n_steps+1)-1;
  * *count = the number of such steps.  Either pointer may be NULL. */
 FDF_API int fdf_supersteps(fdf_ctx* c, int32_t* is_super, int32_t len, int32_t* count);
+
+/* Which particle-pass kernel the last fdf_step (or the run of fdf_run_graph) used:
+ * info[0] the state form (0 plain FP64, 1 FP64 state with FP32/BF16 grids, 2 split
+ * state), info[1] 1 if every pass evaluated its step integrals as series or fitted
+ * polynomials (FDF_PREC_F32/BF16: the polynomials of include/fdf.h's precision notes;
+ * split state: the drift's power series) and 0 if any pass summed them node by node,
+ * info[2] the number of passes, info[3] the most leapfrog steps in one pass.  info:
+ * 4 host int32.  The paper has no counterpart (an inspection hook for tests). */
+FDF_API int fdf_pass_info(fdf_ctx* c, int32_t* info);
 
 /* Current step index (0..n_steps) and its ln a. */
 FDF_API int fdf_state(fdf_ctx* c, int32_t* step, double* lna);

@@ -360,7 +360,7 @@ struct fdf_ctx {
     std::vector<double> tab_host;     // T_psi, T_phi, dT_phi/dln a on the host (super-step schedule)
     std::vector<int> is_super;        // super-step schedule, n_steps + 1 entries
     bool supersteps = false;
-    bool sum7 = false;                   // the steps' grids carry phi + psi in slot 7 (FDF_EOM_EXACT)
+    int slot7 = kSlot7Psi;               // what the grids built next carry in slot 7
     void* Gss[2] = {nullptr, nullptr};
     int ssk[2] = {-1, -1};            // the step each super-step grid holds
     double lnk0 = 0, dlnk = 0, lnat0 = 0, dlnat = 0;
@@ -405,6 +405,8 @@ struct fdf_ctx {
     bool stepped = false;
     int k = 0;
     int64_t launches = 0;
+    // the passes of the last fdf_step: all with series integrals, count, most steps in one
+    int pass_series = 1, pass_count = 0, pass_steps = 0;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> pool;
@@ -418,11 +420,12 @@ struct fdf_ctx {
         cudaStream_t own = nullptr;      // records and replays a run queued on the legacy stream
         int gk[kMaxBuf];
         int ssk[2];
-        bool sum7 = false;
+        int slot7 = kSlot7Psi;
         int k = 0;
         double disp = 0;
         ParticleState st{}, st_alt{};
         int64_t launches = 0, sorts = 0;
+        int pass_series = 1, pass_count = 0, pass_steps = 0;
     } graph;
 
     double hubble(double a) const
@@ -642,8 +645,8 @@ int draw_noise(fdf_ctx* c)
     return rc;
 }
 
-// The eight fields at ln a into G, on stream s; slot 7 is phi + psi if sum7, else psi.
-int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s, bool sum7)
+// The eight fields at ln a into G, on stream s; slot 7 as `slot7` says (kSlot7*).
+int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s, int slot7)
 {
     if (!c->noise_ready) {
         if (s != c->sf) FDF_CUDA(cudaStreamSynchronize(c->stream), "sync");
@@ -652,7 +655,7 @@ int build_fields(fdf_ctx* c, double lna, void* G, cudaStream_t s, bool sum7)
         if (s != c->sf) FDF_CUDA(cudaStreamSynchronize(c->sf), "sync");
     }
     FieldArgs a = make_field_args(c->p, c->nk, c->na, c->lnk0, c->dlnk, c->lnat0, c->dlnat, lna);
-    a.slot7_sum = sum7 ? 1 : 0;
+    a.slot7 = slot7;
     const int prec = grid_prec(c->p.precision);
     int rc = timed_on(c, s, FDF_K_FIELDS_Z, "mode table",
                       [&] { return launch_mode_table(s, prec, a, c->tabs, c->modeA); });
@@ -748,7 +751,7 @@ void superstep_schedule(fdf_ctx* c)
 // two super-step grids as needed (a step that is itself a super-step is the copy w = 0).
 int produce_grid(fdf_ctx* c, int k, void* G)
 {
-    if (!c->supersteps) return build_fields(c, c->lna(k), G, c->sf, c->sum7);
+    if (!c->supersteps) return build_fields(c, c->lna(k), G, c->sf, c->slot7);
     int s = k, e = k;
     while (!c->is_super[s]) --s;
     while (!c->is_super[e]) ++e;
@@ -765,7 +768,7 @@ int produce_grid(fdf_ctx* c, int k, void* G)
         }
         const int i = slot[1 - n] == 0 ? 1 : 0;   // the grid the other end does not use
         c->ssk[i] = -1;
-        int rc = build_fields(c, c->lna(need[n]), c->Gss[i], c->sf, c->sum7);
+        int rc = build_fields(c, c->lna(need[n]), c->Gss[i], c->sf, c->slot7);
         if (rc) return rc;
         c->ssk[i] = need[n];
         slot[n] = i;
@@ -1140,7 +1143,7 @@ int sample_enqueue(fdf_ctx* c)
     const void* G0 = nullptr;
     int b0 = -1;
     if (c->st.sd) FDF_CUDA(cudaMemsetAsync(c->st.sd, 0, (size_t)c->n * 8, c->stream), "clearing phi + psi");
-    c->sum7 = false;                     // the initial transform reads psi from slot 7
+    c->slot7 = kSlot7Psi;                // the initial transform reads psi from slot 7
     rc = ensure_grid(c, 0, 0u, &G0, &b0);
     if (rc) return rc;
     rc = acquire_grid(c, b0);
@@ -1157,9 +1160,13 @@ int sample_enqueue(fdf_ctx* c)
     if (rc) return rc;
     if (c->p.eom == FDF_EOM_EXACT) {
         // the steps' grids carry phi + psi in slot 7: none built so far may be reused
-        c->sum7 = true;
+        c->slot7 = kSlot7Sum;
         for (int i = 0; i < kMaxBuf; ++i) c->gk[i] = -1;
         c->ssk[0] = c->ssk[1] = -1;
+    } else {
+        // the steps' passes read no slot 7: phi_dot is transformed alone from here on (the
+        // grid of step 0, built with psi, serves the opening half kick as it is)
+        c->slot7 = kSlot7Zero;
     }
     c->k = 0;
     if (sort0 && !split) {
@@ -1201,6 +1208,9 @@ int fdf_step(fdf_ctx* c, int32_t n)
     if (target < 0 || target > c->p.n_steps) return fail(FDF_EINVAL, "step index would leave [0, n_steps]");
     if (n == 0) return FDF_OK;
     c->stepped = true;
+    c->pass_series = 1;
+    c->pass_count = 0;
+    c->pass_steps = 0;
     const int dir = n > 0 ? 1 : -1;
     const int steps = n > 0 ? n : -n;
     const int k_start = c->k;
@@ -1281,6 +1291,11 @@ int fdf_step(fdf_ctx* c, int32_t n)
             if (a.sub[u].emax > kSeriesMaxE) a.drift_series = 0;
             if (!a.sub[u].wide_ok) a.wide_series = 0;
         }
+        const int form = form_of(c->p.precision);
+        if ((form == kWide && !a.wide_series) || (form == kFixed && !a.drift_series) || form == kPlain)
+            c->pass_series = 0;
+        ++c->pass_count;
+        c->pass_steps = std::max(c->pass_steps, pass_len(j));
         for (int b : bufs_cur) {
             rc = acquire_grid(c, b);
             if (rc) return rc;
@@ -1367,13 +1382,16 @@ int fdf_run_graph(fdf_ctx* c, int32_t n)
         g.n = n;
         std::memcpy(g.gk, c->gk, sizeof(g.gk));
         std::memcpy(g.ssk, c->ssk, sizeof(g.ssk));
-        g.sum7 = c->sum7;
+        g.slot7 = c->slot7;
         g.k = c->k;
         g.disp = c->disp;
         g.st = c->st;
         g.st_alt = c->st_alt;
         g.launches = captured;
         g.sorts = sorted;
+        g.pass_series = c->pass_series;
+        g.pass_count = c->pass_count;
+        g.pass_steps = c->pass_steps;
     }
     FDF_CUDA(cudaGraphLaunch(g.exec, c->stream), "launching the run's graph");
     // later work on the fields stream follows the run, and the grids the run left in
@@ -1385,13 +1403,16 @@ int fdf_run_graph(fdf_ctx* c, int32_t n)
     std::memcpy(c->gk, g.gk, sizeof(g.gk));
     std::memcpy(c->ssk, g.ssk, sizeof(g.ssk));
     for (int b = 0; b < kMaxBuf; ++b) c->has_release[b] = false;
-    c->sum7 = g.sum7;
+    c->slot7 = g.slot7;
     c->k = g.k;
     c->disp = g.disp;
     c->st = g.st;
     c->st_alt = g.st_alt;
     c->launches += g.launches;
     c->sorts += g.sorts;
+    c->pass_series = g.pass_series;
+    c->pass_count = g.pass_count;
+    c->pass_steps = g.pass_steps;
     c->noise_ready = true;
     c->sampled = true;
     c->stepped = n > 0;
@@ -1559,12 +1580,19 @@ int fdf_build_fields(fdf_ctx* c, double lna, double* out, int32_t out_on_device)
     for (int i = 0; i < c->nbuf; ++i)
         if (c->gk[i] != c->k) buf = i;
     c->gk[buf] = -1;
-    int rc = build_fields(c, lna, c->G[buf], c->stream, false);
-    if (rc) return rc;
+    // slots 0-6 as the steps' passes read them (phi_dot transformed alone), then slot 7 (psi)
+    // from a second build, as the initial transform reads it
     double* dst = out;
     if (!out_on_device) FDF_CUDA(cudaMalloc(&dst, 8 * N3 * 8), "allocating the field copy");
-    rc = timed(c, FDF_K_OTHER, "field export",
-               [&] { return launch_fields_to_f64(c->stream, grid_prec(c->p.precision), N, c->G[buf], dst); });
+    int rc = FDF_OK;
+    for (int pass = 0; pass < 2 && rc == FDF_OK; ++pass) {
+        rc = build_fields(c, lna, c->G[buf], c->stream, pass == 0 ? kSlot7Zero : kSlot7Psi);
+        if (rc) break;
+        rc = timed(c, FDF_K_OTHER, "field export", [&] {
+            return launch_fields_to_f64(c->stream, grid_prec(c->p.precision), N, c->G[buf], dst,
+                                        pass == 0 ? 0x7Fu : 0x80u);
+        });
+    }
     if (!rc && !out_on_device) {
         cudaError_t e = cudaMemcpyAsync(out, dst, 8 * N3 * 8, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1618,6 +1646,17 @@ int fdf_supersteps(fdf_ctx* c, int32_t* is_super, int32_t len, int32_t* count)
         if (is_super && (int64_t)j < len) is_super[j] = c->is_super[j];
     }
     if (count) *count = n;
+    return FDF_OK;
+}
+
+int fdf_pass_info(fdf_ctx* c, int32_t* info)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!info) return fail(FDF_EINVAL, "info is NULL");
+    info[0] = form_of(c->p.precision);
+    info[1] = c->pass_series;
+    info[2] = c->pass_count;
+    info[3] = c->pass_steps;
     return FDF_OK;
 }
 

@@ -122,6 +122,14 @@ struct PushArgs {
     const void* G[kMaxSub];     // the grid each sub-step's kick reads
 };
 
+// What slot 7 of a gather grid holds.  It shares its packed transform with phi_dot
+// (phi_dot + i slot 7), and an FFT's rounding is relative to the larger of the two, so
+// the steps' grids of the separable forms, whose passes never read slot 7, carry zero
+// there and phi_dot is transformed alone.
+constexpr int kSlot7Psi = 0;    // psi: the initial transform (eq:transform) reads it
+constexpr int kSlot7Sum = 1;    // phi + psi: the drift factor of the exact equations of motion
+constexpr int kSlot7Zero = 2;   // nothing
+
 // Field-build arguments for one scale factor.
 struct FieldArgs {
     int N, logN;
@@ -136,7 +144,7 @@ struct FieldArgs {
     double lnkp;                // ln k_pivot
     uint32_t key0, key1;        // Philox key (seed)
     int fixed_amp;
-    int slot7_sum;              // slot 7 holds phi + psi instead of psi
+    int slot7;                  // slot 7: kSlot7Psi, kSlot7Sum (phi + psi) or kSlot7Zero
 };
 
 inline int ilog2_host(int v)
@@ -177,8 +185,9 @@ cudaError_t launch_fields_y(cudaStream_t s, int precision, const FieldArgs& a, c
                             void* W1);
 cudaError_t launch_fields_x(cudaStream_t s, int precision, const FieldArgs& a, const void* tw, const void* W1,
                             void* G);
-// G (any precision) <-> [8][N^3] FP64.
-cudaError_t launch_fields_to_f64(cudaStream_t s, int precision, int N, const void* G, double* out);
+// G (any precision) <-> [8][N^3] FP64; to_f64 writes the slots whose bit is set in mask.
+cudaError_t launch_fields_to_f64(cudaStream_t s, int precision, int N, const void* G, double* out,
+                                 unsigned mask = 0xFFu);
 // G = (1 - w) A + w B over whole gather grids (super-steps, Sec. 2.1)
 cudaError_t launch_interp_grid(cudaStream_t s, int precision, int N, const void* A, const void* B, double w,
                                void* G);

@@ -104,15 +104,20 @@ extern "C" int fdf_build_fields_noalloc(const fdf_params* p, const fdf_tables* t
         e = f64 ? cudaMemcpyAsync(s + oTw, twd.data(), twd.size() * 8, cudaMemcpyHostToDevice, st)
                 : cudaMemcpyAsync(s + oTw, twf.data(), twf.size() * 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(FDF_ECUDA, (std::string("table upload: ") + cudaGetErrorString(e)).c_str());
-    const FieldArgs a = make_field_args(*p, t->nk, t->na, lnk0, dlnk, lnat0, dlnat, lna);
+    FieldArgs a = make_field_args(*p, t->nk, t->na, lnk0, dlnk, lnat0, dlnat, lna);
     void* W0 = s + oW0;
     void* W1 = s + oW1;
     if (e == cudaSuccess) e = launch_noise(st, gp, a, s + oR);
     if (e == cudaSuccess) e = launch_mode_table(st, gp, a, T64, s + oA);
-    if (e == cudaSuccess) e = launch_fields_z(st, gp, a, s + oA, s + oR, s + oTw, W0);
-    if (e == cudaSuccess) e = launch_fields_y(st, gp, a, s + oTw, W0, W1);
-    if (e == cudaSuccess) e = launch_fields_x(st, gp, a, s + oTw, W1, W0);
-    if (e == cudaSuccess) e = launch_fields_to_f64(st, gp, p->n_grid, W0, out);
+    // as fdf_build_fields: slots 0-6 from a build with phi_dot transformed alone, slot 7
+    // (psi) from a second build
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+        a.slot7 = pass == 0 ? kSlot7Zero : kSlot7Psi;
+        e = launch_fields_z(st, gp, a, s + oA, s + oR, s + oTw, W0);
+        if (e == cudaSuccess) e = launch_fields_y(st, gp, a, s + oTw, W0, W1);
+        if (e == cudaSuccess) e = launch_fields_x(st, gp, a, s + oTw, W1, W0);
+        if (e == cudaSuccess) e = launch_fields_to_f64(st, gp, p->n_grid, W0, out, pass == 0 ? 0x7Fu : 0x80u);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return set_error(FDF_ECUDA, (std::string("fdf_build_fields_noalloc: ") + cudaGetErrorString(e)).c_str());

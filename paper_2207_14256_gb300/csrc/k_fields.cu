@@ -7,7 +7,8 @@
 // f_a + i f_b):
 //   P0 = d_x psi + i d_y psi     P1 = d_z psi + i d_x phi
 //   P2 = d_y phi + i d_z phi     P3 = phi_dot + i psi
-// (P3 = phi_dot + i (phi + psi) for the steps of the exact equations of motion)
+// (P3 = phi_dot + i (phi + psi) for the steps of the exact equations of motion, and
+// phi_dot + i 0 for the steps of the separable forms, whose passes read no slot 7)
 // with d_j f = sum_n i k_j T_f(k, a) R_n e^{i k.x}, phi_dot = a H dT_phi/dln a R.
 // R_n is a Hermitian Gaussian field drawn from Philox4x32-10 addressed by the
 // signed mode (so the realisation does not depend on the launch), with
@@ -395,13 +396,14 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
         // one branch per packed grid, so that each reads only the amplitudes it uses
         // (psi; psi and phi; phi; phi_dot and psi) from shared memory
         V v[N1];
-        // Q = 4 is grid 3 with slot 7 = phi + psi (the exact drift's factor)
+        // Q = 4 is grid 3 with slot 7 = phi + psi (the exact drift's factor), Q = 5 grid 3
+        // with slot 7 = 0 (phi_dot transformed alone)
         auto form = [&](auto Q) {
             constexpr int P = Q < 4 ? (int)Q : 3;
             sfor<N1>([&](auto I) {
                 const T kz = kf * (T)sidx(N2 * I + t, N);
                 const int o = I * NT + threadIdx.x;
-                const T apsi = (P == 2) ? T(0) : As[0 * N1 * NT + o];
+                const T apsi = (P == 2 || Q == 5) ? T(0) : As[0 * N1 * NT + o];
                 const T aphi = (P == 1 || P == 2 || Q == 4) ? As[1 * N1 * NT + o] : T(0);
                 const T adot = (P == 3) ? As[2 * N1 * NT + o] : T(0);
                 v[I] = packed<V>(P, Rv[I], Q == 4 ? apsi + aphi : apsi, aphi, adot, kx, ky, kz);
@@ -412,7 +414,8 @@ __global__ void __launch_bounds__(Shape<N>::THREADS_Z, sizeof(V) == 8 ? 4 : 2) k
             case 1: form(Idx<1>{}); break;
             case 2: form(Idx<2>{}); break;
             default:
-                if (a.slot7_sum) form(Idx<4>{});
+                if (a.slot7 == kSlot7Sum) form(Idx<4>{});
+                else if (a.slot7 == kSlot7Zero) form(Idx<5>{});
                 else form(Idx<3>{});
                 break;
         }
@@ -558,10 +561,11 @@ __device__ __forceinline__ double gval(const Gt* G, size_t cell, int s)
 }
 
 template <typename Gt>
-__global__ void k_fields_to_f64(size_t N3, const Gt* __restrict__ G, double* __restrict__ out)
+__global__ void k_fields_to_f64(size_t N3, const Gt* __restrict__ G, double* __restrict__ out, unsigned mask)
 {
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < N3; c += (size_t)gridDim.x * blockDim.x)
-        for (int s = 0; s < 8; ++s) out[s * N3 + c] = gval(G, c, s);
+        for (int s = 0; s < 8; ++s)
+            if (mask & (1u << s)) out[s * N3 + c] = gval(G, c, s);
 }
 
 template <typename Gt>
@@ -747,13 +751,14 @@ cudaError_t launch_fields_x(cudaStream_t s, int precision, const FieldArgs& a, c
 #undef X16
 }
 
-cudaError_t launch_fields_to_f64(cudaStream_t s, int precision, int N, const void* G, double* out)
+cudaError_t launch_fields_to_f64(cudaStream_t s, int precision, int N, const void* G, double* out, unsigned mask)
 {
     const size_t N3 = (size_t)N * N * N;
     const unsigned blocks = (unsigned)((N3 + 255) / 256 < 152 * 32 ? (N3 + 255) / 256 : 152 * 32);
-    if (precision == FDF_PREC_F64) k_fields_to_f64<double><<<blocks, 256, 0, s>>>(N3, (const double*)G, out);
-    else if (precision == FDF_PREC_F32) k_fields_to_f64<float><<<blocks, 256, 0, s>>>(N3, (const float*)G, out);
-    else k_fields_to_f64<__nv_bfloat16><<<blocks, 256, 0, s>>>(N3, (const __nv_bfloat16*)G, out);
+    if (precision == FDF_PREC_F64) k_fields_to_f64<double><<<blocks, 256, 0, s>>>(N3, (const double*)G, out, mask);
+    else if (precision == FDF_PREC_F32)
+        k_fields_to_f64<float><<<blocks, 256, 0, s>>>(N3, (const float*)G, out, mask);
+    else k_fields_to_f64<__nv_bfloat16><<<blocks, 256, 0, s>>>(N3, (const __nv_bfloat16*)G, out, mask);
     return cudaGetLastError();
 }
 

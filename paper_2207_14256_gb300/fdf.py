@@ -123,6 +123,7 @@ def lib():
             "fdf_build_fields_noalloc": (C.c_int, [P, T, C.c_double, _V, _V]),
             "fdf_supersteps": (C.c_int, [_V, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)]),
             "fdf_state": (C.c_int, [_V, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+            "fdf_pass_info": (C.c_int, [_V, C.POINTER(C.c_int32)]),
             "fdf_timing": (C.c_int, [_V, C.c_int32]),
             "fdf_kernel_time": (C.c_int, [_V, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
             "fdf_launch_count": (C.c_int64, [_V]),
@@ -339,6 +340,13 @@ def fdf_supersteps(ctx, n_steps):
     _check(lib().fdf_supersteps(ctx, out.ctypes.data_as(C.POINTER(C.c_int32)), len(out), C.byref(cnt)),
            "fdf_supersteps")
     return out, cnt.value
+
+
+def fdf_pass_info(ctx):
+    """dict(form, series, passes, steps_per_pass) of the last fdf_step or fdf_run_graph run."""
+    info = np.zeros(4, np.int32)
+    _check(lib().fdf_pass_info(ctx, info.ctypes.data_as(C.POINTER(C.c_int32))), "fdf_pass_info")
+    return dict(form=int(info[0]), series=int(info[1]), passes=int(info[2]), steps_per_pass=int(info[3]))
 
 
 def fdf_state(ctx):

@@ -72,14 +72,19 @@ def test_sampler_bit_exact(F, inputs, c1_tables, prec):
         assert np.array_equal(got[s][2].view(np.uint64), pm.view(np.uint64))
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 3e-6), (2, 1e-2)])
-def test_fields_match_oracle(F, inputs, c1_tables, prec, tol):
-    """Each slot against the oracle.  Slots are transformed in packed pairs
-    (d_x psi + i d_y psi, d_z psi + i d_x phi, d_y phi + i d_z phi, phi_dot + i psi);
-    an FFT's rounding is relative to the magnitude of the complex signal it
-    transforms, so each slot's error is measured against the larger maximum of
-    its pair.  (phi_dot, near zero in the radiation and matter eras, shares its
-    transform with psi.)"""
+# The grid bars, each slot's error relative to that slot's own largest value: FP32 and
+# FP64 from the method's contract (1e-6 and 1e-12); BF16 from its storage rounding (2^-9).
+FIELD_TOL = {0: 1e-12, 1: 1e-6, 2: 4e-3}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_fields_match_oracle(F, inputs, c1_tables, prec):
+    """Each slot against the oracle, on its own scale, at four scale factors from z = 1e9
+    to the end.  Slots are transformed in packed pairs (d_x psi + i d_y psi,
+    d_z psi + i d_x phi, d_y phi + i d_z phi, phi_dot + i slot 7) and an FFT's rounding is
+    relative to the complex signal it transforms: the steps' grids carry zero in slot 7,
+    so phi_dot, about 1e4 times smaller than psi late in the run, is transformed alone."""
+    tol = FIELD_TOL[prec]
     p = inputs.config("c1_32", n_grid=32, precision=prec, seed=31)
     o = O.Oracle(p, c1_tables)
     R = o.noise()
@@ -90,20 +95,19 @@ def test_fields_match_oracle(F, inputs, c1_tables, prec, tol):
             g = r.build_fields(lna)
             ref, _ = o.fields(lna, 0xFF, R)
             for s in range(8):
-                pair = s & ~1
-                scale = max(np.max(np.abs(ref[pair])), np.max(np.abs(ref[pair + 1])))
-                errs.append((k, s, np.max(np.abs(ref[s])), np.max(np.abs(g[s] - ref[s])) / scale))
+                scale = np.max(np.abs(ref[s]))
+                errs.append((k, s, scale, np.max(np.abs(g[s] - ref[s])) / scale))
     for e in errs:
-        print("k %3d slot %d  max|ref| %.3e  err / pair scale %.3e" % e)
+        print("k %3d slot %d  max|ref| %.3e  err / own scale %.3e" % e)
     assert all(e[2] > 0 and e[3] < tol for e in errs)
 
 
-@pytest.mark.parametrize("prec,N,tol", [(1, 8, 3e-6), (1, 16, 3e-6), (1, 64, 3e-6), (1, 128, 3e-6), (1, 256, 3e-6),
-                                        (0, 8, 1e-12), (0, 64, 1e-12), (0, 128, 1e-12), (2, 128, 1e-2)])
-def test_fields_match_oracle_at_every_grid_size(F, inputs, c1_tables, prec, N, tol):
+@pytest.mark.parametrize("prec,N", [(1, 8), (1, 16), (1, 64), (1, 128), (1, 256), (0, 8), (0, 64), (0, 128),
+                                    (2, 128)])
+def test_fields_match_oracle_at_every_grid_size(F, inputs, c1_tables, prec, N):
     """The FFT passes are compiled per grid size (each N = N1 N2 has its own register
     split and shared-memory shape), so every size the workloads use is checked against
-    the oracle, slot by slot, at one scale factor in the matter era."""
+    the oracle, slot by slot on its own scale, at one scale factor in the matter era."""
     p = inputs.config("c1_32", n_grid=N, box=1000.0 * N / 32, precision=prec, seed=33)
     o = O.Oracle(p, c1_tables)
     lna = o.lna(80)
@@ -112,11 +116,9 @@ def test_fields_match_oracle_at_every_grid_size(F, inputs, c1_tables, prec, N, t
     ref, _ = o.fields(lna, 0xFF, o.noise())
     worst = 0.0
     for s in range(8):
-        pair = s & ~1
-        scale = max(np.max(np.abs(ref[pair])), np.max(np.abs(ref[pair + 1])))
-        worst = max(worst, np.max(np.abs(g[s] - ref[s])) / scale)
-    print("N %d prec %d: largest slot error / pair scale %.3e" % (N, prec, worst))
-    assert worst < tol
+        worst = max(worst, np.max(np.abs(g[s] - ref[s])) / np.max(np.abs(ref[s])))
+    print("N %d prec %d: largest slot error / own scale %.3e" % (N, prec, worst))
+    assert worst < FIELD_TOL[prec]
 
 
 def test_run_c1_plain_fp64(F, inputs, c1_tables):

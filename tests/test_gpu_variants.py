@@ -215,14 +215,14 @@ def test_exact_equations_of_motion_match_the_oracle(F, inputs, c1_tables, spp, o
 def test_accel_terms_match_the_oracle(F, inputs, c1_tables, prec, order):
     """fdf_accel_terms against the oracle's on the oracle's own particles, per species and
     for all, at an early step (relativistic: the first two terms alike) and a late one.
-    The q phi_dot term has its own bound in the split forms: phi_dot shares its packed
-    transform with psi, about 1e4 times larger late in the run, and the FP32 (BF16)
-    rounding of that pair sets phi_dot's error."""
+    Every term, the q phi_dot term included, is held to one bar per precision: the steps'
+    grids transform phi_dot alone (its packed partner, slot 7, is zero there), so its FP32
+    rounding is relative to phi_dot itself."""
     p = inputs.config("c1_32", n_part=3001, n_species=2, m_ev=[0.05, 0.2], n_grid=16, n_steps=60, precision=prec,
                       seed=181, interp_order=order)
     o = O.Oracle(p, c1_tables)
-    tol = {0: 1e-9, 1: 1e-5, 2: 3e-3, 3: 1e-5}[prec]
-    tol_dot = {0: 1e-9, 1: 1e-3, 2: 1.0, 3: 1e-3}[prec]
+    tol = {0: 1e-9, 1: 1e-6, 2: 3e-3, 3: 1e-6}[prec]
+    tol_dot = tol
     with F.Run(p, c1_tables) as r:
         r.sample()
         done = 0

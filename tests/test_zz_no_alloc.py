@@ -19,9 +19,9 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 
-# the parity tests' field tolerances, relative to the larger maximum of a slot's
-# packed pair: FP32 grids and the FP64 form
-TOL = {1: 3e-6, 0: 1e-12}
+# the parity tests' field tolerances, relative to each slot's own largest value: FP32
+# grids and the FP64 form
+TOL = {1: 1e-6, 0: 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -35,12 +35,7 @@ def F():
 
 
 def _err(got, ref):
-    worst = 0.0
-    for s in range(8):
-        pair = s & ~1   # slots are transformed in packed pairs (see the parity tests)
-        scale = max(np.max(np.abs(ref[pair])), np.max(np.abs(ref[pair + 1])))
-        worst = max(worst, np.max(np.abs(got[s] - ref[s])) / scale)
-    return worst
+    return max(np.max(np.abs(got[s] - ref[s])) / np.max(np.abs(ref[s])) for s in range(8))
 
 
 @pytest.mark.parametrize("prec", [1, 0])
@@ -58,7 +53,11 @@ def test_noalloc_fields_match_the_oracle_and_the_context_path_on_two_calls(F, in
     T, keep = F.make_tables(c1_tables)
     N = p["n_grid"]
     out = torch.empty((8, N, N, N), dtype=torch.float64, device="cuda")
-    F.fdf_build_fields_noalloc(P, T, o.lna(5), out)       # warm-up: the first call looks up the array
+    # warm-up: the first call looks up the array; torch's fill and copy kernels load their
+    # modules on first use, which takes device memory, so they run once here too
+    out.fill_(float("nan"))
+    F.fdf_build_fields_noalloc(P, T, o.lna(5), out)
+    out.cpu()
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     for lna, ref_o, ref_c in zip(lnas, oracle, context):
