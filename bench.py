@@ -44,11 +44,11 @@ FORM_NAMES = {0: "FP64 grids and state", 1: "FP32 grids, FP64 state", 2: "BF16 g
               4: "BF16 grids, split state (fixed-point x, FP32 q0 + dq)"}
 # FP64-pipe instructions of the FP64-state pass (k_push_wide), counted in its source: a drift
 # takes 19 (|q|^2 3, the centre's argument 1, the inverse square root 4, t 2, five FP64 terms
-# of the polynomial 5, D 1, x += q D 3) and a kick 17 (argument 1, inverse square root 4, t 2,
-# two FP64 terms of each of two polynomials 4, K_phi 1, K_psi 2, q += dq 3); |q0|^2 takes 3
-# per particle and pass.  Conversions run on the integer pipe.  ncu's count of FP64-pipe
-# instructions (profiles/) checks these figures.
-WIDE_FP64_PER_STEP = 36
+# of the polynomial 5, D 1, x += q D 3) and a kick 14 (argument 1, first-order inverse square
+# root 3, two FP64 terms of each of two polynomials 4, K_phi 1, K_psi 2, q += dq 3); |q0|^2
+# takes 3 per particle and pass.  Conversions run on the integer pipe.  ncu's count of
+# FP64-pipe instructions (profiles/) checks these figures.
+WIDE_FP64_PER_STEP = 33
 WIDE_FP64_PER_PASS = 3
 
 # DRAM bytes per particle pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean
@@ -134,12 +134,14 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------------------------
-def rank_params(workload, rank, n_species=0):
+def rank_params(workload, rank, n_species=0, precision=-1):
     """The workload of one replica: every rank runs the same shapes with its own seed."""
     p = I.config(workload, seed=I.config(workload)["seed"] + 1000 * rank)
     if n_species:
         p["n_species"] = n_species
         p["m_ev"] = (p["m_ev"] * 4)[:n_species]
+    if precision >= 0:
+        p["precision"] = precision
     return p
 
 
@@ -248,7 +250,7 @@ def bench_ours(args, rank, world, dist):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    p = rank_params(args.workload, rank, args.n_species)
+    p = rank_params(args.workload, rank, args.n_species, args.precision)
     tables = I.transfer_tables(p)
     stream = torch.cuda.Stream(device=dev)
     P = fdf.make_params(p)
@@ -573,6 +575,9 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the reduced-precision workload")
     ap.add_argument("--schedule", default="", help='schedule knobs as JSON, e.g. {"sort_tile": 1} (no tuning)')
     ap.add_argument("--served-requests", type=int, default=64)
+    ap.add_argument("--precision", type=int, default=-1,
+                    help="override the workload's precision setting (FDF_PREC_*: 0 FP64, 1/2 FP32/BF16 grids with "
+                         "the FP64 state, 3/4 the split state)")
     ap.add_argument("--n-species", type=int, default=0,
                     help="override the species count (smaller device footprint for profiler captures)")
     args = ap.parse_args()
@@ -623,12 +628,16 @@ def main():
 
     pk = peaks()
     hbm = pk.get("hbm_gbs")
-    roof = fp64_roofline(r["p"], r["ktimes"], r["pipes"]["dfma_per_s"])
-    roof["kernel"] = "k_push_wide (fused drift + wrap + gather + kick over a pass of leapfrog steps, FP64 state)"
-    roof["launch_timing"] = ("CUDA events around every launch of one run on the context's stream, right after the "
-                             "timed region")
-    roof_hbm = hbm_roofline(r["p"], r["ktimes"], hbm)
-    roof_hbm["kernel"] = roof["kernel"]
+    prec = r["p"]["precision"]
+    kname = {0: "k_push_f64", 1: "k_push_wide", 2: "k_push_wide", 3: "k_push_split", 4: "k_push_split"}[prec]
+    kname += " (fused drift + wrap + gather + kick over a pass of leapfrog steps)"
+    timing = "CUDA events around every launch of one run on the context's stream, right after the timed region"
+    roof_hbm = dict(hbm_roofline(r["p"], r["ktimes"], hbm), kernel=kname, launch_timing=timing)
+    if prec in (1, 2):
+        # the FP64-state pass is bound by the FP64 pipe: that is its roofline
+        roof = dict(fp64_roofline(r["p"], r["ktimes"], r["pipes"]["dfma_per_s"]), kernel=kname, launch_timing=timing)
+    else:
+        roof = roof_hbm
     n_total = r["p"]["n_species"] * r["p"]["n_part"]
     per_run = {k: {"ms_per_step": v[0], "launches_per_step": v[1]} for k, v in r["ktimes"].items()}
     per_run["note"] = ("one instrumented run after the timed region (sequential calls, an event pair per launch: "

@@ -122,6 +122,16 @@ __device__ __forceinline__ double rsqrt_fp64(double u)
     return fma(y, s, y);
 }
 
+// The same to first order, r = y (1 + e/2), three FP64 instructions, relative error
+// 3 e^2 / 8 (below 2^-40): for the kick integrals, which scale a kick of at most ~1e-3
+// of |q| and are needed to ~1e-9.
+__device__ __forceinline__ double rsqrt_fp64_1(double u)
+{
+    const float yf = rsqrtf(d2f_bits(u));
+    const double y = f2d_bits(yf), yh = f2d_bits(0.5f * yf);
+    return fma(y, fma(-(u * y), yh, 0.5), y);
+}
+
 // ---- complex ----
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {

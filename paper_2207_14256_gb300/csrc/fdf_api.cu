@@ -561,11 +561,11 @@ void fill_wide(fdf_ctx* c, bool drift, double d1, double d2, const double* Wd, c
         if (!it->second.first) u.wide_ok = 0;
     };
     if (drift) {
-        w.a2c = std::exp(d1 + d2);
+        for (int s = 0; s < c->p.n_species; ++s) w.muc[s] = c->p.m_ev[s] * c->p.m_ev[s] * std::exp(d1 + d2);
         fit(d1, d2, 0, Wd, ad, c->ngl, w.drift);
     }
     if (kick) {
-        w.a2k = std::exp(k1 + k2);
+        for (int s = 0; s < c->p.n_species; ++s) w.muk[s] = c->p.m_ev[s] * c->p.m_ev[s] * std::exp(k1 + k2);
         fit(k1, k2, 1, Wk, ak, c->nkick, w.kphi);
         fit(k1, k2, 2, Wk, ak, c->nkick, w.kpsi);
         double dt = 0;

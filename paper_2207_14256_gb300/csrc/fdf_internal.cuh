@@ -78,8 +78,8 @@ struct WidePoly {
 };
 
 struct WideCoef {
-    double a2c;                 // a_c^2 of the drift interval (m^2 a_c^2 = m^2 a2c)
-    double a2k;                 // a_c^2 of the kick interval
+    double muc[kMaxSpecies];    // m^2 a_c^2 of the drift interval, per species
+    double muk[kMaxSpecies];    // m^2 a_c^2 of the kick interval, per species
     WidePoly drift;             // gm of the drift interval
     WidePoly kphi;              // gm of the kick interval: K_phi = r gm(t)
     WidePoly kpsi;              // gp of the kick interval: K_psi = u r gp(t)

@@ -552,12 +552,11 @@ void push_split(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleSta
 // and FP64 <-> FP32 conversions at 1/64 of its FP32 rate, so every conversion goes
 // through the integer pipe (d2f_bits, f2d_bits).
 
-// p(t) = sum_k c_k t^k: the terms from k = NF64 up in FP32 (Horner), then the terms
-// below NF64 in FP64
+// p(t) = sum_k c_k t^k: the terms from k = NF64 up in FP32 (Horner, from tf, t in FP32),
+// then the terms below NF64 in FP64
 template <int NF64>
-__device__ __forceinline__ double wide_poly(const WidePoly& P, double t)
+__device__ __forceinline__ double wide_poly(const WidePoly& P, double t, float tf)
 {
-    const float tf = d2f_bits(t);
     float tail = P.c32[kWideDeg - NF64];
 #pragma unroll
     for (int k = kWideDeg - NF64 - 1; k >= 0; --k) tail = fmaf(tail, tf, P.c32[k]);
@@ -592,7 +591,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_push_wide(const __grid_constant
         const int64_t i = i0 + threadIdx.x;
         if (i >= n) continue;
         const int s = UNI ? 0 : species_of(a, i);
-        const double m2 = a.m2[s];
         double x[3] = {__ldcs(xd + i), __ldcs(xd + n + i), __ldcs(xd + 2 * n + i)};
         double q[3] = {__ldcs(qd + i), __ldcs(qd + n + i), __ldcs(qd + 2 * n + i)};
         const float qa = __ldcs(q0f + i), qb = __ldcs(q0f + n + i), qc = __ldcs(q0f + 2 * n + i);
@@ -608,11 +606,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_push_wide(const __grid_constant
                 const double qq = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
                 double D;
                 if constexpr (SERIES) {
-                    const double muc = m2 * c.a2c;
+                    const double muc = c.muc[s];
                     const double uc = qq + muc;
                     const double r = rsqrt_fp64(uc);
                     const double t = (muc * r) * r;
-                    D = r * wide_poly<kWideD64>(c.drift, t);
+                    D = r * wide_poly<kWideD64>(c.drift, t, d2f_bits(t));
                 } else {
                     const SpeciesCoef& sc = st.sp[s];
                     D = 0.0;
@@ -627,12 +625,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_push_wide(const __grid_constant
                 gather_wide<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, invh, x, g);
                 double Kpsi, Kphi;
                 if constexpr (SERIES) {
-                    const double muk = m2 * c.a2k;
+                    // the kick integrals are needed to ~1e-9 (they scale a kick of at most
+                    // ~1e-3 of |q|): r0 to first order, t0 from FP32 (its error enters
+                    // times the first coefficient, ~1e-3 of the integral)
+                    const double muk = c.muk[s];
                     const double u0 = s0 + muk;
-                    const double r0 = rsqrt_fp64(u0);
-                    const double t0 = (muk * r0) * r0;
-                    Kphi = r0 * wide_poly<kWideK64>(c.kphi, t0);
-                    Kpsi = (u0 * r0) * wide_poly<kWideK64>(c.kpsi, t0);
+                    const double r0 = rsqrt_fp64_1(u0);
+                    const float r0f = d2f_bits(r0);
+                    const float t0f = d2f_bits(muk) * r0f * r0f;
+                    const double t0 = f2d_bits(t0f);
+                    Kphi = r0 * wide_poly<kWideK64>(c.kphi, t0, t0f);
+                    Kpsi = (u0 * r0) * wide_poly<kWideK64>(c.kpsi, t0, t0f);
                 } else {
                     const SpeciesCoef& sc = st.sp[s];
                     Kpsi = 0.0;
