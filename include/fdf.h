@@ -163,6 +163,11 @@ typedef struct fdf_params {
                                   (eq:p_eq), FDF_EOM_Q_SIMPLE (eq:q_eq), FDF_EOM_NEWTONIAN, and
                                   FDF_EOM_EXACT (eq:releq and eq:geodesic themselves, not
                                   symplectic; steps_per_pass 0, 1 or 2) */
+    int32_t  pass_blocks;      /* the FP32/BF16-grid forms with the FP64 state: resident blocks
+                                  of 256 threads per SM of the particle pass, whose grid is
+                                  that many per SM (persistent), 0 = automatic (3) or 1..3;
+                                  fewer leave room on each SM for the field builds of the
+                                  next pass.  Ignored by the other forms. */
 } fdf_params;
 
 /* ---- equations of motion (fdf_params.eom) -------------------------------- */
@@ -364,12 +369,12 @@ FDF_API const char* fdf_last_error(void);
 FDF_API void fdf_destroy(fdf_ctx* c);
 
 /* Autotuner of the schedule knobs that change speed only (no result beyond the
- * stated tolerances): sort_cells, sort_tile and steps_per_pass.  It times whole
- * runs (fdf_sample + fdf_step(n_steps)) of p on the device, one knob at a time
- * (coordinate descent over sort_cells in {2, 4, 8}, sort_tile in {0, 1, 2},
- * steps_per_pass in {2, 3, 4}, then sort_cells again in {3, 5, 6}), starting from
- * the automatic choices, and writes
- * the fastest parameter set to *out (p with the three knobs set).  The paper
+ * stated tolerances): sort_cells, sort_tile, steps_per_pass and (FP64-state forms)
+ * pass_blocks.  It times whole runs (fdf_sample + fdf_step(n_steps)) of p on the
+ * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8},
+ * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4}, pass_blocks in {2, 3}, then
+ * sort_cells again in {3, 5, 6}), starting from the automatic choices, and writes
+ * the fastest parameter set to *out (p with the knobs set).  The paper
  * has no counterpart.  stream: a cudaStream_t or NULL; every trial allocates
  * and frees its own context.  ms (may be NULL) receives the best run time;
  * trials (may be NULL) the number of timed runs.  Only the FP32/BF16-grid forms are tuned;

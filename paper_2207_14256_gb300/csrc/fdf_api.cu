@@ -311,6 +311,7 @@ int fdf::validate_params(const fdf_params* p)
         return fail(FDF_EINVAL, "sort_tile must be 0..3 and at most log2(n_grid)");
     if (p->sort_cells < 0) return fail(FDF_EINVAL, "sort_cells must be >= 0");
     if (p->interp_order < 0 || p->interp_order > 2) return fail(FDF_EINVAL, "interp_order must be 0, 1 or 2");
+    if (p->pass_blocks < 0 || p->pass_blocks > 3) return fail(FDF_EINVAL, "pass_blocks must be 0 (automatic) or 1..3");
     if (!(p->superstep_tol >= 0.0) || !std::isfinite(p->superstep_tol))
         return fail(FDF_EINVAL, "superstep_tol must be finite and >= 0");
     if (p->eom < FDF_EOM_GEODESIC || p->eom > FDF_EOM_EXACT) return fail(FDF_EINVAL, "unknown eom");
@@ -352,6 +353,7 @@ struct fdf_ctx {
     cudaStream_t stream = nullptr;
     int64_t n = 0;
     int ngl = 4, nkick = 4;
+    int sm_count = 152;                     // SMs of the context's device
     double glx[kMaxGL]{}, glw[kMaxGL]{};    // drift rule
     double glxk[kMaxGL]{}, glwk[kMaxGL]{};  // kick rule
     int uniform = 0;                        // all species share one mass
@@ -529,6 +531,7 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.eom = c->p.eom;
     a.wide_series = 1;
     for (int s = 0; s < kMaxSpecies; ++s) a.m2[s] = c->p.m_ev[s] * c->p.m_ev[s];
+    a.grid_blocks = c->sm_count * (c->p.pass_blocks > 0 ? c->p.pass_blocks : 3);
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
     a.invL = 1.0 / c->p.box_mpc;
@@ -977,6 +980,12 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     if (!c) return fail(FDF_ENOMEM, "host allocation failed");
     c->p = *p;
     c->stream = (cudaStream_t)stream;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            c->sm_count = sms;
+    }
     c->n = p->n_part * p->n_species;
     c->H0 = p->h / kC_over_H100;
     c->ol = 1.0 - p->omega_m - p->omega_r;

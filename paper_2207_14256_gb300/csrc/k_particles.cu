@@ -577,8 +577,62 @@ __device__ __forceinline__ double wrap_rare(double x, double L, double invL, lon
     return x;
 }
 
+// The step integrals of one sub-step.  The drift's D depends on |q|^2, the kick's K_phi
+// and K_psi on |q0|^2 only: the two chains are independent of each other and of the
+// gather, so the pass issues them back to back and the FP64 pipe overlaps their
+// latencies and the gather's.
+template <bool SERIES>
+__device__ __forceinline__ double drift_integral(const SubStep& st, int s, int n_gl, double qq)
+{
+    if constexpr (SERIES) {
+        const double muc = st.wide.muc[s];
+        const double uc = qq + muc;
+        const double r = rsqrt_fp64(uc);
+        const double t = (muc * r) * r;
+        return r * wide_poly<kWideD64>(st.wide.drift, t, d2f_bits(t));
+    } else {
+        const SpeciesCoef& sc = st.sp[s];
+        double D = 0.0;
+        for (int j = 0; j < n_gl; ++j) D = fma(sc.Wd[j], rsqrt_fp64(qq + sc.mud[j]), D);
+        return D;
+    }
+}
+
+template <bool SERIES>
+__device__ __forceinline__ void kick_integrals(const SubStep& st, int s, int n_kick, double s0, float& Kpsif,
+                                               float& Kphif)
+{
+    double Kpsi, Kphi;
+    if constexpr (SERIES) {
+        // needed to ~1e-9 (they scale a kick of at most ~1e-3 of |q|): r0 to first order,
+        // t0 from FP32 (its error enters times the first coefficient, ~1e-3 of the integral)
+        const double muk = st.wide.muk[s];
+        const double u0 = s0 + muk;
+        const double r0 = rsqrt_fp64_1(u0);
+        const float r0f = d2f_bits(r0);
+        const float t0f = d2f_bits(muk) * r0f * r0f;
+        const double t0 = f2d_bits(t0f);
+        Kphi = r0 * wide_poly<kWideK64>(st.wide.kphi, t0, t0f);
+        Kpsi = (u0 * r0) * wide_poly<kWideK64>(st.wide.kpsi, t0, t0f);
+    } else {
+        const SpeciesCoef& sc = st.sp[s];
+        Kpsi = 0.0;
+        Kphi = 0.0;
+        for (int j = 0; j < n_kick; ++j) {
+            const double e2 = s0 + sc.muk[j];
+            const double ie = rsqrt_fp64(e2);
+            Kpsi = fma(sc.Wk[j], e2 * ie, Kpsi);
+            Kphi = fma(sc.Wk[j], ie, Kphi);
+        }
+    }
+    Kpsif = d2f_bits(Kpsi);
+    Kphif = d2f_bits(Kphi);
+}
+
+// Three resident blocks per SM (80 registers, no spills): 24 warps keep the FP64 pipe
+// busy through the latency of its results and of the gather.
 template <typename Gt, bool SERIES, bool UNI>
-__global__ void __launch_bounds__(kThreads, 2) k_push_wide(const __grid_constant__ PushArgs a,
+__global__ void __launch_bounds__(kThreads, 3) k_push_wide(const __grid_constant__ PushArgs a,
                                                            double* __restrict__ xd, double* __restrict__ qd,
                                                            const float* __restrict__ q0f)
 {
@@ -601,21 +655,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_push_wide(const __grid_constant
         bool moved = false, kicked = false;
         for (int u = 0; u < a.nsub; ++u) {
             const SubStep& st = a.sub[u];
-            const WideCoef& c = st.wide;
+            float Kpsif = 0.f, Kphif = 0.f;
+            if (st.do_kick) kick_integrals<SERIES>(st, s, a.n_kick, s0, Kpsif, Kphif);
             if (st.do_drift) {
-                const double qq = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
-                double D;
-                if constexpr (SERIES) {
-                    const double muc = c.muc[s];
-                    const double uc = qq + muc;
-                    const double r = rsqrt_fp64(uc);
-                    const double t = (muc * r) * r;
-                    D = r * wide_poly<kWideD64>(c.drift, t, d2f_bits(t));
-                } else {
-                    const SpeciesCoef& sc = st.sp[s];
-                    D = 0.0;
-                    for (int j = 0; j < a.n_gl; ++j) D = fma(sc.Wd[j], rsqrt_fp64(qq + sc.mud[j]), D);
-                }
+                const double D =
+                    drift_integral<SERIES>(st, s, a.n_gl, fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2])));
 #pragma unroll
                 for (int d = 0; d < 3; ++d) x[d] = wrap_rare(fma(q[d], D, x[d]), a.L, a.invL, Lbits);
                 moved = true;
@@ -623,33 +667,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_push_wide(const __grid_constant
             if (st.do_kick) {
                 float g[8];
                 gather_wide<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, invh, x, g);
-                double Kpsi, Kphi;
-                if constexpr (SERIES) {
-                    // the kick integrals are needed to ~1e-9 (they scale a kick of at most
-                    // ~1e-3 of |q|): r0 to first order, t0 from FP32 (its error enters
-                    // times the first coefficient, ~1e-3 of the integral)
-                    const double muk = c.muk[s];
-                    const double u0 = s0 + muk;
-                    const double r0 = rsqrt_fp64_1(u0);
-                    const float r0f = d2f_bits(r0);
-                    const float t0f = d2f_bits(muk) * r0f * r0f;
-                    const double t0 = f2d_bits(t0f);
-                    Kphi = r0 * wide_poly<kWideK64>(c.kphi, t0, t0f);
-                    Kpsi = (u0 * r0) * wide_poly<kWideK64>(c.kpsi, t0, t0f);
-                } else {
-                    const SpeciesCoef& sc = st.sp[s];
-                    Kpsi = 0.0;
-                    Kphi = 0.0;
-                    for (int j = 0; j < a.n_kick; ++j) {
-                        const double e2 = s0 + sc.muk[j];
-                        const double ie = rsqrt_fp64(e2);
-                        Kpsi = fma(sc.Wk[j], e2 * ie, Kpsi);
-                        Kphi = fma(sc.Wk[j], ie, Kphi);
-                    }
-                }
-                const float Kpsif = d2f_bits(Kpsi), Kphif = d2f_bits(Kphi);
                 const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
-                const float b = qdphi * Kphif + g[6] * c.dtau_k;
+                const float b = qdphi * Kphif + g[6] * st.wide.dtau_k;
                 const float a2 = q02 * Kphif;
                 q[0] += f2d_bits(-g[0] * Kpsif - g[3] * a2 + qa * b);
                 q[1] += f2d_bits(-g[1] * Kpsif - g[4] * a2 + qb * b);
@@ -999,8 +1018,11 @@ cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, 
     if (f == kPlain) {
         k_push_f64<<<grid_for(a.n), kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d, st.sd);
     } else if (f == kWide) {
-        // two resident blocks per SM (the FP64 pipe, not occupancy, bounds the pass)
-        const unsigned b = grid_for(a.n);
+        // a persistent grid of pass_blocks (<= 3 resident) blocks per SM, each walking the
+        // particles with a grid stride
+        int64_t nb = (a.n + kThreads - 1) / kThreads;
+        if (nb > a.grid_blocks) nb = a.grid_blocks;
+        const unsigned b = (unsigned)(nb < 1 ? 1 : nb);
         if (gp == FDF_PREC_F32) push_wide<float>(s, b, a, st);
         else push_wide<__nv_bfloat16>(s, b, a, st);
     } else {

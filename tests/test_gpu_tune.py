@@ -1,5 +1,5 @@
 """fdf_tune: the autotuner of the schedule knobs (sort_cells, sort_tile,
-steps_per_pass).
+steps_per_pass and, for the FP64-state forms, pass_blocks).
 
 The knobs change how the work is scheduled, not what is computed, so a run
 with the tuned parameters must give the same particles as a run with the
@@ -49,9 +49,10 @@ def test_tuned_knobs_are_valid_and_change_no_result(F, inputs):
     print("tuned knobs", k, "best run %.2f ms over %d timed runs" % (ms, trials))
     assert trials >= 6 and ms > 0
     assert k["sort_cells"] in (2, 3, 4, 5, 6, 8) and k["sort_tile"] in (0, 1, 2) and k["steps_per_pass"] in (2, 3, 4)
+    assert k["pass_blocks"] in (2, 3)
     # every other field is the caller's
     for f, _ in F.fdf_params._fields_:
-        if f not in ("sort_every", "sort_cells", "sort_tile", "steps_per_pass"):
+        if f not in ("sort_every", "sort_cells", "sort_tile", "steps_per_pass", "pass_blocks"):
             a, b = getattr(P, f), getattr(tuned, f)
             assert (list(a) == list(b)) if f == "m_ev" else a == b, f
     ref = _run(F, P, T, p["n_part"], 2)
