@@ -43,13 +43,19 @@ FORM_NAMES = {0: "FP64 grids and state", 1: "FP32 grids, FP64 state", 2: "BF16 g
               3: "FP32 grids, split state (fixed-point x, FP32 q0 + dq)",
               4: "BF16 grids, split state (fixed-point x, FP32 q0 + dq)"}
 # FP64-pipe instructions of the FP64-state pass (k_push_wide), counted in its source: a drift
-# takes 19 (|q|^2 3, the centre's argument 1, the inverse square root 4, t 2, five FP64 terms
-# of the polynomial 5, D 1, x += q D 3) and a kick 14 (argument 1, first-order inverse square
-# root 3, two FP64 terms of each of two polynomials 4, K_phi 1, K_psi 2, q += dq 3); |q0|^2
-# takes 3 per particle and pass.  Conversions run on the integer pipe.  ncu's count of
+# takes 18 (|q|^2 3, v = 1 + |q|^2 / (m a_c)^2 1, the inverse square root 4, t 1, five FP64
+# terms of the polynomial 5, D 1, x += q D 3) and a kick 14 (argument 1, first-order inverse
+# square root 3, two FP64 terms of each of two polynomials 4, K_phi 1, K_psi 2, q += dq 3);
+# |q0|^2 takes 3 per particle and pass.  Conversions run on the integer pipe.  ncu's count of
 # FP64-pipe instructions (profiles/) checks these figures.
-WIDE_FP64_PER_STEP = 33
+WIDE_FP64_PER_STEP = 32
 WIDE_FP64_PER_PASS = 3
+
+# FP64-pipe instructions per particle-step of the plain FP64 pass (k_push_f64), from ncu
+# (sm__inst_executed_pipe_fp64.sum x 32 / particle-steps of the launch, 128^3 particles, one step
+# per pass; profiles/), for its FP64-pipe roofline.  Dropped if the sources changed.
+PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3,
+              "sources_sha256": "PLACEHOLDER"}
 
 # DRAM bytes per particle pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # over the passes of a run; profiles/), per particle of the launch, by precision setting.  Valid
@@ -377,6 +383,14 @@ def bench_ours(args, rank, world, dist):
             fdf.fdf_destroy(c3)
         plain = {"value": units / (pms / 1e3), "ms_per_step": pms, "push_ms_per_launch": push64[0] / push64[1],
                  "push_launches": push64[1]}
+        if push_sources_hash() == PLAIN_FP64["sources_sha256"]:
+            # the plain pass against the FP64 pipe: ncu's FP64 instructions per particle-step
+            ops = PLAIN_FP64["per_particle_step"] * p["n_species"] * p["n_part"] * p["n_steps"] / push64[1]
+            ach = ops / (push64[0] / push64[1] / 1e3) / 1e9
+            plain["roofline_fp64"] = {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": d_rate / 1e9,
+                                      "unit": "G FP64-pipe instructions/s", "frac": ach / (d_rate / 1e9),
+                                      "per_unit": "%.0f FP64-pipe instructions per particle-step (ncu)"
+                                                  % PLAIN_FP64["per_particle_step"]}
 
     # the paper's super-steps (Sec. 2.1: fields built only where the transfer functions
     # changed by more than 1%, interpolated in between), same workload and schedule

@@ -564,8 +564,19 @@ void fill_wide(fdf_ctx* c, bool drift, double d1, double d2, const double* Wd, c
         if (!it->second.first) u.wide_ok = 0;
     };
     if (drift) {
-        for (int s = 0; s < c->p.n_species; ++s) w.muc[s] = c->p.m_ev[s] * c->p.m_ev[s] * std::exp(d1 + d2);
-        fit(d1, d2, 0, Wd, ad, c->ngl, w.drift);
+        WidePoly P;
+        fit(d1, d2, 0, Wd, ad, c->ngl, P);
+        double sum = 0;
+        for (int j = 0; j < c->ngl; ++j) sum += Wd[j];
+        for (int s = 0; s < c->p.n_species; ++s) {
+            const double mac = c->p.m_ev[s] * std::exp(0.5 * (d1 + d2));      // m a_c
+            w.wsum[s] = sum;
+            w.inv_muc[s] = mac > 0 ? 1.0 / (mac * mac) : 0.0;
+            // the species' copy of the polynomial carries the factor 1/(m a_c)
+            const double f = mac > 0 ? 1.0 / mac : 0.0;
+            for (int k = 0; k < kWideD64; ++k) w.drift[s].c64[k] = P.c64[k] * f;
+            for (int k = 0; k <= kWideDeg; ++k) w.drift[s].c32[k] = (float)((double)P.c32[k] * f);
+        }
     }
     if (kick) {
         for (int s = 0; s < c->p.n_species; ++s) w.muk[s] = c->p.m_ev[s] * c->p.m_ev[s] * std::exp(k1 + k2);

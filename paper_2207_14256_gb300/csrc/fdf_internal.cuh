@@ -78,9 +78,14 @@ struct WidePoly {
 };
 
 struct WideCoef {
-    double muc[kMaxSpecies];    // m^2 a_c^2 of the drift interval, per species
+    // The drift in the variable v = 1 + |q|^2 / (m^2 a_c^2) (per species, m > 0): then
+    // t = 1/v = r_v^2 with r_v = v^(-1/2), and D = r gm(t) = r_v gm(t) / (m a_c), the
+    // factor 1/(m a_c) folded into the species' copy of the polynomial.  A massless
+    // species (inv_muc = 0) takes D = |q|^-1 sum_j W_j.
+    double inv_muc[kMaxSpecies];    // 1 / (m^2 a_c^2) of the drift interval, or 0 for m = 0
+    double wsum[kMaxSpecies];       // sum_j W_j (the massless drift)
+    WidePoly drift[kMaxSpecies];    // gm of the drift interval / (m a_c), per species
     double muk[kMaxSpecies];    // m^2 a_c^2 of the kick interval, per species
-    WidePoly drift;             // gm of the drift interval
     WidePoly kphi;              // gm of the kick interval: K_phi = r gm(t)
     WidePoly kpsi;              // gp of the kick interval: K_psi = u r gp(t)
     float dtau_k;               // conformal time of the kick interval
@@ -94,7 +99,7 @@ struct SubStep {
     double emax;                // largest |e_j| of any species (the series converges for <= 1/4)
     int wide_ok;                // the FP64-state form's fits of this sub-step passed
     SpeciesCoef sp[kMaxSpecies];
-    WideCoef wide;              // the FP64-state form (species enter through m^2 only)
+    WideCoef wide;              // the FP64-state form
 };
 
 constexpr double kSeriesMaxE = 0.25;
@@ -122,6 +127,8 @@ struct PushArgs {
     SubStep sub[kMaxSub];
     const void* G[kMaxSub];     // the grid each sub-step's kick reads
 };
+// a kernel's parameters may take up to 32764 bytes
+static_assert(sizeof(PushArgs) <= 32000, "PushArgs must fit the kernel parameter space");
 
 // What slot 7 of a gather grid holds.  It shares its packed transform with phi_dot
 // (phi_dot + i slot 7), and an FFT's rounding is relative to the larger of the two, so

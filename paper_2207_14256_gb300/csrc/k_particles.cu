@@ -582,15 +582,20 @@ __device__ __forceinline__ double wrap_rare(double x, double L, double invL, lon
 // gather, so the pass issues them back to back and the FP64 pipe overlaps their
 // latencies and the gather's.
 template <bool SERIES>
-__device__ __forceinline__ double drift_integral(const SubStep& st, int s, int n_gl, double qq)
+__device__ __forceinline__ double drift_integral(const SubStep& st, int s, int n_gl, const double q[3])
 {
     if constexpr (SERIES) {
-        const double muc = st.wide.muc[s];
-        const double uc = qq + muc;
-        const double r = rsqrt_fp64(uc);
-        const double t = (muc * r) * r;
-        return r * wide_poly<kWideD64>(st.wide.drift, t, d2f_bits(t));
+        const double inv = st.wide.inv_muc[s];
+        if (inv > 0.0) {
+            // v = 1 + |q|^2 / (m^2 a_c^2), t = 1/v, D = v^(-1/2) gm(t) / (m a_c)
+            const double v = fma(fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2])), inv, 1.0);
+            const double rv = rsqrt_fp64(v);
+            const double t = rv * rv;
+            return rv * wide_poly<kWideD64>(st.wide.drift[s], t, d2f_bits(t));
+        }
+        return rsqrt_fp64(fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]))) * st.wide.wsum[s];
     } else {
+        const double qq = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
         const SpeciesCoef& sc = st.sp[s];
         double D = 0.0;
         for (int j = 0; j < n_gl; ++j) D = fma(sc.Wd[j], rsqrt_fp64(qq + sc.mud[j]), D);
@@ -658,8 +663,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_push_wide(const __grid_constant
             float Kpsif = 0.f, Kphif = 0.f;
             if (st.do_kick) kick_integrals<SERIES>(st, s, a.n_kick, s0, Kpsif, Kphif);
             if (st.do_drift) {
-                const double D =
-                    drift_integral<SERIES>(st, s, a.n_gl, fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2])));
+                const double D = drift_integral<SERIES>(st, s, a.n_gl, q);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) x[d] = wrap_rare(fma(q[d], D, x[d]), a.L, a.invL, Lbits);
                 moved = true;
