@@ -44,11 +44,11 @@ FORM_NAMES = {0: "FP64 grids and state", 1: "FP32 grids, FP64 state", 2: "BF16 g
               4: "BF16 grids, split state (fixed-point x, FP32 q0 + dq)"}
 # FP64-pipe instructions of the FP64-state pass (k_push_wide), counted in its source: a drift
 # takes 18 (|q|^2 3, v = 1 + |q|^2 / (m a_c)^2 1, the inverse square root 4, t 1, five FP64
-# terms of the polynomial 5, D 1, x += q D 3) and a kick 14 (argument 1, first-order inverse
-# square root 3, two FP64 terms of each of two polynomials 4, K_phi 1, K_psi 2, q += dq 3);
+# terms of the polynomial 5, D 1, x += q D 3) and a kick 12 (argument 1, first-order inverse
+# square root 3, one FP64 term of each of two polynomials 2, K_phi 1, K_psi 2, q += dq 3);
 # |q0|^2 takes 3 per particle and pass.  Conversions run on the integer pipe.  ncu's count of
 # FP64-pipe instructions (profiles/) checks these figures.
-WIDE_FP64_PER_STEP = 32
+WIDE_FP64_PER_STEP = 30
 WIDE_FP64_PER_PASS = 3
 
 # FP64-pipe instructions per particle-step of the plain FP64 pass (k_push_f64), from ncu
@@ -478,10 +478,10 @@ def served_requests(n_req):
     return reqs
 
 
-def serve(fdf, reqs, tables, arrivals, max_active, slice_steps):
+def serve(fdf, reqs, tables, arrivals, max_active, slice_steps, merge=False):
     """Submit request i at arrivals[i] seconds (server clock), release each as it
     finishes; returns per-request latencies and the span from first submit to last done."""
-    srv = fdf.Server(SERVED_BUDGET, max_active=max_active, slice_steps=slice_steps)
+    srv = fdf.Server(SERVED_BUDGET, max_active=max_active, slice_steps=slice_steps, merge=merge)
     try:
         t_start = srv.clock()
         ids, infos = [], {}
@@ -508,29 +508,33 @@ def serve(fdf, reqs, tables, arrivals, max_active, slice_steps):
     return lat, span, work
 
 
-def bench_served(n_req=64, load=0.8, max_active=8, slice_steps=8):
+def bench_served(n_req=64, load=0.8, max_active=8, slice_steps=8, merge=False):
     """The served stream: first all requests at once (the batched capacity), then
-    Poisson arrivals at `load` times that capacity; p50/p99 latency of the second."""
+    Poisson arrivals at `load` times that capacity; p50/p99 latency of the second.
+    merge: the server steps the requests' passes in merged launches."""
     from paper_2207_14256_gb300 import fdf
 
     reqs = served_requests(n_req)
     tables = I.transfer_tables(reqs[0])
-    lat0, span0, work = serve(fdf, reqs, tables, [0.0] * n_req, max_active, slice_steps)
+    lat0, span0, work = serve(fdf, reqs, tables, [0.0] * n_req, max_active, slice_steps, merge)
     capacity = work / span0
     mean_service = work / n_req / capacity
     rate = load / mean_service
     gaps = np.random.default_rng(SERVED_ARRIVAL_SEED).exponential(1.0 / rate, size=n_req)
     arrivals = np.cumsum(gaps) - gaps[0]
-    lat, span, work = serve(fdf, reqs, tables, arrivals, max_active, slice_steps)
-    return {"requests": n_req, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+    lat, span, work = serve(fdf, reqs, tables, arrivals, max_active, slice_steps, merge)
+    return {"requests": n_req, "merged_passes": merge,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "max_s": float(lat.max()), "value": work / span, "unit": UNIT,
             "capacity": capacity, "offered_load": load, "arrival_rate_per_s": rate,
             "saturated_p50_s": float(np.percentile(lat0, 50)), "saturated_p99_s": float(np.percentile(lat0, 99)),
             "budget_bytes": SERVED_BUDGET, "max_active": max_active, "slice_steps": slice_steps,
-            "note": "requests: grid 64/128/256, 64^3..512^3 particles per species, 1-3 species, m U(0.02, 0.3) eV, "
-                    "100-300 steps, box 1000 Mpc, FP32 grids (request i from seed 1000 + i); Poisson arrivals "
-                    "(seed 5) at %.0f%% of the capacity measured with every request queued at once; latency = "
-                    "submit to results resident on the device" % (100 * load)}
+            "note": ("requests: grid 64/128/256, 64^3..512^3 particles per species, 1-3 species, m U(0.02, 0.3) eV, "
+                     "100-300 steps, box 1000 Mpc, FP32 grids and FP64 state (request i from seed 1000 + i); %s; "
+                     "Poisson arrivals (seed 5) at %.0f%% of the capacity measured with every request queued at "
+                     "once; latency = submit to results resident on the device"
+                     % ("one merged launch per round steps a pass of every running request" if merge else
+                        "each request launches its own passes on its own streams", 100 * load))}
 
 
 # ----------------------------------------------------------------------------------------------
@@ -697,6 +701,7 @@ def main():
                          note="the reduced-precision workload, timed as the headline (graph replays + deposit)")
     if not args.no_served and world == 1:
         out["served"] = bench_served(args.served_requests)
+        out["served_merged"] = bench_served(args.served_requests, merge=True)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(out))

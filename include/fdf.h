@@ -64,9 +64,10 @@ extern "C" {
  *   int eps_0 dtau and int dtau / eps_0 (eq:discrete_drift, eq:releq_approx).
  *   Each integral is r_c sum_k C_k t^k, a series about the interval's centre in
  *   t = m^2 a_c^2 r_c^2 with r_c = (|q|^2 + m^2 a_c^2)^(-1/2) and FP64
- *   coefficients from the host; r_c, t and the leading terms (six for the drift,
- *   three for a kick) are FP64, and the terms beyond them, which add less than
- *   1e-7 of the integral at the workloads' step sizes, are FP32.  The kick
+ *   coefficients from the host; r_c, t and the leading terms (five for the
+ *   drift, one for a kick, whose integrals only scale a kick of ~1e-3 of |q|) are
+ *   FP64, and the terms beyond them (below 1e-7 of the drift integral, 3e-3 of
+ *   a kick's, at the workloads' step sizes) are FP32.  The kick
  *   itself (a change of at most ~1e-3 of |q| per step) is formed in FP32 from
  *   the FP32 gradients and q_0 (stored in FP32) and added to q in FP64.
  * FDF_PREC_BF16: FDF_PREC_F32 with BF16 gradient-grid storage (FP32
@@ -432,6 +433,19 @@ typedef struct fdf_request_info {
  * fdf_step call of the worker (>= 1).  FDF_ENOMEM if the arena cannot be
  * allocated. */
 FDF_API int fdf_server_create(size_t hbm_budget, int32_t max_active, int32_t slice_steps, fdf_server** out);
+
+/* fdf_server_create with options: FDF_SERVER_MERGE_PASSES steps the running requests
+ * of the FP32/BF16-grid forms with the FP64 state (per grid precision, at most 16 at a
+ * time) in merged launches, one kernel issuing the next pass of every such request
+ * (the other forms keep their own launches).  Each request's particles run the same
+ * arithmetic alone and in a merge, so its results are bitwise the same either way
+ * within this mode; against the default mode they differ by rounding only. */
+#define FDF_SERVER_MERGE_PASSES 1
+FDF_API int fdf_server_create_opts(size_t hbm_budget, int32_t max_active, int32_t slice_steps, int32_t options,
+                                   fdf_server** out);
+
+/* The number of merged launches the server made so far (0 without FDF_SERVER_MERGE_PASSES). */
+FDF_API int fdf_server_merged_launches(const fdf_server* s, int64_t* launches);
 
 /* Queue a run.  p and t are copied (host memory; the caller may free them on
  * return).  *id receives the request's id.  FDF_EINVAL for invalid

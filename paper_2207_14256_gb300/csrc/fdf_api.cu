@@ -409,6 +409,13 @@ struct fdf_ctx {
     int64_t launches = 0;
     // the passes of the last fdf_step: all with series integrals, count, most steps in one
     int pass_series = 1, pass_count = 0, pass_steps = 0;
+    // the call of fdf_step being issued (slice_begin .. slice_done)
+    struct Slice {
+        bool active = false;
+        int dir = 1, steps = 0, k_start = 0, passes = 0, j = 0;
+        std::vector<int> bufs_cur, bufs_next;
+        std::vector<const void*> grids_cur, grids_next;
+    } slice;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> pool;
@@ -1204,6 +1211,160 @@ cudaStream_t ctx_stream(fdf_ctx* c) { return c->stream; }
 
 }  // namespace fdf
 
+namespace fdf {
+
+// ---- a call of fdf_step, pass by pass -------------------------------------------------
+// Passes of up to spp leapfrog steps; pass j covers steps [first_j, first_j + len_j).  The
+// grids of pass j+1 are built on the fields stream while pass j runs.  fdf_step runs the
+// passes one after the other; the request server can launch the passes of several
+// contexts together (slice_next gives a pass's arguments, slice_done what follows it).
+namespace {
+
+int pass_first(const fdf_ctx* c, int j) { return j * c->spp; }
+int pass_len(const fdf_ctx* c, int j) { return std::min(c->spp, c->slice.steps - j * c->spp); }
+
+// The grids pass j reads (its opening half kick's, then one per step), built as needed.
+int slice_prepare(fdf_ctx* c, int j, std::vector<int>& bufs, std::vector<const void*>& grids, unsigned busy)
+{
+    const auto& sl = c->slice;
+    bufs.clear();
+    grids.clear();
+    std::vector<int> ks;
+    if (j == 0) ks.push_back(sl.k_start);                       // the opening half kick
+    for (int i = 0; i < pass_len(c, j); ++i) ks.push_back(sl.k_start + sl.dir * (pass_first(c, j) + i + 1));
+    for (int kk : ks) {
+        const void* G = nullptr;
+        int b = -1;
+        int rc = ensure_grid(c, kk, busy, &G, &b);
+        if (rc) return rc;
+        if (b >= 0) busy |= 1u << b;
+        bufs.push_back(b);
+        grids.push_back(G);
+    }
+    return FDF_OK;
+}
+
+unsigned mask_of(const std::vector<int>& bufs)
+{
+    unsigned m = 0;
+    for (int b : bufs)
+        if (b >= 0) m |= 1u << b;
+    return m;
+}
+
+}  // namespace
+
+int slice_begin(fdf_ctx* c, int32_t n)
+{
+    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
+    if (!c->sampled) return fail(FDF_ESTATE, "fdf_step before fdf_sample");
+    if (c->slice.active) return fail(FDF_ESTATE, "a slice of steps is still being issued");
+    const int64_t target = (int64_t)c->k + n;
+    if (target < 0 || target > c->p.n_steps) return fail(FDF_EINVAL, "step index would leave [0, n_steps]");
+    if (n == 0) return FDF_OK;
+    c->stepped = true;
+    c->pass_series = 1;
+    c->pass_count = 0;
+    c->pass_steps = 0;
+    auto& sl = c->slice;
+    sl.dir = n > 0 ? 1 : -1;
+    sl.steps = n > 0 ? n : -n;
+    sl.k_start = c->k;
+    sl.passes = (sl.steps + c->spp - 1) / c->spp;
+    sl.j = 0;
+    int rc = slice_prepare(c, 0, sl.bufs_cur, sl.grids_cur, 0u);
+    if (rc) return rc;
+    sl.active = true;
+    return FDF_OK;
+}
+
+bool slice_active(const fdf_ctx* c) { return c->slice.active; }
+
+int slice_next(fdf_ctx* c, PushArgs& a)
+{
+    auto& sl = c->slice;
+    if (!sl.active) return fail(FDF_ESTATE, "no pass to issue");
+    const int j = sl.j, dir = sl.dir;
+    if (j + 1 < sl.passes) {
+        int rc = slice_prepare(c, j + 1, sl.bufs_next, sl.grids_next, mask_of(sl.bufs_cur));
+        if (rc) return rc;
+    }
+    fill_pass(c, a);
+    a.nsub = 0;
+    size_t gi = 0;
+    if (j == 0) {
+        fill_substep(c, false, 0, 0, true, c->lna(c->k), c->lna(c->k + 0.5 * dir), a.sub[0]);
+        a.G[0] = sl.grids_cur[gi++];
+        a.nsub = 1;
+    }
+    for (int i = 0; i < pass_len(c, j); ++i) {
+        const int k0 = c->k, k1 = k0 + dir;
+        const bool last = (j == sl.passes - 1) && (i == pass_len(c, j) - 1);
+        // drift over the step; merged kick (closing half of this step, opening half
+        // of the next) at x_{k+1} with the fields of step k+1, or only the closing half
+        if (c->p.eom == FDF_EOM_EXACT) {
+            // the halves stay apart: each holds q at its own start (eq:releq)
+            fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir), c->lna(k1), a.sub[a.nsub]);
+            a.G[a.nsub] = sl.grids_cur[gi];
+            ++a.nsub;
+            if (!last) {
+                fill_substep(c, false, 0, 0, true, c->lna(k1), c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
+                a.G[a.nsub] = sl.grids_cur[gi];
+                ++a.nsub;
+            }
+            ++gi;
+        } else {
+            fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir),
+                         last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
+            a.G[a.nsub] = sl.grids_cur[gi++];
+            ++a.nsub;
+        }
+        c->k = k1;
+        c->disp += typical_displacement(c, c->lna(k0), c->lna(k1));
+    }
+    a.drift_series = 1;
+    for (int u = 0; u < a.nsub; ++u) {
+        if (a.sub[u].emax > kSeriesMaxE) a.drift_series = 0;
+        if (!a.sub[u].wide_ok) a.wide_series = 0;
+    }
+    const int form = form_of(c->p.precision);
+    if ((form == kWide && !a.wide_series) || (form == kFixed && !a.drift_series) || form == kPlain)
+        c->pass_series = 0;
+    ++c->pass_count;
+    c->pass_steps = std::max(c->pass_steps, pass_len(c, j));
+    // the context's stream waits for the pass's grids
+    for (int b : sl.bufs_cur) {
+        int rc = acquire_grid(c, b);
+        if (rc) return rc;
+    }
+    return FDF_OK;
+}
+
+int slice_done(fdf_ctx* c)
+{
+    auto& sl = c->slice;
+    for (int b : sl.bufs_cur) {
+        int rc = release_grid(c, b);
+        if (rc) return rc;
+    }
+    if (sl.j + 1 < sl.passes) {
+        int rc = maybe_sort(c, (c->k - sl.k_start) * sl.dir, sl.dir);
+        if (rc) return rc;
+    }
+    std::swap(sl.bufs_cur, sl.bufs_next);
+    std::swap(sl.grids_cur, sl.grids_next);
+    if (++sl.j == sl.passes) {
+        sl.active = false;
+        return join_fields(c);
+    }
+    return FDF_OK;
+}
+
+const ParticleState& ctx_state(const fdf_ctx* c) { return c->st; }
+int ctx_precision(const fdf_ctx* c) { return c->p.precision; }
+
+}  // namespace fdf
+
 extern "C" {
 
 int fdf_sample(fdf_ctx* c)
@@ -1222,118 +1383,14 @@ int fdf_sample(fdf_ctx* c)
 
 int fdf_step(fdf_ctx* c, int32_t n)
 {
-    if (!c) return fail(FDF_EINVAL, "ctx is NULL");
-    if (!c->sampled) return fail(FDF_ESTATE, "fdf_step before fdf_sample");
-    const int64_t target = (int64_t)c->k + n;
-    if (target < 0 || target > c->p.n_steps) return fail(FDF_EINVAL, "step index would leave [0, n_steps]");
-    if (n == 0) return FDF_OK;
-    c->stepped = true;
-    c->pass_series = 1;
-    c->pass_count = 0;
-    c->pass_steps = 0;
-    const int dir = n > 0 ? 1 : -1;
-    const int steps = n > 0 ? n : -n;
-    const int k_start = c->k;
-    // Passes of up to spp leapfrog steps; pass j covers steps [first_j, first_j + len_j).
-    // The grids of pass j+1 are built on the fields stream while pass j runs.
-    auto pass_first = [&](int j) { return j * c->spp; };
-    auto pass_len = [&](int j) { return std::min(c->spp, steps - j * c->spp); };
-    const int passes = (steps + c->spp - 1) / c->spp;
-    std::vector<int> bufs_cur, bufs_next;
-    std::vector<const void*> grids_cur, grids_next;
-    auto prepare = [&](int j, std::vector<int>& bufs, std::vector<const void*>& grids, unsigned busy) -> int {
-        bufs.clear();
-        grids.clear();
-        std::vector<int> ks;
-        if (j == 0) ks.push_back(k_start);                       // the opening half kick
-        for (int i = 0; i < pass_len(j); ++i) ks.push_back(k_start + dir * (pass_first(j) + i + 1));
-        for (int kk : ks) {
-            const void* G = nullptr;
-            int b = -1;
-            int rc = ensure_grid(c, kk, busy, &G, &b);
-            if (rc) return rc;
-            if (b >= 0) busy |= 1u << b;
-            bufs.push_back(b);
-            grids.push_back(G);
-        }
-        return FDF_OK;
-    };
-    auto mask_of = [](const std::vector<int>& bufs) {
-        unsigned m = 0;
-        for (int b : bufs)
-            if (b >= 0) m |= 1u << b;
-        return m;
-    };
-    int rc = prepare(0, bufs_cur, grids_cur, 0u);
-    if (rc) return rc;
-    for (int j = 0; j < passes; ++j) {
-        if (j + 1 < passes) {
-            rc = prepare(j + 1, bufs_next, grids_next, mask_of(bufs_cur));
-            if (rc) return rc;
-        }
+    int rc = slice_begin(c, n);
+    while (rc == FDF_OK && slice_active(c)) {
         PushArgs a;
-        fill_pass(c, a);
-        a.nsub = 0;
-        size_t gi = 0;
-        if (j == 0) {
-            fill_substep(c, false, 0, 0, true, c->lna(c->k), c->lna(c->k + 0.5 * dir), a.sub[0]);
-            a.G[0] = grids_cur[gi++];
-            a.nsub = 1;
-        }
-        for (int i = 0; i < pass_len(j); ++i) {
-            const int k0 = c->k, k1 = k0 + dir;
-            const bool last = (j == passes - 1) && (i == pass_len(j) - 1);
-            // drift over the step; merged kick (closing half of this step, opening half
-            // of the next) at x_{k+1} with the fields of step k+1, or only the closing half
-            if (c->p.eom == FDF_EOM_EXACT) {
-                // the halves stay apart: each holds q at its own start (eq:releq)
-                fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir), c->lna(k1),
-                             a.sub[a.nsub]);
-                a.G[a.nsub] = grids_cur[gi];
-                ++a.nsub;
-                if (!last) {
-                    fill_substep(c, false, 0, 0, true, c->lna(k1), c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
-                    a.G[a.nsub] = grids_cur[gi];
-                    ++a.nsub;
-                }
-                ++gi;
-            } else {
-                fill_substep(c, true, c->lna(k0), c->lna(k1), true, c->lna(k0 + 0.5 * dir),
-                             last ? c->lna(k1) : c->lna(k1 + 0.5 * dir), a.sub[a.nsub]);
-                a.G[a.nsub] = grids_cur[gi++];
-                ++a.nsub;
-            }
-            c->k = k1;
-            c->disp += typical_displacement(c, c->lna(k0), c->lna(k1));
-        }
-        a.drift_series = 1;
-        for (int u = 0; u < a.nsub; ++u) {
-            if (a.sub[u].emax > kSeriesMaxE) a.drift_series = 0;
-            if (!a.sub[u].wide_ok) a.wide_series = 0;
-        }
-        const int form = form_of(c->p.precision);
-        if ((form == kWide && !a.wide_series) || (form == kFixed && !a.drift_series) || form == kPlain)
-            c->pass_series = 0;
-        ++c->pass_count;
-        c->pass_steps = std::max(c->pass_steps, pass_len(j));
-        for (int b : bufs_cur) {
-            rc = acquire_grid(c, b);
-            if (rc) return rc;
-        }
-        rc = push(c, a);
-        if (rc) return rc;
-        for (int b : bufs_cur) {
-            rc = release_grid(c, b);
-            if (rc) return rc;
-        }
-        if (j + 1 < passes) {
-            rc = maybe_sort(c, (c->k - k_start) * dir, dir);
-            if (rc) return rc;
-        }
-        std::swap(bufs_cur, bufs_next);
-        std::swap(grids_cur, grids_next);
+        rc = slice_next(c, a);
+        if (!rc) rc = push(c, a);
+        if (!rc) rc = slice_done(c);
     }
-    return join_fields(c);
+    return rc;
 }
 
 int fdf_run_graph(fdf_ctx* c, int32_t n)

@@ -70,7 +70,7 @@ struct SpeciesCoef {
 // kWideK64 (kick) coefficients in FP64 and the rest in FP32.
 constexpr int kWideDeg = 10;    // highest degree of a fitted polynomial
 constexpr int kWideD64 = 5;     // drift terms evaluated in FP64
-constexpr int kWideK64 = 2;     // kick terms evaluated in FP64
+constexpr int kWideK64 = 1;     // kick terms evaluated in FP64 (the kick needs ~1e-9)
 
 struct WidePoly {
     double c64[kWideD64];       // coefficients 0..kWideD64-1 (FP64)
@@ -220,6 +220,23 @@ cudaError_t launch_initial(cudaStream_t s, int precision, const ParticleState& s
                            const double* m_ev, double a0, double tau0, int order, int N, double L, const void* G);
 cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, const PushArgs& a);
 
+// The passes of up to kMaxMerge contexts of the FP64-state form with one grid precision,
+// in one launch: segment k covers global particle indices [begin, begin + args->n).
+constexpr int kMaxMerge = 16;
+struct MultiPass {
+    struct Seg {
+        int64_t begin;
+        const PushArgs* args;   // device memory
+        double* xd;
+        double* qd;
+        const float* q0f;
+    };
+    int nseg;
+    int64_t total;
+    Seg seg[kMaxMerge];
+};
+cudaError_t launch_push_multi(cudaStream_t s, int grid_precision, const MultiPass& m, int grid_blocks);
+
 // Counting sort of the particle state a into b by (species, Morton index of
 // the particle's tile of 2^tile_shift cells per axis, tile_shift = sort_tile).  key: n words; hist:
 // n_species * tiles words; bsum: scan_scratch_words(bins) words; recs: n records
@@ -270,6 +287,16 @@ cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& s
 int sample_enqueue(fdf_ctx* c);
 int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, int32_t parity, double* out_dev);
 int* ctx_error_flag(fdf_ctx* c);
+// fdf_step(c, n) pass by pass: slice_begin(c, n), then while slice_active(c):
+// slice_next (the pass's arguments; c's stream then waits for the pass's grids), a
+// launch of the pass on c's stream (or one that c's stream waits for), slice_done (the
+// grids' release and a re-sort, on c's stream).
+int slice_begin(fdf_ctx* c, int32_t n);
+bool slice_active(const fdf_ctx* c);
+int slice_next(fdf_ctx* c, PushArgs& a);
+int slice_done(fdf_ctx* c);
+const ParticleState& ctx_state(const fdf_ctx* c);
+int ctx_precision(const fdf_ctx* c);
 cudaStream_t ctx_stream(fdf_ctx* c);
 double* ctx_deposit_grid(fdf_ctx* c);
 

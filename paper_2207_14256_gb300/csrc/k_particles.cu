@@ -634,6 +634,58 @@ __device__ __forceinline__ void kick_integrals(const SubStep& st, int s, int n_k
     Kphif = d2f_bits(Kphi);
 }
 
+// One particle through the sub-steps of a pass of the FP64-state form.
+template <typename Gt, bool SERIES, bool UNI>
+__device__ __forceinline__ void wide_particle(const PushArgs& a, double* __restrict__ xd, double* __restrict__ qd,
+                                              const float* __restrict__ q0f, int64_t i)
+{
+    const int64_t n = a.n;
+    const uint32_t N = (uint32_t)a.N;
+    const float invh = (float)a.invh;
+    const long long Lbits = __double_as_longlong(a.L);
+    const int s = UNI ? 0 : species_of(a, i);
+    double x[3] = {__ldcs(xd + i), __ldcs(xd + n + i), __ldcs(xd + 2 * n + i)};
+    double q[3] = {__ldcs(qd + i), __ldcs(qd + n + i), __ldcs(qd + 2 * n + i)};
+    const float qa = __ldcs(q0f + i), qb = __ldcs(q0f + n + i), qc = __ldcs(q0f + 2 * n + i);
+    // |q0|^2: exact products of the FP32 components, summed in FP64 (once per pass)
+    const double da = f2d_bits(qa), db = f2d_bits(qb), dc = f2d_bits(qc);
+    const double s0 = fma(da, da, fma(db, db, dc * dc));
+    const float q02 = d2f_bits(s0);
+    bool moved = false, kicked = false;
+    for (int u = 0; u < a.nsub; ++u) {
+        const SubStep& st = a.sub[u];
+        float Kpsif = 0.f, Kphif = 0.f;
+        if (st.do_kick) kick_integrals<SERIES>(st, s, a.n_kick, s0, Kpsif, Kphif);
+        if (st.do_drift) {
+            const double D = drift_integral<SERIES>(st, s, a.n_gl, q);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) x[d] = wrap_rare(fma(q[d], D, x[d]), a.L, a.invL, Lbits);
+            moved = true;
+        }
+        if (st.do_kick) {
+            float g[8];
+            gather_wide<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, invh, x, g);
+            const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
+            const float b = qdphi * Kphif + g[6] * st.wide.dtau_k;
+            const float a2 = q02 * Kphif;
+            q[0] += f2d_bits(-g[0] * Kpsif - g[3] * a2 + qa * b);
+            q[1] += f2d_bits(-g[1] * Kpsif - g[4] * a2 + qb * b);
+            q[2] += f2d_bits(-g[2] * Kpsif - g[5] * a2 + qc * b);
+            kicked = true;
+        }
+    }
+    if (moved) {
+        __stcs(xd + i, x[0]);
+        __stcs(xd + n + i, x[1]);
+        __stcs(xd + 2 * n + i, x[2]);
+    }
+    if (kicked) {
+        __stcs(qd + i, q[0]);
+        __stcs(qd + n + i, q[1]);
+        __stcs(qd + 2 * n + i, q[2]);
+    }
+}
+
 // Three resident blocks per SM (80 registers, no spills): 24 warps keep the FP64 pipe
 // busy through the latency of its results and of the gather.
 template <typename Gt, bool SERIES, bool UNI>
@@ -641,55 +693,29 @@ __global__ void __launch_bounds__(kThreads, 3) k_push_wide(const __grid_constant
                                                            double* __restrict__ xd, double* __restrict__ qd,
                                                            const float* __restrict__ q0f)
 {
-    const int64_t n = a.n;
-    const uint32_t N = (uint32_t)a.N;
-    const float invh = (float)a.invh;
-    const long long Lbits = __double_as_longlong(a.L);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.n; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
-        if (i >= n) continue;
-        const int s = UNI ? 0 : species_of(a, i);
-        double x[3] = {__ldcs(xd + i), __ldcs(xd + n + i), __ldcs(xd + 2 * n + i)};
-        double q[3] = {__ldcs(qd + i), __ldcs(qd + n + i), __ldcs(qd + 2 * n + i)};
-        const float qa = __ldcs(q0f + i), qb = __ldcs(q0f + n + i), qc = __ldcs(q0f + 2 * n + i);
-        // |q0|^2: exact products of the FP32 components, summed in FP64 (once per pass)
-        const double da = f2d_bits(qa), db = f2d_bits(qb), dc = f2d_bits(qc);
-        const double s0 = fma(da, da, fma(db, db, dc * dc));
-        const float q02 = d2f_bits(s0);
-        bool moved = false, kicked = false;
-        for (int u = 0; u < a.nsub; ++u) {
-            const SubStep& st = a.sub[u];
-            float Kpsif = 0.f, Kphif = 0.f;
-            if (st.do_kick) kick_integrals<SERIES>(st, s, a.n_kick, s0, Kpsif, Kphif);
-            if (st.do_drift) {
-                const double D = drift_integral<SERIES>(st, s, a.n_gl, q);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) x[d] = wrap_rare(fma(q[d], D, x[d]), a.L, a.invL, Lbits);
-                moved = true;
-            }
-            if (st.do_kick) {
-                float g[8];
-                gather_wide<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, invh, x, g);
-                const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
-                const float b = qdphi * Kphif + g[6] * st.wide.dtau_k;
-                const float a2 = q02 * Kphif;
-                q[0] += f2d_bits(-g[0] * Kpsif - g[3] * a2 + qa * b);
-                q[1] += f2d_bits(-g[1] * Kpsif - g[4] * a2 + qb * b);
-                q[2] += f2d_bits(-g[2] * Kpsif - g[5] * a2 + qc * b);
-                kicked = true;
-            }
-        }
-        if (moved) {
-            __stcs(xd + i, x[0]);
-            __stcs(xd + n + i, x[1]);
-            __stcs(xd + 2 * n + i, x[2]);
-        }
-        if (kicked) {
-            __stcs(qd + i, q[0]);
-            __stcs(qd + n + i, q[1]);
-            __stcs(qd + 2 * n + i, q[2]);
-        }
+        if (i < a.n) wide_particle<Gt, SERIES, UNI>(a, xd, qd, q0f, i);
+    }
+}
+
+// The passes of several contexts in one launch (the request server): the particles of
+// segment k are the global indices [seg[k].begin, seg[k].begin + args->n), each segment's
+// pass arguments in device memory.  Every particle runs the arithmetic of k_push_wide.
+template <typename Gt>
+__global__ void __launch_bounds__(kThreads, 3) k_push_wide_multi(const __grid_constant__ MultiPass m)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < m.total; g0 += stride) {
+        const int64_t g = g0 + threadIdx.x;
+        if (g >= m.total) continue;
+        int k = 0;
+        while (k + 1 < m.nseg && g >= m.seg[k + 1].begin) ++k;
+        const MultiPass::Seg& sg = m.seg[k];
+        const PushArgs& a = *sg.args;
+        if (a.wide_series) wide_particle<Gt, true, false>(a, sg.xd, sg.qd, sg.q0f, g - sg.begin);
+        else wide_particle<Gt, false, false>(a, sg.xd, sg.qd, sg.q0f, g - sg.begin);
     }
 }
 
@@ -1039,6 +1065,17 @@ cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, 
             else push_split<__nv_bfloat16, false>(s, b, a, st);
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_multi(cudaStream_t s, int grid_precision, const MultiPass& m, int grid_blocks)
+{
+    if (m.total <= 0) return cudaSuccess;
+    int64_t nb = (m.total + kThreads - 1) / kThreads;
+    if (nb > grid_blocks) nb = grid_blocks;
+    const unsigned b = (unsigned)(nb < 1 ? 1 : nb);
+    if (grid_precision == FDF_PREC_F32) k_push_wide_multi<float><<<b, kThreads, 0, s>>>(m);
+    else k_push_wide_multi<__nv_bfloat16><<<b, kThreads, 0, s>>>(m);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,7 @@ using Clock = std::chrono::steady_clock;
 constexpr size_t kArenaAlign = 2u << 20;   // ranges start on 2 MiB boundaries
 constexpr int kMaxInFlight = 2;            // step slices enqueued ahead per request
 constexpr int kFlagSlots = 4096;           // requests held at once (pinned flag words)
+constexpr int kRing = 4;                   // merged pass launches in flight
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -102,6 +103,8 @@ struct Request {
     int issued = 0;
     std::deque<cudaEvent_t> inflight;
     cudaEvent_t done_ev = nullptr;
+    cudaEvent_t pass_ev = nullptr;   // merged passes: the request's stream is ready for its pass
+    bool merged = false;             // its passes go into the server's merged launches
     int slot = -1;
     int* hflag = nullptr;        // pinned copy of the sampling error flag (a slot of the server's pool)
     Clock::time_point origin;
@@ -129,6 +132,19 @@ struct fdf_server {
     std::vector<int> free_slots;
     bool stop = false;
     std::thread worker;
+    // merged passes (FDF_SERVER_MERGE_PASSES): one launch steps one pass of every running
+    // request of the FP64-state form (per grid precision), from a ring of argument slots
+    bool merge = false;
+    cudaStream_t ms = nullptr;
+    struct Slot {
+        fdf::PushArgs* host = nullptr;   // pinned, kMaxMerge entries
+        fdf::PushArgs* dev = nullptr;    // device, kMaxMerge entries
+        cudaEvent_t done = nullptr;
+        bool used = false;
+    } ring[fdf::kRing];
+    int next_slot = 0;
+    int sm_count = 152;
+    int64_t merged_launches = 0;
 
     double now() const { return std::chrono::duration<double>(fdf::Clock::now() - t0).count(); }
 };
@@ -162,6 +178,8 @@ void teardown(Request* r)
     r->inflight.clear();
     if (r->done_ev) cudaEventDestroy(r->done_ev);
     r->done_ev = nullptr;
+    if (r->pass_ev) cudaEventDestroy(r->pass_ev);
+    r->pass_ev = nullptr;
     if (r->ctx) fdf_destroy(r->ctx);
     r->ctx = nullptr;
     if (r->stream) cudaStreamDestroy(r->stream);
@@ -182,6 +200,8 @@ bool advance(fdf_server* S, Request* r)
         const int prio = greatest + std::min(r->rank, levels - 1);
         cudaError_t e = cudaStreamCreateWithPriority(&r->stream, cudaStreamNonBlocking, prio);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->pass_ev, cudaEventDisableTiming);
+        r->merged = S->merge && form_of(r->p.precision) == kWide;
         if (e != cudaSuccess) {
             fail_request(S, r, FDF_ECUDA, std::string("server: ") + cudaGetErrorString(e));
             return true;
@@ -205,7 +225,21 @@ bool advance(fdf_server* S, Request* r)
         did = true;
     }
     if (!r->finishing) {
-        if (r->issued < r->p.n_steps && (int)r->inflight.size() < kMaxInFlight) {
+        if (r->merged) {
+            // the worker's merged launches issue the passes of the slice begun here
+            if (slice_active(r->ctx)) return did;
+            if (r->issued < r->p.n_steps) {
+                const int n = std::min(S->slice, r->p.n_steps - r->issued);
+                int rc = slice_begin(r->ctx, n);
+                if (rc) {
+                    fail_request(S, r, rc, fdf_last_error());
+                    return true;
+                }
+                r->issued += n;
+                return true;
+            }
+        }
+        if (!r->merged && r->issued < r->p.n_steps && (int)r->inflight.size() < kMaxInFlight) {
             const int n = std::min(S->slice, r->p.n_steps - r->issued);
             int rc = fdf_step(r->ctx, n);
             cudaEvent_t ev = nullptr;
@@ -259,6 +293,71 @@ bool advance(fdf_server* S, Request* r)
     return true;
 }
 
+// One merged launch: the next pass of each request of `group` (all of the FP64-state form
+// with one grid precision, at most kMaxMerge), in one kernel on the server's stream.
+// Each request's stream is ordered before it (its previous pass, re-sorts and field
+// builds) and after it (the grids' release, the next re-sort).
+void merged_tick(fdf_server* S, const std::vector<Request*>& group, int gprec)
+{
+    auto& slot = S->ring[S->next_slot];
+    S->next_slot = (S->next_slot + 1) % kRing;
+    if (slot.used) cudaEventSynchronize(slot.done);   // its pinned arguments are free again
+    slot.used = true;
+    MultiPass m{};
+    std::vector<Request*> in;
+    for (Request* r : group) {
+        const int k = (int)in.size();
+        int rc = slice_next(r->ctx, slot.host[k]);
+        cudaError_t e = cudaSuccess;
+        if (!rc) e = cudaEventRecord(r->pass_ev, r->stream);
+        if (!rc && e == cudaSuccess) e = cudaStreamWaitEvent(S->ms, r->pass_ev, 0);
+        if (rc || e != cudaSuccess) {
+            fail_request(S, r, rc ? rc : FDF_ECUDA, rc ? fdf_last_error() : cudaGetErrorString(e));
+            continue;
+        }
+        const ParticleState& st = ctx_state(r->ctx);
+        m.seg[k] = MultiPass::Seg{m.total, slot.dev + k, st.xd, st.qd, st.q0f};
+        m.total += slot.host[k].n;
+        in.push_back(r);
+    }
+    m.nseg = (int)in.size();
+    cudaError_t e = cudaSuccess;
+    if (m.nseg) {
+        e = cudaMemcpyAsync(slot.dev, slot.host, m.nseg * sizeof(PushArgs), cudaMemcpyHostToDevice, S->ms);
+        if (e == cudaSuccess) e = launch_push_multi(S->ms, gprec, m, S->sm_count * 3);
+        ++S->merged_launches;
+    }
+    cudaEventRecord(slot.done, S->ms);
+    for (Request* r : in) {
+        int rc = FDF_OK;
+        cudaError_t w = e;
+        if (w == cudaSuccess) w = cudaStreamWaitEvent(r->stream, slot.done, 0);
+        if (w == cudaSuccess) rc = slice_done(r->ctx);
+        if (w != cudaSuccess) fail_request(S, r, FDF_ECUDA, std::string("server: ") + cudaGetErrorString(w));
+        else if (rc) fail_request(S, r, rc, fdf_last_error());
+    }
+}
+
+// The merged launches of one round: every running request with a pass to issue, by grid
+// precision, in groups of at most kMaxMerge.
+bool merged_round(fdf_server* S, const std::vector<Request*>& run)
+{
+    bool did = false;
+    for (int gprec : {FDF_PREC_F32, FDF_PREC_BF16}) {
+        std::vector<Request*> group;
+        for (Request* r : run)
+            if (r->merged && r->ctx && r->status == FDF_REQ_RUNNING && !r->finishing && slice_active(r->ctx) &&
+                grid_prec(r->p.precision) == gprec)
+                group.push_back(r);
+        for (size_t b = 0; b < group.size(); b += kMaxMerge) {
+            std::vector<Request*> part(group.begin() + b, group.begin() + std::min(group.size(), b + kMaxMerge));
+            merged_tick(S, part, gprec);
+            did = true;
+        }
+    }
+    return did;
+}
+
 void worker_loop(fdf_server* S)
 {
     cudaSetDevice(S->device);
@@ -283,6 +382,7 @@ void worker_loop(fdf_server* S)
         lk.unlock();
         bool did = false;
         for (Request* r : run) did |= advance(S, r);
+        if (S->merge) did |= merged_round(S, run);
         lk.lock();
         // finished requests leave the running set (they keep their memory until released)
         S->running.erase(std::remove_if(S->running.begin(), S->running.end(),
@@ -310,10 +410,17 @@ extern "C" {
 
 int fdf_server_create(size_t hbm_budget, int32_t max_active, int32_t slice_steps, fdf_server** out)
 {
+    return fdf_server_create_opts(hbm_budget, max_active, slice_steps, 0, out);
+}
+
+int fdf_server_create_opts(size_t hbm_budget, int32_t max_active, int32_t slice_steps, int32_t options,
+                           fdf_server** out)
+{
     if (!out) return set_error(FDF_EINVAL, "out is NULL");
     *out = nullptr;
     if (max_active < 1 || slice_steps < 1 || hbm_budget < kArenaAlign)
         return set_error(FDF_EINVAL, "need max_active >= 1, slice_steps >= 1 and a budget of at least 2 MiB");
+    if (options & ~FDF_SERVER_MERGE_PASSES) return set_error(FDF_EINVAL, "unknown server options");
     auto S = std::make_unique<fdf_server>();
     cudaError_t e = cudaGetDevice(&S->device);
     if (e != cudaSuccess) return set_error(FDF_ECUDA, cudaGetErrorString(e));
@@ -329,6 +436,29 @@ int fdf_server_create(size_t hbm_budget, int32_t max_active, int32_t slice_steps
         return set_error(FDF_ENOMEM, (std::string("server flags: ") + cudaGetErrorString(e)).c_str());
     }
     for (int i = kFlagSlots - 1; i >= 0; --i) S->free_slots.push_back(i);
+    S->merge = (options & FDF_SERVER_MERGE_PASSES) != 0;
+    if (S->merge) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device) == cudaSuccess && sms > 0)
+            S->sm_count = sms;
+        e = cudaStreamCreateWithFlags(&S->ms, cudaStreamNonBlocking);
+        for (int i = 0; i < kRing && e == cudaSuccess; ++i) {
+            e = cudaHostAlloc((void**)&S->ring[i].host, kMaxMerge * sizeof(PushArgs), cudaHostAllocDefault);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&S->ring[i].dev, kMaxMerge * sizeof(PushArgs));
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ring[i].done, cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            for (auto& sl : S->ring) {
+                if (sl.host) cudaFreeHost(sl.host);
+                if (sl.dev) cudaFree(sl.dev);
+                if (sl.done) cudaEventDestroy(sl.done);
+            }
+            if (S->ms) cudaStreamDestroy(S->ms);
+            cudaFree(S->arena);
+            cudaFreeHost(S->flags);
+            return set_error(FDF_ENOMEM, (std::string("server merged passes: ") + cudaGetErrorString(e)).c_str());
+        }
+    }
     S->ranges.init(S->budget);
     S->max_active = max_active;
     S->slice = slice_steps;
@@ -475,6 +605,13 @@ int fdf_server_release(fdf_server* S, int64_t id)
 
 double fdf_server_clock(const fdf_server* S) { return S ? S->now() : 0.0; }
 
+int fdf_server_merged_launches(const fdf_server* S, int64_t* launches)
+{
+    if (!S || !launches) return set_error(FDF_EINVAL, "NULL argument");
+    *launches = S->merged_launches;
+    return FDF_OK;
+}
+
 int fdf_server_load(fdf_server* S, int32_t* queued, int32_t* running, size_t* bytes_in_use)
 {
     if (!S) return set_error(FDF_EINVAL, "NULL server");
@@ -496,6 +633,13 @@ void fdf_server_destroy(fdf_server* S)
     if (S->worker.joinable()) S->worker.join();
     for (auto& kv : S->all) teardown(kv.second.get());
     S->all.clear();
+    if (S->ms) cudaStreamSynchronize(S->ms);
+    for (auto& sl : S->ring) {
+        if (sl.host) cudaFreeHost(sl.host);
+        if (sl.dev) cudaFree(sl.dev);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    if (S->ms) cudaStreamDestroy(S->ms);
     if (S->arena) cudaFree(S->arena);
     if (S->flags) cudaFreeHost(S->flags);
     delete S;

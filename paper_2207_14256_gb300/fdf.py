@@ -78,6 +78,7 @@ class fdf_tables(C.Structure):
 
 
 FDF_REQ_QUEUED, FDF_REQ_RUNNING, FDF_REQ_DONE, FDF_REQ_FAILED = 0, 1, 2, 3
+FDF_SERVER_MERGE_PASSES = 1
 
 
 class fdf_request_info(C.Structure):
@@ -134,6 +135,8 @@ def lib():
             "fdf_destroy": (None, [_V]),
             "fdf_tune": (C.c_int, [P, T, _V, P, C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
             "fdf_server_create": (C.c_int, [C.c_size_t, C.c_int32, C.c_int32, C.POINTER(_V)]),
+            "fdf_server_create_opts": (C.c_int, [C.c_size_t, C.c_int32, C.c_int32, C.c_int32, C.POINTER(_V)]),
+            "fdf_server_merged_launches": (C.c_int, [_V, C.POINTER(C.c_int64)]),
             "fdf_server_submit": (C.c_int, [_V, P, T, C.POINTER(C.c_int64)]),
             "fdf_server_wait": (C.c_int, [_V, C.c_int32, C.POINTER(C.c_int64)]),
             "fdf_server_info": (C.c_int, [_V, C.c_int64, C.POINTER(fdf_request_info)]),
@@ -412,6 +415,19 @@ def fdf_server_create(hbm_budget, max_active, slice_steps):
     return srv
 
 
+def fdf_server_create_opts(hbm_budget, max_active, slice_steps, options):
+    srv = _V()
+    _check(lib().fdf_server_create_opts(int(hbm_budget), int(max_active), int(slice_steps), int(options),
+                                        C.byref(srv)), "fdf_server_create_opts")
+    return srv
+
+
+def fdf_server_merged_launches(srv):
+    n = C.c_int64(0)
+    _check(lib().fdf_server_merged_launches(srv, C.byref(n)), "fdf_server_merged_launches")
+    return n.value
+
+
 def fdf_server_submit(srv, params, tables):
     rid = C.c_int64(0)
     _check(lib().fdf_server_submit(srv, C.byref(params), C.byref(tables), C.byref(rid)), "fdf_server_submit")
@@ -545,8 +561,9 @@ class Run:
 class Server:
     """The request server: ``with Server(budget_bytes) as s: rid = s.submit(p, t); s.wait(); s.get(rid)``."""
 
-    def __init__(self, hbm_budget, max_active=8, slice_steps=8):
-        self.srv = fdf_server_create(hbm_budget, max_active, slice_steps)
+    def __init__(self, hbm_budget, max_active=8, slice_steps=8, merge=False):
+        self.srv = fdf_server_create_opts(hbm_budget, max_active, slice_steps,
+                                          FDF_SERVER_MERGE_PASSES if merge else 0)
         self.params = {}
 
     def close(self):
@@ -578,6 +595,9 @@ class Server:
 
     def load(self):
         return fdf_server_load(self.srv)
+
+    def merged_launches(self):
+        return fdf_server_merged_launches(self.srv)
 
     def get(self, rid, species=0):
         n = int(self.params[rid]["n_part"])

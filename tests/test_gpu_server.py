@@ -56,11 +56,14 @@ def _results(F, srv, rid):
     return out, srv.deposit(rid)
 
 
-def test_each_request_is_the_same_alone_and_in_the_mix(F, inputs):
+@pytest.mark.parametrize("merge", [False, True], ids=["streams", "merged"])
+def test_each_request_is_the_same_alone_and_in_the_mix(F, inputs, merge):
+    """With merged passes the FP64-state requests of the mix share launches (the FP32 and
+    the BF16 ones separately); the split-state and plain FP64 requests keep their own."""
     reqs = _mix(inputs)
     tables = inputs.transfer_tables(reqs[0])
     alone = []
-    with F.Server(4 * GiB, max_active=1, slice_steps=5) as srv:
+    with F.Server(4 * GiB, max_active=1, slice_steps=5, merge=merge) as srv:
         for p in reqs:
             rid = srv.submit(p, tables)
             assert srv.wait(120000) == rid
@@ -68,7 +71,7 @@ def test_each_request_is_the_same_alone_and_in_the_mix(F, inputs):
             assert info.status == F.FDF_REQ_DONE, info.message
             alone.append(_results(F, srv, rid))
             srv.release(rid)
-    with F.Server(4 * GiB, max_active=5, slice_steps=5) as srv:
+    with F.Server(4 * GiB, max_active=5, slice_steps=5, merge=merge) as srv:
         ids = [srv.submit(p, tables) for p in reqs[:-1]]
         # one request arrives while the others are on the GPU
         got = srv.wait(120000)
@@ -90,14 +93,18 @@ def test_each_request_is_the_same_alone_and_in_the_mix(F, inputs):
             print("request %d: deposit alone vs mix %.2e of max cell" % (rid, err))
             assert err <= 1e-12
             srv.release(rid)
+        if merge:
+            print("merged launches:", srv.merged_launches())
+            assert srv.merged_launches() > 0
 
 
-def test_server_result_matches_the_oracle(F, inputs):
+@pytest.mark.parametrize("merge", [False, True], ids=["streams", "merged"])
+def test_server_result_matches_the_oracle(F, inputs, merge):
     p = inputs.config("c1_32", n_part=3000, n_grid=16, n_steps=20, precision=1, seed=77)
     tables = inputs.transfer_tables(p)
     o = O.Oracle(p, tables)
     ref = o.run(np.arange(p["n_part"]))
-    with F.Server(2 * GiB, max_active=2, slice_steps=3) as srv:
+    with F.Server(2 * GiB, max_active=2, slice_steps=3, merge=merge) as srv:
         rid = srv.submit(p, tables)
         assert srv.wait(120000) == rid
         assert srv.info(rid).status == F.FDF_REQ_DONE
