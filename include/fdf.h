@@ -169,6 +169,10 @@ typedef struct fdf_params {
                                   that many per SM (persistent), 0 = automatic (3) or 1..3;
                                   fewer leave room on each SM for the field builds of the
                                   next pass.  Ignored by the other forms. */
+    int32_t  gather_tile;      /* the split-state forms: 1 = each block's kicks read the grid from a
+                                  shared-memory tile of the cells its particles occupy (loaded once
+                                  per kick; order-1 reads only), -1 = every read from the grid in
+                                  device memory, 0 = automatic (1).  Ignored by the other forms. */
 } fdf_params;
 
 /* ---- equations of motion (fdf_params.eom) -------------------------------- */
@@ -373,8 +377,9 @@ FDF_API void fdf_destroy(fdf_ctx* c);
  * stated tolerances): sort_cells, sort_tile, steps_per_pass and (FP64-state forms)
  * pass_blocks.  It times whole runs (fdf_sample + fdf_step(n_steps)) of p on the
  * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16},
- * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4}, pass_blocks in {2, 3}, then
- * sort_cells again in {3, 5, 6, 12}), starting from the automatic choices, and writes
+ * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4}, pass_blocks in {2, 3} (FP64-state
+ * forms) or gather_tile in {1, -1} (split-state forms), then sort_cells again in
+ * {3, 5, 6, 12}), starting from the automatic choices, and writes
  * the fastest parameter set to *out (p with the knobs set).  The paper
  * has no counterpart.  stream: a cudaStream_t or NULL; every trial allocates
  * and frees its own context.  ms (may be NULL) receives the best run time;

@@ -312,6 +312,7 @@ int fdf::validate_params(const fdf_params* p)
     if (p->sort_cells < 0) return fail(FDF_EINVAL, "sort_cells must be >= 0");
     if (p->interp_order < 0 || p->interp_order > 2) return fail(FDF_EINVAL, "interp_order must be 0, 1 or 2");
     if (p->pass_blocks < 0 || p->pass_blocks > 3) return fail(FDF_EINVAL, "pass_blocks must be 0 (automatic) or 1..3");
+    if (p->gather_tile < -1 || p->gather_tile > 1) return fail(FDF_EINVAL, "gather_tile must be -1, 0 or 1");
     if (!(p->superstep_tol >= 0.0) || !std::isfinite(p->superstep_tol))
         return fail(FDF_EINVAL, "superstep_tol must be finite and >= 0");
     if (p->eom < FDF_EOM_GEODESIC || p->eom > FDF_EOM_EXACT) return fail(FDF_EINVAL, "unknown eom");
@@ -539,6 +540,7 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.wide_series = 1;
     for (int s = 0; s < kMaxSpecies; ++s) a.m2[s] = c->p.m_ev[s] * c->p.m_ev[s];
     a.grid_blocks = c->sm_count * (c->p.pass_blocks > 0 ? c->p.pass_blocks : 3);
+    a.tile_gather = c->p.gather_tile >= 0 ? 1 : 0;
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
     a.invL = 1.0 / c->p.box_mpc;

@@ -117,6 +117,7 @@ struct PushArgs {
     int order;                  // interpolation order r: 1 cloud-in-cell, 2 TSC
     int eom;                    // FDF_EOM_* (the plain FP64 form)
     int grid_blocks;            // the FP64-state form: blocks of its persistent pass grid
+    int tile_gather;            // the split-state form: kicks gather from shared-memory tiles
     int wide_series;            // the FP64-state form: every fitted polynomial of this pass passed
                                 // its check (else the integrals loop over the nodes)
     double m2[kMaxSpecies];     // m^2 per species (eV^2)

@@ -403,6 +403,126 @@ __device__ __forceinline__ SplitState load_split(const uint32_t* __restrict__ X,
     return s;
 }
 
+// ---- the gather from a shared-memory tile of the grid (split-state pass) ---------------
+// The particles are sorted by cell, so the 256 particles of a block sit in a few
+// neighbouring buckets.  Per kick, the block loads the grid cells of the box that holds
+// every particle's cell and its upper neighbours once into shared memory, and each
+// particle reads its eight corners there instead of from L2.  The box is taken about the
+// block's first particle (minimum image on the periodic grid); one larger than
+// kTileCells, or a call that is not of order 1, returns false and the caller reads G
+// directly.  Every thread of the block calls it (it synchronises the block); `live`
+// marks the threads with a particle.
+constexpr int kTileCells = 640;
+
+template <typename Gt> struct TileRec;
+template <> struct TileRec<float> { static constexpr int kWords = 2; };          // 32-byte records
+template <> struct TileRec<__nv_bfloat16> { static constexpr int kWords = 1; };  // 16-byte records
+
+struct TileShared {
+    uint4 rec[kTileCells * 2];
+    int ref[3];
+    int box[6];      // lo x, y, z, extent x, y, z (cells)
+    int red[kThreads / 32][6];
+};
+
+template <typename Gt>
+__device__ __forceinline__ void tile_unpack(const uint4* r, float v[8])
+{
+    if constexpr (TileRec<Gt>::kWords == 2) {
+        const uint32_t w[8] = {r[0].x, r[0].y, r[0].z, r[0].w, r[1].x, r[1].y, r[1].z, r[1].w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(w[k]);
+    } else {
+        const uint32_t w[4] = {r[0].x, r[0].y, r[0].z, r[0].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __uint_as_float(w[k] << 16);
+            v[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+    }
+}
+
+template <typename Gt>
+__device__ bool tile_gather(TileShared& sh, const Gt* __restrict__ G, uint32_t N, bool live, uint32_t X0, uint32_t X1,
+                            uint32_t X2, float g[8])
+{
+    constexpr int W = TileRec<Gt>::kWords;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t c[3] = {__umulhi(X0, N), __umulhi(X1, N), __umulhi(X2, N)};
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sh.ref[k] = (int)c[k];
+    }
+    __syncthreads();
+    const int half = (int)(N >> 1), mask = (int)N - 1;
+    int d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = live ? (((int)c[k] - sh.ref[k] + half) & mask) - half : 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int mn = __reduce_min_sync(0xffffffffu, d[k]);
+        const int mx = __reduce_max_sync(0xffffffffu, d[k]);
+        if (lane == 0) {
+            sh.red[warp][k] = mn;
+            sh.red[warp][3 + k] = mx;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int lo[3], hi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = sh.red[0][k];
+            hi[k] = sh.red[0][3 + k];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                lo[k] = min(lo[k], sh.red[w][k]);
+                hi[k] = max(hi[k], sh.red[w][3 + k]);
+            }
+            sh.box[k] = lo[k];
+            sh.box[3 + k] = hi[k] - lo[k] + 2;      // the cells and their upper neighbours
+        }
+    }
+    __syncthreads();
+    const int ex = sh.box[3], ey = sh.box[4], ez = sh.box[5];
+    const int vol = ex * ey * ez;
+    if (vol > kTileCells || ex > (int)N || ey > (int)N || ez > (int)N) return false;   // block-uniform
+    const int bx = sh.ref[0] + sh.box[0], by = sh.ref[1] + sh.box[1], bz = sh.ref[2] + sh.box[2];
+    for (int t = tid; t < vol; t += blockDim.x) {
+        const int ax = t % ex, ay = (t / ex) % ey, az = t / (ex * ey);
+        const uint32_t cell = ((uint32_t)((bz + az) & mask) * N + (uint32_t)((by + ay) & mask)) * N +
+                              (uint32_t)((bx + ax) & mask);
+        const uint4* src = reinterpret_cast<const uint4*>(G) + (size_t)cell * W;
+#pragma unroll
+        for (int w = 0; w < W; ++w) sh.rec[t * W + w] = __ldg(src + w);
+    }
+    __syncthreads();
+    if (live) {
+        uint32_t i0, i1;
+        float f[3];
+        int l[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t Xk = k == 0 ? X0 : (k == 1 ? X1 : X2);
+            fixed_cell(Xk, N, i0, i1, f[k]);
+            l[k] = d[k] - sh.box[k];
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s) g[s] = 0.f;
+#pragma unroll
+        for (int cn = 0; cn < 8; ++cn) {
+            const int cx = cn & 1, cy = (cn >> 1) & 1, cz = cn >> 2;
+            const float w = (cx ? f[0] : 1.f - f[0]) * (cy ? f[1] : 1.f - f[1]) * (cz ? f[2] : 1.f - f[2]);
+            const int t = ((l[2] + cz) * ey + (l[1] + cy)) * ex + (l[0] + cx);
+            float v[8];
+            tile_unpack<Gt>(sh.rec + t * W, v);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) g[s] = fmaf(w, v[s], g[s]);
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 // D (q0 + dq) in position quanta, as a normalised float-float: D q0 with an exact
 // product, D dq (|dq| << |q0|) folded into the low part.
 __device__ __forceinline__ FF scale_q(FF D, float q0, float dq)
@@ -419,11 +539,14 @@ __device__ __forceinline__ FF scale_q(FF D, float q0, float dq)
 // SERIES: the drift correction as a power series (else a loop over the drift
 // nodes); NK kick nodes are compile-time, so the loops unroll into constant-bank
 // operands; UNI: every species has the same mass.
-template <typename Gt, bool SERIES, int NK, bool UNI>
+// TILE: the kicks gather from a shared-memory tile of the grid (tile_gather), with G's
+// direct reads where a block's box is too large.
+template <typename Gt, bool SERIES, int NK, bool UNI, bool TILE>
 __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constant__ PushArgs a,
                                                             uint32_t* __restrict__ X, const float* __restrict__ q0f,
                                                             float* __restrict__ dqf)
 {
+    __shared__ typename std::conditional<TILE, TileShared, int>::type tile_sh;
     const int64_t n = a.n;
     const uint32_t N = (uint32_t)a.N;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -447,10 +570,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
         const float q02 = s2;
         bool moved = false, kicked = false;
         for (int u = 0; u < a.nsub; ++u) {
-            if (!live) continue;
+            if (!TILE && !live) continue;
             const SubStep& st = a.sub[u];
             const SpeciesCoef& c = st.sp[s];
-            if (st.do_drift) {
+            if (live && st.do_drift) {
                 // |q|^2 = |q0|^2 + (2 q0 + dq).dq; the second term is at most a few per
                 // cent of the first and carries FP32 rounding only.
                 const float small = fmaf(2.f * qa + da, da, fmaf(2.f * qb + db, db, (2.f * qc + dc) * dc));
@@ -493,7 +616,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
             }
             if (st.do_kick) {
                 float g[8];
-                gather_order<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, X0, X1, X2, g);
+                bool tiled = false;
+                if constexpr (TILE) tiled = tile_gather<Gt>(tile_sh, reinterpret_cast<const Gt*>(a.G[u]), N, live, X0,
+                                                           X1, X2, g);
+                if (!live) continue;
+                if (!tiled) gather_order<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, X0, X1, X2, g);
                 float Kpsi = 0.f, Kphi = 0.f;
 #pragma unroll
                 for (int j = 0; j < NK; ++j) {
@@ -524,14 +651,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_split(const __grid_constan
     }
 }
 
+template <typename Gt, bool SERIES, bool UNI, bool TILE>
+void push_split_tile(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
+{
+    switch (a.n_kick) {
+        case 2: k_push_split<Gt, SERIES, 2, UNI, TILE><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
+        case 3: k_push_split<Gt, SERIES, 3, UNI, TILE><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
+        default: k_push_split<Gt, SERIES, 4, UNI, TILE><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
+    }
+}
+
 template <typename Gt, bool SERIES, bool UNI>
 void push_split_nk(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
 {
-    switch (a.n_kick) {
-        case 2: k_push_split<Gt, SERIES, 2, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
-        case 3: k_push_split<Gt, SERIES, 3, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
-        default: k_push_split<Gt, SERIES, 4, UNI><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
-    }
+    // the tile serves the trilinear read (order 1)
+    if (a.tile_gather && a.order == 1) push_split_tile<Gt, SERIES, UNI, true>(s, b, a, st);
+    else push_split_tile<Gt, SERIES, UNI, false>(s, b, a, st);
 }
 
 template <typename Gt, bool UNI>

@@ -1,10 +1,11 @@
 // tune.cu -- fdf_tune: the autotuner of the schedule knobs.
 //
-// Four knobs change the speed of a run but not its results beyond the stated
+// Five knobs change the speed of a run but not its results beyond the stated
 // tolerances: how far particles may drift before they are re-bucketed
 // (sort_cells), the size of a bucket (sort_tile: cubes of 2^t cells per axis),
 // the number of leapfrog steps one particle pass covers (steps_per_pass) and, for
-// the FP64-state forms, the resident blocks per SM of the pass (pass_blocks).
+// the FP64-state forms, the resident blocks per SM of the pass (pass_blocks), for the
+// split-state forms, whether kicks read the grid from shared-memory tiles (gather_tile).
 // Their best values depend on the workload: on how fast the particles cross
 // cells (mass, momentum, box, step), on the grid size against L2 and on the
 // particle count.  The tuner times whole runs on the device and walks the knobs
@@ -67,6 +68,7 @@ extern "C" int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, 
     best.steps_per_pass = 4;
     const bool wide = form_of(p->precision) == kWide;
     best.pass_blocks = wide ? 3 : 0;
+    best.gather_tile = wide ? 0 : 1;
     double best_ms = 0;
     int n = 0;
     // one untimed run first (module load, first-touch of the allocation)
@@ -85,9 +87,11 @@ extern "C" int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, 
                                      {&fdf_params::sort_tile, {0, 1, 2}},
                                      {&fdf_params::steps_per_pass, {2, 3, 4}},
                                      {&fdf_params::pass_blocks, {2, 3}},
+                                     {&fdf_params::gather_tile, {1, -1}},
                                      {&fdf_params::sort_cells, {3, 5, 6, 12}}};
     for (const Knob& k : knobs) {
         if (k.field == &fdf_params::pass_blocks && !wide) continue;
+        if (k.field == &fdf_params::gather_tile && wide) continue;
         const int32_t start = best.*(k.field);
         for (int32_t v : k.values) {
             if (v == start) continue;

@@ -59,6 +59,7 @@ class fdf_params(C.Structure):
         ("superstep_tol", C.c_double),
         ("eom", C.c_int32),
         ("pass_blocks", C.c_int32),
+        ("gather_tile", C.c_int32),
     ]
 
 
@@ -209,13 +210,14 @@ def make_params(d):
     p.superstep_tol = float(d.get("superstep_tol", 0.0))
     p.eom = int(d.get("eom", 0))
     p.pass_blocks = int(d.get("pass_blocks", 0))
+    p.gather_tile = int(d.get("gather_tile", 0))
     return p
 
 
 def knobs(p):
     """The schedule knobs of an fdf_params as a dict (for reports)."""
     return {k: int(getattr(p, k)) for k in ("sort_every", "sort_cells", "sort_tile", "steps_per_pass", "pass_blocks",
-                                             "n_gl")}
+                                             "gather_tile", "n_gl")}
 
 
 def make_tables(d):

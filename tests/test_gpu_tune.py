@@ -52,7 +52,7 @@ def test_tuned_knobs_are_valid_and_change_no_result(F, inputs):
     assert k["pass_blocks"] in (2, 3)
     # every other field is the caller's
     for f, _ in F.fdf_params._fields_:
-        if f not in ("sort_every", "sort_cells", "sort_tile", "steps_per_pass", "pass_blocks"):
+        if f not in ("sort_every", "sort_cells", "sort_tile", "steps_per_pass", "pass_blocks", "gather_tile"):
             a, b = getattr(P, f), getattr(tuned, f)
             assert (list(a) == list(b)) if f == "m_ev" else a == b, f
     ref = _run(F, P, T, p["n_part"], 2)
