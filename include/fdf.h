@@ -172,7 +172,8 @@ typedef struct fdf_params {
     int32_t  gather_tile;      /* the split-state forms: 1 = each block's kicks read the grid from a
                                   shared-memory tile of the cells its particles occupy (loaded once
                                   per kick; order-1 reads only), -1 = every read from the grid in
-                                  device memory, 0 = automatic (1).  Ignored by the other forms. */
+                                  device memory, 0 = automatic (-1: the tile measured slower on
+                                  the 3 x 256^3 workload).  Ignored by the other forms. */
 } fdf_params;
 
 /* ---- equations of motion (fdf_params.eom) -------------------------------- */
@@ -378,7 +379,7 @@ FDF_API void fdf_destroy(fdf_ctx* c);
  * pass_blocks.  It times whole runs (fdf_sample + fdf_step(n_steps)) of p on the
  * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16},
  * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4}, pass_blocks in {2, 3} (FP64-state
- * forms) or gather_tile in {1, -1} (split-state forms), then sort_cells again in
+ * forms) or gather_tile in {-1, 1} (split-state forms), then sort_cells again in
  * {3, 5, 6, 12}), starting from the automatic choices, and writes
  * the fastest parameter set to *out (p with the knobs set).  The paper
  * has no counterpart.  stream: a cudaStream_t or NULL; every trial allocates

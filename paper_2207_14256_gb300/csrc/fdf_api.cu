@@ -540,7 +540,7 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.wide_series = 1;
     for (int s = 0; s < kMaxSpecies; ++s) a.m2[s] = c->p.m_ev[s] * c->p.m_ev[s];
     a.grid_blocks = c->sm_count * (c->p.pass_blocks > 0 ? c->p.pass_blocks : 3);
-    a.tile_gather = c->p.gather_tile >= 0 ? 1 : 0;
+    a.tile_gather = c->p.gather_tile > 0 ? 1 : 0;
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
     a.invL = 1.0 / c->p.box_mpc;

@@ -68,7 +68,7 @@ extern "C" int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, 
     best.steps_per_pass = 4;
     const bool wide = form_of(p->precision) == kWide;
     best.pass_blocks = wide ? 3 : 0;
-    best.gather_tile = wide ? 0 : 1;
+    best.gather_tile = wide ? 0 : -1;
     double best_ms = 0;
     int n = 0;
     // one untimed run first (module load, first-touch of the allocation)
@@ -87,7 +87,7 @@ extern "C" int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, 
                                      {&fdf_params::sort_tile, {0, 1, 2}},
                                      {&fdf_params::steps_per_pass, {2, 3, 4}},
                                      {&fdf_params::pass_blocks, {2, 3}},
-                                     {&fdf_params::gather_tile, {1, -1}},
+                                     {&fdf_params::gather_tile, {-1, 1}},
                                      {&fdf_params::sort_cells, {3, 5, 6, 12}}};
     for (const Knob& k : knobs) {
         if (k.field == &fdf_params::pass_blocks && !wide) continue;
