@@ -581,6 +581,7 @@ void fill_wide(fdf_ctx* c, bool drift, double d1, double d2, const double* Wd, c
             const double mac = c->p.m_ev[s] * std::exp(0.5 * (d1 + d2));      // m a_c
             w.wsum[s] = sum;
             w.inv_muc[s] = mac > 0 ? 1.0 / (mac * mac) : 0.0;
+            w.massless[s] = mac > 0 ? 0 : 1;
             // the species' copy of the polynomial carries the factor 1/(m a_c)
             const double f = mac > 0 ? 1.0 / mac : 0.0;
             for (int k = 0; k < kWideD64; ++k) w.drift[s].c64[k] = P.c64[k] * f;

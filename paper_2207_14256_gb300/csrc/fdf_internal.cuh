@@ -83,6 +83,7 @@ struct WideCoef {
     // factor 1/(m a_c) folded into the species' copy of the polynomial.  A massless
     // species (inv_muc = 0) takes D = |q|^-1 sum_j W_j.
     double inv_muc[kMaxSpecies];    // 1 / (m^2 a_c^2) of the drift interval, or 0 for m = 0
+    int massless[kMaxSpecies];      // m = 0 (tested as an integer: an FP64 comparison costs an FP64 slot)
     double wsum[kMaxSpecies];       // sum_j W_j (the massless drift)
     WidePoly drift[kMaxSpecies];    // gm of the drift interval / (m a_c), per species
     double muk[kMaxSpecies];    // m^2 a_c^2 of the kick interval, per species

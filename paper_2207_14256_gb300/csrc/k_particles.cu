@@ -720,8 +720,8 @@ template <bool SERIES>
 __device__ __forceinline__ double drift_integral(const SubStep& st, int s, int n_gl, const double q[3])
 {
     if constexpr (SERIES) {
-        const double inv = st.wide.inv_muc[s];
-        if (inv > 0.0) {
+        if (!st.wide.massless[s]) {
+            const double inv = st.wide.inv_muc[s];
             // v = 1 + |q|^2 / (m^2 a_c^2), t = 1/v, D = v^(-1/2) gm(t) / (m a_c)
             const double v = fma(fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2])), inv, 1.0);
             const double rv = rsqrt_fp64(v);
