@@ -54,14 +54,15 @@ WIDE_FP64_PER_PASS = 3
 # FP64-pipe instructions per particle-step of the plain FP64 pass (k_push_f64), from ncu
 # (sm__inst_executed_pipe_fp64.sum x 32 / particle-steps of the launch, 128^3 particles, one step
 # per pass; profiles/), for its FP64-pipe roofline.  Dropped if the sources changed.
-PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3,
-              "sources_sha256": "PLACEHOLDER"}
+PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "523d64612ff505c7:fab49efda94cccf0:5d3cf58f191c3ce4"}
 
 # DRAM bytes per particle pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the passes of a run; profiles/), per particle of the launch, by precision setting.  Valid
-# only for the kernel sources they were measured on: their hash is checked and the figure
-# dropped if they changed.
-PUSH_TRAFFIC = {3: {"bytes_per_particle": 3.832e9 / 256 ** 3, "sources_sha256": "592657e412cf2c27:d27dd9ad17a7f14f:bac8a9f67003931c"}}
+# over the 50 passes of a one-species 256^3 run of the bench's schedule; profiles/), per particle
+# of the launch, by precision setting: the species are sorted one after the other, so a
+# three-species launch moves three times as much.  Valid only for the kernel sources they were
+# measured on: their hash is checked and the figure dropped if they changed.
+PUSH_TRAFFIC = {1: {"bytes_per_particle": (4.369e9 + 0.787e9) / 256 ** 3, "sources_sha256": "523d64612ff505c7:fab49efda94cccf0:5d3cf58f191c3ce4"},
+                3: {"bytes_per_particle": (3.431e9 + 0.401e9) / 256 ** 3, "sources_sha256": "523d64612ff505c7:fab49efda94cccf0:5d3cf58f191c3ce4"}}
 PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
 
 
