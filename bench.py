@@ -54,23 +54,32 @@ WIDE_FP64_PER_PASS = 3
 # FP64-pipe instructions per particle-step of the plain FP64 pass (k_push_f64), from ncu
 # (sm__inst_executed_pipe_fp64.sum x 32 / particle-steps of the launch, 128^3 particles, one step
 # per pass; profiles/), for its FP64-pipe roofline.  Dropped if the sources changed.
-PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "523d64612ff505c7:fab49efda94cccf0:5d3cf58f191c3ce4"}
+PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"}
 
 # DRAM bytes per particle pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # over the 50 passes of a one-species 256^3 run of the bench's schedule; profiles/), per particle
 # of the launch, by precision setting: the species are sorted one after the other, so a
 # three-species launch moves three times as much.  Valid only for the kernel sources they were
 # measured on: their hash is checked and the figure dropped if they changed.
-PUSH_TRAFFIC = {1: {"bytes_per_particle": (4.369e9 + 0.787e9) / 256 ** 3, "sources_sha256": "523d64612ff505c7:fab49efda94cccf0:5d3cf58f191c3ce4"},
-                3: {"bytes_per_particle": (3.431e9 + 0.401e9) / 256 ** 3, "sources_sha256": "523d64612ff505c7:fab49efda94cccf0:5d3cf58f191c3ce4"}}
+PUSH_TRAFFIC = {1: {"bytes_per_particle": (4.369e9 + 0.787e9) / 256 ** 3, "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"},
+                3: {"bytes_per_particle": (3.431e9 + 0.401e9) / 256 ** 3, "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"}}
 PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
 
 
 def push_sources_hash():
+    """Hash of the pass kernels' sources with comments and blank space removed, so that only a
+    change of the code itself drops the ncu figures measured on it."""
     import hashlib
+    import re
 
     d = os.path.join(ROOT, "paper_2207_14256_gb300", "csrc")
-    return ":".join(hashlib.sha256(open(os.path.join(d, f), "rb").read()).hexdigest()[:16] for f in PUSH_SOURCES)
+    parts = []
+    for f in PUSH_SOURCES:
+        src = open(os.path.join(d, f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        parts.append(hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16])
+    return ":".join(parts)
 
 
 def describe(p):

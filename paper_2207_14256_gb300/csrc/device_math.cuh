@@ -178,7 +178,7 @@ __device__ __forceinline__ double dfweight(double qm, double p, double T)
     return -expm1((p - qm) / T) / (1.0 + exp(-qm / T));
 }
 
-// The same weight as the split forms compute it: the small difference p - |q| in
+// The same weight as the FP32/BF16-grid forms compute it: the small difference p - |q| in
 // FP64 (|q| from norm3_rn), the rest in FP32 (their momenta carry FP32 rounding
 // already, and GB300's FP64 transcendental functions are slow).
 __device__ __forceinline__ float dfweight_split(double qm, double p, double T)

@@ -188,7 +188,7 @@ struct StateLayout {
     size_t X, q0f, dqf, xd, qd, q0d, sd, pmag, id;
 };
 
-// Steps per particle pass: the caller's choice, else 4 for the split forms (the
+// Steps per particle pass: the caller's choice, else 4 for the FP32/BF16-grid forms (the
 // particle state is read and written once per 4 steps) and 1 for the plain form.
 int steps_per_pass(const fdf_params& p)
 {
@@ -876,7 +876,7 @@ int sort_particles(fdf_ctx* c, int dir, bool pre_transform = false)
 {
     SortLead lead{};
     if (pre_transform) {
-        // split forms right after sampling: by position alone, carrying the sampled momenta
+        // the FP32/BF16-grid forms right after sampling: by position alone, carrying the sampled momenta
         lead.pre_transform = 1;
     } else if (form_of(c->p.precision) != kPlain) {
         const double l1 = c->lna(c->k), l2 = c->lna(c->k + 0.5 * c->spp * dir);
@@ -1160,7 +1160,7 @@ int sample_enqueue(fdf_ctx* c)
     c->ssk[0] = c->ssk[1] = -1;
     rc = draw_noise(c);
     if (rc) return rc;
-    // The split forms sort right after sampling, so that the transform's gather of the
+    // The FP32/BF16-grid forms sort right after sampling, so that the transform's gather of the
     // step-0 grid runs over spatially ordered particles (at z_start a particle crosses a
     // negligible part of a cell in the first pass, so no lead is lost).  The plain form
     // keeps its sampled positions in id order and sorts after the transform.

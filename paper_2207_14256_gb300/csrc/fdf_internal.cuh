@@ -205,7 +205,7 @@ cudaError_t launch_fields_from_f64(cudaStream_t s, int precision, int N, const d
 
 // Particle passes.
 struct ParticleState {
-    uint32_t* X;        // [3][n] fixed-point positions (split forms; sampler output in all forms)
+    uint32_t* X;        // [3][n] fixed-point positions (split-state form; sampler output in all forms)
     float* q0f;         // [3][n] (split-state and FP64-state forms)
     float* dqf;         // [3][n] (split-state form)
     double* xd;         // [3][n] (plain and FP64-state forms)
@@ -213,7 +213,7 @@ struct ParticleState {
     double* q0d;        // [3][n] (plain form)
     double* sd;         // [n] phi + psi from the last kick (the exact equations of motion), or NULL
     double* qs;         // [3][n] sampled momenta (one array for both halves: id order in the plain form;
-                        // the split forms carry it through their sort before the transform only)
+                        // the FP32/BF16-grid forms carry it through their sort before the transform only)
     double* pmag;       // [n]
     uint32_t* id;       // [n]
 };
@@ -243,14 +243,14 @@ cudaError_t launch_push_multi(cudaStream_t s, int grid_precision, const MultiPas
 // the particle's tile of 2^tile_shift cells per axis, tile_shift = sort_tile).  key: n words; hist:
 // n_species * tiles words; bsum: scan_scratch_words(bins) words; recs: n records
 // of sort_record_bytes(precision).
-// The split form buckets particles by where they will be halfway through the
+// The FP32/BF16-grid forms bucket particles by where they will be halfway through the
 // next pass: X + q dtau / sqrt(q^2 + m^2 a^2) (a free-streaming estimate), so that
 // neighbours in memory stay neighbours in space for longer.
 struct SortLead {
     int on;
     float dtau_q32[kMaxSpecies];  // conformal time of the lead, times 2^32 / L
     float m2a2[kMaxSpecies];      // m^2 a^2 at the middle of the lead
-    // split forms, before the momentum transform: q0/dq do not exist yet; the keys
+    // FP32/BF16-grid forms, before the momentum transform: the momenta do not exist yet; the keys
     // use the positions alone and the sampled momenta qs travel with the particles
     int pre_transform;
 };

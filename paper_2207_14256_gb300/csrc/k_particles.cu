@@ -8,11 +8,13 @@
 //            (Sec. 2.2) in particle-index order;
 //   deposit: the weighted CIC density estimate (eq:empirical_rho).
 //
-// Two state forms.  The plain form keeps x, q, q_0 in FP64 and reads an FP64
-// grid.  The split form keeps positions as 32-bit fixed-point fractions of the
-// box (the periodic wrap is the integer overflow), momenta as q = q_0 + dq
-// with both parts in FP32, and evaluates the drift integral in float-float so
-// that no FP64 instruction runs in the per-step pass.
+// Three state forms.  The plain form keeps x, q, q_0 in FP64 and reads an FP64
+// grid.  The FP64-state form (the FP32/BF16-grid precision settings) keeps x and q
+// in FP64 and q_0 in FP32, reads an FP32 or BF16 grid, and spends as few FP64
+// instructions as FP64 integrals allow (k_push_wide).  The split-state form keeps
+// positions as 32-bit fixed-point fractions of the box (the periodic wrap is the
+// integer overflow), momenta as q = q_0 + dq with both parts in FP32, and evaluates
+// the drift integral in float-float so that no FP64 instruction runs in its pass.
 #include <cuda_bf16.h>
 
 #include <type_traits>
@@ -982,7 +984,7 @@ __global__ void __launch_bounds__(kThreads) k_export(ParticleState st, int64_t n
     }
 }
 
-// The pre-initial draw in particle-index order.  The split form's fixed-point
+// The pre-initial draw in particle-index order.  The FP32/BF16-grid forms' fixed-point
 // positions and sampled momenta are the live state and follow the permutation (it
 // sorts before the momentum transform); the plain form keeps them in id order.
 // |q_sampled| follows the permutation in both forms.
