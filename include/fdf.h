@@ -377,7 +377,7 @@ FDF_API void fdf_destroy(fdf_ctx* c);
 /* Autotuner of the schedule knobs that change speed only (no result beyond the
  * stated tolerances): sort_cells, sort_tile, steps_per_pass and (FP64-state forms)
  * pass_blocks.  It times whole runs (fdf_sample + fdf_step(n_steps)) of p on the
- * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16},
+ * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16, 32},
  * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4}, pass_blocks in {2, 3} (FP64-state
  * forms) or gather_tile in {-1, 1} (split-state forms), then sort_cells again in
  * {3, 5, 6, 12}), starting from the automatic choices, and writes

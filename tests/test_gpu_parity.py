@@ -324,3 +324,30 @@ def test_full_size_workloads_few_steps(F, inputs, name):
             assert ex < BF16_TOL_X and eq < BF16_TOL_Q and ew < BF16_TOL_W, (ex, eq, ew)
         else:
             assert ex < TOL_X and eq < TOL_Q and ew < TOL_W, (ex, eq, ew)
+
+
+# ---- inspection hooks --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,n_steps,series", [(1, 200, 1), (1, 100, 0), (3, 100, 1), (0, 40, 0)])
+def test_pass_info_reports_the_pass_kernel(F, inputs, c1_tables, prec, n_steps, series):
+    """fdf_pass_info names the state form and whether every pass evaluated its step integrals
+    as fitted polynomials or series: at 200 steps over the run the FP64-state form fits them
+    (the throughput workloads' step size), at 100 it sums the nodes; the split-state form's
+    drift series holds at 100 steps; the plain form always sums the nodes."""
+    p = inputs.config("c1_32", n_part=2000, n_grid=16, n_steps=n_steps, precision=prec)
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        r.step(n_steps)
+        info = F.fdf_pass_info(r.ctx)
+    print(prec, n_steps, info)
+    assert info["form"] == {0: 0, 1: 1, 3: 2}[prec]
+    assert info["series"] == series
+    spp = 1 if prec == 0 else 4
+    assert info["steps_per_pass"] == spp and info["passes"] == -(-n_steps // spp)
+
+
+def test_pipe_rates_are_plausible(F):
+    """The issue-rate probes behind the FP64 roofline: positive, and FP64 far below FP32."""
+    d, f, c = F.fdf_pipe_rates()
+    print("DFMA/s %.3e  FFMA/s %.3e  conversion round trips/s %.3e" % (d, f, c))
+    assert d > 0 and f > 0 and c > 0
+    assert f > 8 * d
