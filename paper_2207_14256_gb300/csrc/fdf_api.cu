@@ -1195,7 +1195,9 @@ int sample_enqueue(fdf_ctx* c)
         c->ssk[0] = c->ssk[1] = -1;
     } else {
         // the steps' passes read no slot 7: phi_dot is transformed alone from here on (the
-        // grid of step 0, built with psi, serves the opening half kick as it is)
+        // grid of step 0, built with psi, serves the opening half kick as it is, and so does
+        // the super-step grid of step 0 for the steps interpolated from it: at z = 1e9 the
+        // potentials are constant and phi_dot's kick term vanishes with the conformal time)
         c->slot7 = kSlot7Zero;
     }
     c->k = 0;
