@@ -56,13 +56,16 @@ WIDE_FP64_PER_PASS = 3
 # per pass; profiles/), for its FP64-pipe roofline.  Dropped if the sources changed.
 PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"}
 
-# DRAM bytes per particle pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over the 50 passes of a one-species 256^3 run of the bench's schedule; profiles/), per particle
-# of the launch, by precision setting: the species are sorted one after the other, so a
-# three-species launch moves three times as much.  Valid only for the kernel sources they were
-# measured on: their hash is checked and the figure dropped if they changed.
-PUSH_TRAFFIC = {1: {"bytes_per_particle": (4.369e9 + 0.787e9) / 256 ** 3, "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"},
-                3: {"bytes_per_particle": (3.431e9 + 0.401e9) / 256 ** 3, "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"}}
+# DRAM bytes per particle-step of the pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean over the 50 passes of 4 steps of a one-species 256^3 run of the bench's schedule;
+# profiles/), by precision setting.  A launch's traffic is this times the particle-steps it
+# processes (the species are sorted one after the other, so each reads the grid on its own).
+# Valid only for the kernel sources they were measured on: their hash is checked and the figure
+# dropped if they changed.
+PUSH_TRAFFIC = {1: {"bytes_per_particle_step": (4.369e9 + 0.787e9) / (256 ** 3 * 4),
+                    "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"},
+                3: {"bytes_per_particle_step": (3.431e9 + 0.401e9) / (256 ** 3 * 4),
+                    "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"}}
 PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
 
 
@@ -231,10 +234,11 @@ def hbm_roofline(p, ktimes, hbm):
     tr = PUSH_TRAFFIC.get(prec)
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if hbm else None,
-            "traffic": (tr["bytes_per_particle"] * n_total if tr and push_sources_hash() == tr["sources_sha256"]
-                        else None),
-            "traffic_note": "ncu DRAM bytes per pass (profiles/), per particle of the launch, scaled to the "
-                            "launch; null when the kernel sources changed since the capture",
+            "traffic": (tr["bytes_per_particle_step"] * n_total * p["n_steps"] / max(push_n, 1)
+                        if tr and push_sources_hash() == tr["sources_sha256"] else None),
+            "traffic_note": "ncu DRAM bytes per particle-step of the pass (one-species 256^3 run, passes of 4 steps; "
+                            "profiles/) times the launch's particle-steps; null when the kernel sources changed "
+                            "since the capture",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800",
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": push_avg,
             "steps_per_launch": p["n_steps"] / max(push_n, 1),
