@@ -607,6 +607,8 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the reduced-precision workload")
     ap.add_argument("--schedule", default="", help='schedule knobs as JSON, e.g. {"sort_tile": 1} (no tuning)')
     ap.add_argument("--served-requests", type=int, default=64)
+    ap.add_argument("--served-merged", action="store_true",
+                    help="also run the served stream with merged pass launches across requests")
     ap.add_argument("--precision", type=int, default=-1,
                     help="override the workload's precision setting (FDF_PREC_*: 0 FP64, 1/2 FP32/BF16 grids with "
                          "the FP64 state, 3/4 the split state)")
@@ -715,7 +717,8 @@ def main():
                          note="the reduced-precision workload, timed as the headline (graph replays + deposit)")
     if not args.no_served and world == 1:
         out["served"] = bench_served(args.served_requests)
-        out["served_merged"] = bench_served(args.served_requests, merge=True)
+        if args.served_merged:
+            out["served_merged"] = bench_served(args.served_requests, merge=True)
     if not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(out))
