@@ -313,6 +313,8 @@ int fdf::validate_params(const fdf_params* p)
     if (p->interp_order < 0 || p->interp_order > 2) return fail(FDF_EINVAL, "interp_order must be 0, 1 or 2");
     if (p->pass_blocks < 0 || p->pass_blocks > 3) return fail(FDF_EINVAL, "pass_blocks must be 0 (automatic) or 1..3");
     if (p->gather_tile < -1 || p->gather_tile > 1) return fail(FDF_EINVAL, "gather_tile must be -1, 0 or 1");
+    if (p->deposit_presum < -1 || p->deposit_presum > 1)
+        return fail(FDF_EINVAL, "deposit_presum must be -1, 0 or 1");
     if (!(p->superstep_tol >= 0.0) || !std::isfinite(p->superstep_tol))
         return fail(FDF_EINVAL, "superstep_tol must be finite and >= 0");
     if (p->eom < FDF_EOM_GEODESIC || p->eom > FDF_EOM_EXACT) return fail(FDF_EINVAL, "unknown eom");
@@ -540,6 +542,10 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.wide_series = 1;
     for (int s = 0; s < kMaxSpecies; ++s) a.m2[s] = c->p.m_ev[s] * c->p.m_ev[s];
     a.grid_blocks = c->sm_count * (c->p.pass_blocks > 0 ? c->p.pass_blocks : 3);
+    // With fewer than three pass blocks per SM a build block fits beside them (registers);
+    // the carveout keeps 100 KB of each SM's shared memory configured for it (the pass
+    // itself uses none), so that the SM need not drain before a build block can start.
+    a.carveout = c->p.pass_blocks > 0 && c->p.pass_blocks < 3 ? 44 : -1;
     a.tile_gather = c->p.gather_tile > 0 ? 1 : 0;
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
@@ -1585,7 +1591,7 @@ int deposit_enqueue(fdf_ctx* c, int32_t species, int32_t quantity, int32_t parit
     return timed(c, FDF_K_OTHER, "deposit", [&] {
         return launch_deposit(c->stream, c->p.precision, c->st, c->n, begin, count, np > 0 ? np : 1, c->p.m_ev, a,
                               c->T_ev, quantity, parity, c->p.interp_order == 2 ? 2 : 1, c->p.n_grid,
-                              c->p.box_mpc, out_dev);
+                              c->p.box_mpc, c->p.deposit_presum > 0, out_dev);
     });
 }
 

@@ -118,6 +118,8 @@ struct PushArgs {
     int order;                  // interpolation order r: 1 cloud-in-cell, 2 TSC
     int eom;                    // FDF_EOM_* (the plain FP64 form)
     int grid_blocks;            // the FP64-state form: blocks of its persistent pass grid
+    int carveout;               // the FP64-state form: the pass kernel's preferred shared-memory
+                                // carveout in percent, -1 = the driver's choice
     int tile_gather;            // the split-state form: kicks gather from shared-memory tiles
     int wide_series;            // the FP64-state form: every fitted polynomial of this pass passed
                                 // its check (else the integrals loop over the nodes)
@@ -279,7 +281,7 @@ cudaError_t launch_accel_terms(cudaStream_t s, int precision, const ParticleStat
 // two halves of the ensemble); order: the kernel order r (1 or 2).
 cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                            int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
-                           int parity, int order, int N, double L, double* grid);
+                           int parity, int order, int N, double L, bool presum, double* grid);
 
 // Asynchronous forms of two entry points, for the request server: the work is
 // enqueued on the context's streams and nothing waits for it.

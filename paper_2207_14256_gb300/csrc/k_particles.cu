@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "device_math.cuh"
 
@@ -34,6 +35,48 @@ unsigned grid_for(int64_t n, int per_sm = 16)
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (unsigned)b;
+}
+
+// The particle passes launch at the device's greatest execution priority
+// (cudaLaunchAttributePriority).  The grids of the next pass are built on another
+// stream at the default priority; when both wait for room on the SMs, the block
+// scheduler places the pass's blocks first and the builds run in the room the pass
+// leaves (pass_blocks < 3 leaves room for one build block per SM).
+int pass_priority()
+{
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+    return greatest;
+}
+
+// A launch error is left for the caller's cudaGetLastError.  Unless carveout is kKeepCarveout
+// the kernel's preferred shared-memory carveout (percent of the largest, -1 = the driver's
+// default) is set first.
+constexpr int kKeepCarveout = -2;
+
+template <typename... K, typename... A>
+void launch_pass_carveout(int carveout, void (*kernel)(K...), unsigned blocks, cudaStream_t s, A&&... args)
+{
+    if (carveout != kKeepCarveout &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout) != cudaSuccess)
+        return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = pass_priority();
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+template <typename... K, typename... A>
+void launch_pass(void (*kernel)(K...), unsigned blocks, cudaStream_t s, A&&... args)
+{
+    launch_pass_carveout(kKeepCarveout, kernel, blocks, s, std::forward<A>(args)...);
 }
 
 // ---- grid reads ------------------------------------------------------------
@@ -657,9 +700,9 @@ template <typename Gt, bool SERIES, bool UNI, bool TILE>
 void push_split_tile(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
 {
     switch (a.n_kick) {
-        case 2: k_push_split<Gt, SERIES, 2, UNI, TILE><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
-        case 3: k_push_split<Gt, SERIES, 3, UNI, TILE><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
-        default: k_push_split<Gt, SERIES, 4, UNI, TILE><<<b, kThreads, 0, s>>>(a, st.X, st.q0f, st.dqf); break;
+        case 2: launch_pass(k_push_split<Gt, SERIES, 2, UNI, TILE>, b, s, a, st.X, st.q0f, st.dqf); break;
+        case 3: launch_pass(k_push_split<Gt, SERIES, 3, UNI, TILE>, b, s, a, st.X, st.q0f, st.dqf); break;
+        default: launch_pass(k_push_split<Gt, SERIES, 4, UNI, TILE>, b, s, a, st.X, st.q0f, st.dqf); break;
     }
 }
 
@@ -859,12 +902,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_push_wide_multi(const __grid_co
 template <typename Gt>
 void push_wide(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
 {
+    const int cv = a.carveout;
     if (a.wide_series) {
-        if (a.uniform_species) k_push_wide<Gt, true, true><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
-        else k_push_wide<Gt, true, false><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
+        if (a.uniform_species) launch_pass_carveout(cv, k_push_wide<Gt, true, true>, b, s, a, st.xd, st.qd, st.q0f);
+        else launch_pass_carveout(cv, k_push_wide<Gt, true, false>, b, s, a, st.xd, st.qd, st.q0f);
     } else {
-        if (a.uniform_species) k_push_wide<Gt, false, true><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
-        else k_push_wide<Gt, false, false><<<b, kThreads, 0, s>>>(a, st.xd, st.qd, st.q0f);
+        if (a.uniform_species) launch_pass_carveout(cv, k_push_wide<Gt, false, true>, b, s, a, st.xd, st.qd, st.q0f);
+        else launch_pass_carveout(cv, k_push_wide<Gt, false, false>, b, s, a, st.xd, st.qd, st.q0f);
     }
 }
 
@@ -1069,17 +1113,48 @@ __global__ void __launch_bounds__(kThreads) k_accel_terms(ParticleState st, int6
     }
 }
 
-template <int F>
+// The deposit's warp pre-sum: the lanes of `peers` (the lanes whose particles share a
+// base cell, from __match_any_sync) add their values v[0..K) so that the lowest lane of
+// the set holds the set's sums.  A pairwise tree over the set in lane order: at each
+// level a lane at an even position within the remaining set adds the values of the next
+// remaining lane above it, and the lanes at odd positions drop out; log2 of the set's
+// size levels, every lane of the warp taking part in each (the ballot-and-shuffle
+// segmented reduction of warp-aggregated atomics).
+template <int K, typename T>
+__device__ __forceinline__ void peer_sum(T (&v)[K], unsigned peers)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned above = peers & (0xfffffffeu << lane);   // the set's lanes above this one
+    unsigned pos = __popc(peers & ((1u << lane) - 1u));   // this lane's position in the set
+    while (__any_sync(0xffffffffu, above != 0u)) {
+        const int src = above ? __ffs(above) - 1 : (int)lane;
+        const bool take = above != 0u && !(pos & 1u);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T t = __shfl_sync(0xffffffffu, v[k], src);
+            if (take) v[k] += t;
+        }
+        above &= ~__ballot_sync(0xffffffffu, pos & 1u);
+        pos >>= 1;
+    }
+}
+
+template <int F, bool PRESUM>
 __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t n, int64_t begin, int64_t count,
                                                       int64_t n_part, Masses ms, double a, double T, int quantity,
                                                       int parity, int order, int N, double L,
                                                       double* __restrict__ grid)
 {
     const double invh = (double)N / L;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = begin + j;
-        if (parity >= 0 && (int)(st.id[i] & 1u) != parity) continue;
+    // Warp-uniform trips: the lanes of a warp take 32 consecutive particles (neighbours in
+    // the bucket order of the last sort) and stay converged for the pre-sum.
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); j0 < count; j0 += stride) {
+        const int64_t j = j0 + (threadIdx.x & 31u);
+        bool live = j < count;
+        const int64_t i = begin + (live ? j : 0);
+        if (live && parity >= 0 && (int)(st.id[i] & 1u) != parity) live = false;
+        if (!PRESUM && !live) continue;
         const double m = ms.m[i / n_part];
         double x[3], q[3];
         load_state<F>(st, n, i, L, x, q);
@@ -1140,14 +1215,43 @@ __global__ void __launch_bounds__(kThreads) k_deposit(ParticleState st, int64_t 
             }
         }
         const Wt vw = (Wt)v;
-        const int m3 = order == 2 ? 3 : 2;
-        for (int cz = 0; cz < m3; ++cz)
-            for (int cy = 0; cy < m3; ++cy)
-                for (int cx = 0; cx < m3; ++cx) {
-                    const Wt wt = w[0][cx] * w[1][cy] * w[2][cz];
-                    const size_t cell = ((size_t)idx[2][cz] * N + idx[1][cy]) * N + idx[0][cx];
-                    atomicAdd(grid + cell, (double)(wt * vw));
+        if constexpr (PRESUM) {
+            // Particles sharing the base cell share every node: one match on it, sums
+            // over the set by shuffles, and one atomic per set and node.
+            const unsigned key = live ? (unsigned)(((size_t)idx[2][0] * N + idx[1][0]) * N + idx[0][0]) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const bool lead = live && (peers & ((1u << (threadIdx.x & 31u)) - 1u)) == 0u;
+            if (order == 2) {
+                double c[27];
+#pragma unroll
+                for (int k = 0; k < 27; ++k) c[k] = live ? (double)(w[0][k % 3] * w[1][(k / 3) % 3] * w[2][k / 9] * vw) : 0.0;
+                peer_sum<27>(c, peers);
+                if (lead) {
+#pragma unroll
+                    for (int k = 0; k < 27; ++k)
+                        atomicAdd(grid + ((size_t)idx[2][k / 9] * N + idx[1][(k / 3) % 3]) * N + idx[0][k % 3], c[k]);
                 }
+            } else {
+                double c[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) c[k] = live ? (double)(w[0][k & 1] * w[1][(k >> 1) & 1] * w[2][k >> 2] * vw) : 0.0;
+                peer_sum<8>(c, peers);
+                if (lead) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        atomicAdd(grid + ((size_t)idx[2][k >> 2] * N + idx[1][(k >> 1) & 1]) * N + idx[0][k & 1], c[k]);
+                }
+            }
+        } else {
+            const int m3 = order == 2 ? 3 : 2;
+            for (int cz = 0; cz < m3; ++cz)
+                for (int cy = 0; cy < m3; ++cy)
+                    for (int cx = 0; cx < m3; ++cx) {
+                        const Wt wt = w[0][cx] * w[1][cy] * w[2][cz];
+                        const size_t cell = ((size_t)idx[2][cz] * N + idx[1][cy]) * N + idx[0][cx];
+                        atomicAdd(grid + cell, (double)(wt * vw));
+                    }
+        }
     }
 }
 
@@ -1183,7 +1287,7 @@ cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, 
     if (a.n <= 0) return cudaSuccess;
     const int f = form_of(precision), gp = grid_prec(precision);
     if (f == kPlain) {
-        k_push_f64<<<grid_for(a.n), kThreads, 0, s>>>(a, st.xd, st.qd, st.q0d, st.sd);
+        launch_pass(k_push_f64, grid_for(a.n), s, a, st.xd, st.qd, st.q0d, st.sd);
     } else if (f == kWide) {
         // a persistent grid of pass_blocks (<= 3 resident) blocks per SM, each walking the
         // particles with a grid stride
@@ -1211,8 +1315,8 @@ cudaError_t launch_push_multi(cudaStream_t s, int grid_precision, const MultiPas
     int64_t nb = (m.total + kThreads - 1) / kThreads;
     if (nb > grid_blocks) nb = grid_blocks;
     const unsigned b = (unsigned)(nb < 1 ? 1 : nb);
-    if (grid_precision == FDF_PREC_F32) k_push_wide_multi<float><<<b, kThreads, 0, s>>>(m);
-    else k_push_wide_multi<__nv_bfloat16><<<b, kThreads, 0, s>>>(m);
+    if (grid_precision == FDF_PREC_F32) launch_pass(k_push_wide_multi<float>, b, s, m);
+    else launch_pass(k_push_wide_multi<__nv_bfloat16>, b, s, m);
     return cudaGetLastError();
 }
 
@@ -1262,17 +1366,21 @@ cudaError_t launch_accel_terms(cudaStream_t s, int precision, const ParticleStat
 
 cudaError_t launch_deposit(cudaStream_t s, int precision, const ParticleState& st, int64_t n, int64_t begin,
                            int64_t count, int64_t n_part, const double* m_ev, double a, double T_ev, int quantity,
-                           int parity, int order, int N, double L, double* grid)
+                           int parity, int order, int N, double L, bool presum, double* grid)
 {
     if (count <= 0) return cudaSuccess;
     const unsigned b = grid_for(count);
     const Masses ms = masses_of(m_ev);
     const int f = form_of(precision);
-#define FDF_DEPOSIT(F_) \
-    k_deposit<F_><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, parity, order, N, L, grid)
-    if (f == kPlain) FDF_DEPOSIT(kPlain);
-    else if (f == kWide) FDF_DEPOSIT(kWide);
-    else FDF_DEPOSIT(kFixed);
+#define FDF_DEPOSIT(F_, P_) \
+    k_deposit<F_, P_><<<b, kThreads, 0, s>>>(st, n, begin, count, n_part, ms, a, T_ev, quantity, parity, order, N, L, \
+                                             grid)
+    if (f == kPlain && presum) FDF_DEPOSIT(kPlain, true);
+    else if (f == kPlain) FDF_DEPOSIT(kPlain, false);
+    else if (f == kWide && presum) FDF_DEPOSIT(kWide, true);
+    else if (f == kWide) FDF_DEPOSIT(kWide, false);
+    else if (presum) FDF_DEPOSIT(kFixed, true);
+    else FDF_DEPOSIT(kFixed, false);
 #undef FDF_DEPOSIT
     return cudaGetLastError();
 }

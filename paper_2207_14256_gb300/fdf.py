@@ -60,6 +60,7 @@ class fdf_params(C.Structure):
         ("eom", C.c_int32),
         ("pass_blocks", C.c_int32),
         ("gather_tile", C.c_int32),
+        ("deposit_presum", C.c_int32),
     ]
 
 
@@ -211,6 +212,7 @@ def make_params(d):
     p.eom = int(d.get("eom", 0))
     p.pass_blocks = int(d.get("pass_blocks", 0))
     p.gather_tile = int(d.get("gather_tile", 0))
+    p.deposit_presum = int(d.get("deposit_presum", 0))
     return p
 
 

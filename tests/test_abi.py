@@ -55,7 +55,7 @@ int main(void) {
   O(fdf_params, omega_m); O(fdf_params, omega_r); O(fdf_params, A_s); O(fdf_params, n_s);
   O(fdf_params, k_pivot); O(fdf_params, flags); O(fdf_params, n_gl); O(fdf_params, sort_every); O(fdf_params, steps_per_pass);
   O(fdf_params, sort_tile); O(fdf_params, sort_cells); O(fdf_params, interp_order);
-  O(fdf_params, superstep_tol); O(fdf_params, eom); O(fdf_params, pass_blocks); O(fdf_params, gather_tile);
+  O(fdf_params, superstep_tol); O(fdf_params, eom); O(fdf_params, pass_blocks); O(fdf_params, gather_tile); O(fdf_params, deposit_presum);
   O(fdf_tables, nk); O(fdf_tables, na); O(fdf_tables, lnk); O(fdf_tables, lna); O(fdf_tables, T_psi);
   O(fdf_tables, T_phi); O(fdf_tables, dTphi_dlna); O(fdf_tables, ncdf); O(fdf_tables, cdf_t);
   O(fdf_tables, cdf_F);
@@ -116,7 +116,7 @@ def test_host_only_calls(fdf, inputs):
     for knob in (dict(interp_order=3), dict(sort_tile=4), dict(sort_cells=-1), dict(steps_per_pass=5),
                  dict(superstep_tol=-0.1), dict(superstep_tol=float("nan")), dict(eom=6), dict(eom=-1),
                  dict(precision=0, eom=5, steps_per_pass=3), dict(precision=5), dict(precision=-1),
-                 dict(flags=4), dict(pass_blocks=4), dict(pass_blocks=-1), dict(gather_tile=2)):
+                 dict(flags=4), dict(pass_blocks=4), dict(pass_blocks=-1), dict(gather_tile=2), dict(deposit_presum=2)):
         with pytest.raises(fdf.FdfError) as e:
             fdf.fdf_footprint(fdf.make_params(inputs.config("c1_32", **knob)))
         assert e.value.code == fdf.FDF_EINVAL, knob

@@ -10,6 +10,8 @@
 * The half-ensemble deposits (Sec. 4 takes power spectra as the cross-spectrum
   of two halves): even and odd ids against the oracle's deposit of those ids,
   and the two halves summing to the whole.
+* The deposit's warp pre-sum (fdf_params.deposit_presum) against the oracle and
+  against one atomic per particle and node.
 * Super-steps (Sec. 2.1): the same schedule as the oracle's, one transform per
   super-step, and the run against the oracle's super-stepped run.
 * The comparison equations of motion (Sec. 3.2 and 5) in the plain FP64 form.
@@ -102,6 +104,44 @@ def test_momentum_density_and_half_ensembles(F, inputs, c1_tables, order):
         print("order %d half %d: %.3e" % (order, parity, err))
         assert err < 1e-5
     assert np.abs(halves[0] + halves[1] - whole).max() <= 1e-12 * np.abs(whole).max()
+
+
+@pytest.mark.parametrize("prec,order", [(0, 1), (0, 2), (1, 1), (1, 2), (3, 1)])
+def test_deposit_presum_matches_the_oracle(F, inputs, c1_tables, prec, order):
+    """The deposit with the warp pre-sum (fdf_params.deposit_presum = 1) against the
+    oracle's deposit and against one atomic per particle and node.  About ten
+    particles per cell and two ragged species, so that a warp's sets of particles
+    sharing a base cell run from one lane to many (every level of the shuffle tree)
+    and the last warp of each species is partly empty; the half-ensemble deposits
+    leave every other lane out of the sums."""
+    p = inputs.config("c1_32", n_part=5003, n_species=2, m_ev=[0.05, 0.2], n_grid=8, n_steps=20, precision=prec,
+                      seed=139, interp_order=order)
+    o = O.Oracle(p, c1_tables)
+    got = {}
+    for presum in (1, -1):
+        with F.Run(dict(p, deposit_presum=presum), c1_tables) as r:
+            r.sample()
+            r.step(p["n_steps"])
+            got[presum] = [r.deposit(-1, F.FDF_Q_W_EPS)] + [r.deposit(-1, F.FDF_Q_W_EPS, par) for par in (0, 1)] + \
+                          [r.deposit(-1, F.FDF_Q_W_QX)]
+    a = math.exp(o.lna(p["n_steps"]))
+    refs = [np.zeros((8, 8, 8)) for _ in range(4)]
+    for s in range(2):
+        g = np.arange(s * p["n_part"], (s + 1) * p["n_part"])
+        ref = o.run(g)
+        refs[0] += o.deposit(g, ref["x"], ref["q"], ref["w"], a, 0)
+        for par in (0, 1):
+            sel = (g % 2) == par
+            refs[1 + par] += o.deposit(g[sel], ref["x"][:, sel], ref["q"][:, sel], ref["w"][sel], a, 0)
+        refs[3] += o.deposit(g, ref["x"], ref["q"], ref["w"], a, 4)
+    bar = 1e-8 if prec == 0 else 1e-5
+    for k, (dep, dref) in enumerate(zip(got[1], refs)):
+        err = np.linalg.norm(dep - dref) / np.linalg.norm(dref)
+        same = np.abs(dep - got[-1][k]).max() / np.abs(got[-1][k]).max()
+        print("prec %d order %d deposit %d: against the oracle %.3e, against the plain deposit %.3e"
+              % (prec, order, k, err, same))
+        assert err < bar
+        assert same <= 1e-12
 
 
 def test_bad_deposit_arguments_are_refused(F, inputs, c1_tables):
