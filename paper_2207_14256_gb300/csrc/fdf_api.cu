@@ -202,7 +202,7 @@ constexpr int kMaxBuf = 2 * (kMaxSub - 1) + 1;
 int grid_buffers(const fdf_params& p) { return std::min(kMaxBuf, 2 * steps_per_pass(p) + 1); }
 
 struct Layout {
-    size_t tabs, modeA, noise, cdf_t, cdf_F, tw, W0, W1, G[kMaxBuf], Gss[2], qs, stage, dep, flag, key, hist, bsum,
+    size_t tabs, modeA, noise, cdf_t, cdf_F, tw, W0, W1, G[kMaxBuf], Gss[2], qs, stage, dep, flag, ctr, key, hist, bsum,
         recs, total;
     int nbuf;
     StateLayout s[2];
@@ -267,6 +267,7 @@ Layout make_layout(const fdf_params& p, int nk, int na, int ncdf)
     L.stage = take(7 * (size_t)p.n_part * 8);
     L.dep = take(N3 * 8);
     L.flag = take(64);
+    L.ctr = take(64);
     L.total = off;
     return L;
 }
@@ -406,6 +407,7 @@ struct fdf_ctx {
     double* stage = nullptr;
     double* dep = nullptr;
     int* dflag = nullptr;
+    unsigned long long* pass_ctr = nullptr;   // the FP64-state pass's work counters (zero between passes)
     bool sampled = false;
     bool stepped = false;
     int k = 0;
@@ -542,10 +544,7 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.wide_series = 1;
     for (int s = 0; s < kMaxSpecies; ++s) a.m2[s] = c->p.m_ev[s] * c->p.m_ev[s];
     a.grid_blocks = c->sm_count * (c->p.pass_blocks > 0 ? c->p.pass_blocks : 3);
-    // With fewer than three pass blocks per SM a build block fits beside them (registers);
-    // the carveout keeps 100 KB of each SM's shared memory configured for it (the pass
-    // itself uses none), so that the SM need not drain before a build block can start.
-    a.carveout = c->p.pass_blocks > 0 && c->p.pass_blocks < 3 ? 44 : -1;
+    a.ctr = c->pass_ctr;
     a.tile_gather = c->p.gather_tile > 0 ? 1 : 0;
     a.N = c->p.n_grid;
     a.L = c->p.box_mpc;
@@ -1099,6 +1098,7 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     c->stage = (double*)(b + L.stage);
     c->dep = (double*)(b + L.dep);
     c->dflag = (int*)(b + L.flag);
+    c->pass_ctr = (unsigned long long*)(b + L.ctr);
     // tables and twiddles
     const size_t ntab = (size_t)t->na * t->nk;
     const int N = p->n_grid;
@@ -1126,6 +1126,7 @@ int fdf_create(const fdf_params* p, const fdf_tables* t, void* stream, void* are
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->cdf_t, t->cdf_t, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice, s0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->cdf_F, t->cdf_F, (size_t)t->ncdf * 8, cudaMemcpyHostToDevice, s0);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->dflag, 0, 64, s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->pass_ctr, 0, 64, s0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
     // the fields stream takes the priority of the caller's stream
     int prio = 0;

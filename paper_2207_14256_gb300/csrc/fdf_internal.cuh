@@ -118,8 +118,7 @@ struct PushArgs {
     int order;                  // interpolation order r: 1 cloud-in-cell, 2 TSC
     int eom;                    // FDF_EOM_* (the plain FP64 form)
     int grid_blocks;            // the FP64-state form: blocks of its persistent pass grid
-    int carveout;               // the FP64-state form: the pass kernel's preferred shared-memory
-                                // carveout in percent, -1 = the driver's choice
+    unsigned long long* ctr;    // the FP64-state form: two work counters, zero at launch
     int tile_gather;            // the split-state form: kicks gather from shared-memory tiles
     int wide_series;            // the FP64-state form: every fitted polynomial of this pass passed
                                 // its check (else the integrals loop over the nodes)

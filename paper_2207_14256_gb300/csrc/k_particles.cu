@@ -40,8 +40,7 @@ unsigned grid_for(int64_t n, int per_sm = 16)
 // The particle passes launch at the device's greatest execution priority
 // (cudaLaunchAttributePriority).  The grids of the next pass are built on another
 // stream at the default priority; when both wait for room on the SMs, the block
-// scheduler places the pass's blocks first and the builds run in the room the pass
-// leaves (pass_blocks < 3 leaves room for one build block per SM).
+// scheduler places the pass's blocks first.
 int pass_priority()
 {
     int least = 0, greatest = 0;
@@ -49,17 +48,10 @@ int pass_priority()
     return greatest;
 }
 
-// A launch error is left for the caller's cudaGetLastError.  Unless carveout is kKeepCarveout
-// the kernel's preferred shared-memory carveout (percent of the largest, -1 = the driver's
-// default) is set first.
-constexpr int kKeepCarveout = -2;
-
+// A launch error is left for the caller's cudaGetLastError.
 template <typename... K, typename... A>
-void launch_pass_carveout(int carveout, void (*kernel)(K...), unsigned blocks, cudaStream_t s, A&&... args)
+void launch_pass(void (*kernel)(K...), unsigned blocks, cudaStream_t s, A&&... args)
 {
-    if (carveout != kKeepCarveout &&
-        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout) != cudaSuccess)
-        return;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(kThreads);
@@ -71,12 +63,6 @@ void launch_pass_carveout(int carveout, void (*kernel)(K...), unsigned blocks, c
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
-}
-
-template <typename... K, typename... A>
-void launch_pass(void (*kernel)(K...), unsigned blocks, cudaStream_t s, A&&... args)
-{
-    launch_pass_carveout(kKeepCarveout, kernel, blocks, s, std::forward<A>(args)...);
 }
 
 // ---- grid reads ------------------------------------------------------------
@@ -866,17 +852,39 @@ __device__ __forceinline__ void wide_particle(const PushArgs& a, double* __restr
     }
 }
 
-// Three resident blocks per SM (80 registers, no spills): 24 warps keep the FP64 pipe
-// busy through the latency of its results and of the gather.
+// Up to three resident blocks per SM (80 registers, no spills): 24 warps keep the FP64
+// pipe busy through the latency of its results and of the gather.  Work is handed out
+// at run time, kWideChunk consecutive particles to a warp at a time (a.ctr[0] counts the
+// chunks taken), so that the pass ends together on every SM however its blocks were
+// placed beside the builds of the next grids.  The last warp to finish (a.ctr[1]
+// counts them) sets both counters back to zero for the next pass.
+constexpr int kWideChunk = 256;
+
 template <typename Gt, bool SERIES, bool UNI>
 __global__ void __launch_bounds__(kThreads, 3) k_push_wide(const __grid_constant__ PushArgs a,
                                                            double* __restrict__ xd, double* __restrict__ qd,
                                                            const float* __restrict__ q0f)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < a.n; i0 += stride) {
-        const int64_t i = i0 + threadIdx.x;
-        if (i < a.n) wide_particle<Gt, SERIES, UNI>(a, xd, qd, q0f, i);
+    const unsigned lane = threadIdx.x & 31u;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(a.ctr, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        const int64_t i0 = (int64_t)c * kWideChunk;
+        if (i0 >= a.n) break;
+#pragma unroll 1
+        for (int r = 0; r < kWideChunk; r += 32) {
+            const int64_t i = i0 + r + lane;
+            if (i < a.n) wide_particle<Gt, SERIES, UNI>(a, xd, qd, q0f, i);
+        }
+    }
+    if (lane == 0) {
+        const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x / 32);
+        __threadfence();
+        if (atomicAdd(a.ctr + 1, 1ull) == warps - 1) {
+            a.ctr[0] = 0;
+            a.ctr[1] = 0;
+        }
     }
 }
 
@@ -902,13 +910,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_push_wide_multi(const __grid_co
 template <typename Gt>
 void push_wide(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
 {
-    const int cv = a.carveout;
     if (a.wide_series) {
-        if (a.uniform_species) launch_pass_carveout(cv, k_push_wide<Gt, true, true>, b, s, a, st.xd, st.qd, st.q0f);
-        else launch_pass_carveout(cv, k_push_wide<Gt, true, false>, b, s, a, st.xd, st.qd, st.q0f);
+        if (a.uniform_species) launch_pass(k_push_wide<Gt, true, true>, b, s, a, st.xd, st.qd, st.q0f);
+        else launch_pass(k_push_wide<Gt, true, false>, b, s, a, st.xd, st.qd, st.q0f);
     } else {
-        if (a.uniform_species) launch_pass_carveout(cv, k_push_wide<Gt, false, true>, b, s, a, st.xd, st.qd, st.q0f);
-        else launch_pass_carveout(cv, k_push_wide<Gt, false, false>, b, s, a, st.xd, st.qd, st.q0f);
+        if (a.uniform_species) launch_pass(k_push_wide<Gt, false, true>, b, s, a, st.xd, st.qd, st.q0f);
+        else launch_pass(k_push_wide<Gt, false, false>, b, s, a, st.xd, st.qd, st.q0f);
     }
 }
 
@@ -1289,8 +1296,9 @@ cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, 
     if (f == kPlain) {
         launch_pass(k_push_f64, grid_for(a.n), s, a, st.xd, st.qd, st.q0d, st.sd);
     } else if (f == kWide) {
-        // a persistent grid of pass_blocks (<= 3 resident) blocks per SM, each walking the
-        // particles with a grid stride
+        // a persistent grid of pass_blocks (<= 3 resident) blocks per SM, whose warps take
+        // chunks of particles from the work counters
+        if (!a.ctr) return cudaErrorInvalidValue;
         int64_t nb = (a.n + kThreads - 1) / kThreads;
         if (nb > a.grid_blocks) nb = a.grid_blocks;
         const unsigned b = (unsigned)(nb < 1 ? 1 : nb);
