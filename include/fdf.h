@@ -164,11 +164,14 @@ typedef struct fdf_params {
                                   (eq:p_eq), FDF_EOM_Q_SIMPLE (eq:q_eq), FDF_EOM_NEWTONIAN, and
                                   FDF_EOM_EXACT (eq:releq and eq:geodesic themselves, not
                                   symplectic; steps_per_pass 0, 1 or 2) */
-    int32_t  pass_blocks;      /* the FP32/BF16-grid forms with the FP64 state: resident blocks
-                                  of 256 threads per SM of the particle pass, whose grid is
-                                  that many per SM (persistent), 0 = automatic (3) or 1..3;
-                                  fewer leave room on each SM for the field builds of the
-                                  next pass.  Ignored by the other forms. */
+    int32_t  pass_blocks;      /* the FP32/BF16-grid forms with the FP64 state: the launch shape
+                                  of the particle pass, a persistent grid of this many blocks
+                                  of 256 threads per SM: 2 = two particles per thread (128
+                                  registers), 1 or 3 = one particle per thread (80 registers);
+                                  0 = automatic (2: measured fastest on the 3 x 256^3
+                                  workload, 714 ms per run against 736 ms with 3).  The
+                                  results are the same bit for bit.  Ignored by the other
+                                  forms. */
     int32_t  gather_tile;      /* the split-state forms: 1 = each block's kicks read the grid from a
                                   shared-memory tile of the cells its particles occupy (loaded once
                                   per kick; order-1 reads only), -1 = every read from the grid in
@@ -385,10 +388,10 @@ FDF_API void fdf_destroy(fdf_ctx* c);
 /* Autotuner of the schedule knobs that change speed only (no result beyond the
  * stated tolerances): sort_cells, sort_tile, steps_per_pass and (FP64-state forms)
  * pass_blocks.  It times whole runs (fdf_sample + fdf_step(n_steps)) of p on the
- * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16, 32},
+ * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16, 32, 64},
  * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4}, pass_blocks in {2, 3} (FP64-state
  * forms) or gather_tile in {-1, 1} (split-state forms), then sort_cells again in
- * {3, 5, 6, 12}), starting from the automatic choices, and writes
+ * {3, 5, 6, 12, 24, 48}), starting from the automatic choices, and writes
  * the fastest parameter set to *out (p with the knobs set).  The paper
  * has no counterpart.  stream: a cudaStream_t or NULL; every trial allocates
  * and frees its own context.  ms (may be NULL) receives the best run time;

@@ -543,7 +543,9 @@ void fill_pass(const fdf_ctx* c, PushArgs& a)
     a.eom = c->p.eom;
     a.wide_series = 1;
     for (int s = 0; s < kMaxSpecies; ++s) a.m2[s] = c->p.m_ev[s] * c->p.m_ev[s];
-    a.grid_blocks = c->sm_count * (c->p.pass_blocks > 0 ? c->p.pass_blocks : 3);
+    const int pb = c->p.pass_blocks > 0 ? c->p.pass_blocks : 2;
+    a.grid_blocks = c->sm_count * pb;
+    a.pair = pb == 2 ? 1 : 0;
     a.ctr = c->pass_ctr;
     a.tile_gather = c->p.gather_tile > 0 ? 1 : 0;
     a.N = c->p.n_grid;

@@ -119,6 +119,7 @@ struct PushArgs {
     int eom;                    // FDF_EOM_* (the plain FP64 form)
     int grid_blocks;            // the FP64-state form: blocks of its persistent pass grid
     unsigned long long* ctr;    // the FP64-state form: two work counters, zero at launch
+    int pair;                   // the FP64-state form: two particles per thread (two blocks per SM)
     int tile_gather;            // the split-state form: kicks gather from shared-memory tiles
     int wide_series;            // the FP64-state form: every fitted polynomial of this pass passed
                                 // its check (else the integrals loop over the nodes)

@@ -852,30 +852,116 @@ __device__ __forceinline__ void wide_particle(const PushArgs& a, double* __restr
     }
 }
 
-// Up to three resident blocks per SM (80 registers, no spills): 24 warps keep the FP64
-// pipe busy through the latency of its results and of the gather.  Work is handed out
-// at run time, kWideChunk consecutive particles to a warp at a time (a.ctr[0] counts the
-// chunks taken), so that the pass ends together on every SM however its blocks were
-// placed beside the builds of the next grids.  The last warp to finish (a.ctr[1]
-// counts them) sets both counters back to zero for the next pass.
-constexpr int kWideChunk = 256;
+// P particles per thread in lockstep (i0 + 32 p, p < P; i0 < n): their chains are
+// independent, so the FP64 pipe overlaps one particle's result latencies with the
+// others' work.  A particle at or past n repeats particle i0's work and stores nothing.
+template <typename Gt, bool SERIES, bool UNI, int P>
+__device__ __forceinline__ void wide_particles(const PushArgs& a, double* __restrict__ xd, double* __restrict__ qd,
+                                               const float* __restrict__ q0f, int64_t i0)
+{
+    const int64_t n = a.n;
+    const uint32_t N = (uint32_t)a.N;
+    const float invh = (float)a.invh;
+    const long long Lbits = __double_as_longlong(a.L);
+    int64_t idx[P];
+    bool ok[P];
+    int s[P];
+    double x[P][3], q[P][3], s0[P];
+    float q0[P][3], q02[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        idx[p] = i0 + 32 * p;
+        ok[p] = idx[p] < n;
+        if (!ok[p]) idx[p] = i0;
+        const int64_t i = idx[p];
+        s[p] = UNI ? 0 : species_of(a, i);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            x[p][d] = __ldcs(xd + d * n + i);
+            q[p][d] = __ldcs(qd + d * n + i);
+            q0[p][d] = __ldcs(q0f + d * n + i);
+        }
+        const double da = f2d_bits(q0[p][0]), db = f2d_bits(q0[p][1]), dc = f2d_bits(q0[p][2]);
+        s0[p] = fma(da, da, fma(db, db, dc * dc));
+        q02[p] = d2f_bits(s0[p]);
+    }
+    bool moved = false, kicked = false;
+    for (int u = 0; u < a.nsub; ++u) {
+        const SubStep& st = a.sub[u];
+        float Kpsif[P], Kphif[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            Kpsif[p] = 0.f;
+            Kphif[p] = 0.f;
+            if (st.do_kick) kick_integrals<SERIES>(st, s[p], a.n_kick, s0[p], Kpsif[p], Kphif[p]);
+        }
+        if (st.do_drift) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const double D = drift_integral<SERIES>(st, s[p], a.n_gl, q[p]);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) x[p][d] = wrap_rare(fma(q[p][d], D, x[p][d]), a.L, a.invL, Lbits);
+            }
+            moved = true;
+        }
+        if (st.do_kick) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                float g[8];
+                gather_wide<Gt>(a.order, reinterpret_cast<const Gt*>(a.G[u]), N, invh, x[p], g);
+                const float qa = q0[p][0], qb = q0[p][1], qc = q0[p][2];
+                const float qdphi = qa * g[3] + qb * g[4] + qc * g[5];
+                const float b = qdphi * Kphif[p] + g[6] * st.wide.dtau_k;
+                const float a2 = q02[p] * Kphif[p];
+                q[p][0] += f2d_bits(-g[0] * Kpsif[p] - g[3] * a2 + qa * b);
+                q[p][1] += f2d_bits(-g[1] * Kpsif[p] - g[4] * a2 + qb * b);
+                q[p][2] += f2d_bits(-g[2] * Kpsif[p] - g[5] * a2 + qc * b);
+            }
+            kicked = true;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (!ok[p]) continue;
+        const int64_t i = idx[p];
+        if (moved)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) __stcs(xd + d * n + i, x[p][d]);
+        if (kicked)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) __stcs(qd + d * n + i, q[p][d]);
+    }
+}
 
-template <typename Gt, bool SERIES, bool UNI>
-__global__ void __launch_bounds__(kThreads, 3) k_push_wide(const __grid_constant__ PushArgs a,
-                                                           double* __restrict__ xd, double* __restrict__ qd,
-                                                           const float* __restrict__ q0f)
+// The pass kernel: P particles per thread, with three resident blocks per SM for P = 1
+// (80 registers, 24 warps) and two for P = 2 (128 registers, 16 warps carrying 32
+// particles each); the second shape measured faster (its pairs give the FP64 pipe two
+// independent chains per thread to overlap).  Work is handed out at run time, 32 P
+// consecutive particles to a warp at a time (a.ctr[0] counts the chunks taken; each
+// warp claims its next chunk before working on the current one, so that the atomic's
+// round trip overlaps the work): the pass ends together on every SM however its
+// blocks were placed, and the particles in flight stay one stretch of the cell order,
+// whose grid cells the gathers share in L2.  The last warp to finish (a.ctr[1] counts
+// them) sets both counters back to zero for the next pass.
+
+template <typename Gt, bool SERIES, bool UNI, int P>
+__global__ void __launch_bounds__(kThreads, P == 2 ? 2 : 3) k_push_wide(const __grid_constant__ PushArgs a,
+                                                                       double* __restrict__ xd,
+                                                                       double* __restrict__ qd,
+                                                                       const float* __restrict__ q0f)
 {
     const unsigned lane = threadIdx.x & 31u;
+    unsigned next = 0;   // chunk indices (n < 2^38)
+    if (lane == 0) next = (unsigned)atomicAdd(a.ctr, 1ull);
     for (;;) {
-        unsigned long long c = 0;
-        if (lane == 0) c = atomicAdd(a.ctr, 1ull);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        const int64_t i0 = (int64_t)c * kWideChunk;
+        const unsigned c = __shfl_sync(0xffffffffu, next, 0);
+        const int64_t i0 = (int64_t)c * (32 * P);
         if (i0 >= a.n) break;
-#pragma unroll 1
-        for (int r = 0; r < kWideChunk; r += 32) {
-            const int64_t i = i0 + r + lane;
-            if (i < a.n) wide_particle<Gt, SERIES, UNI>(a, xd, qd, q0f, i);
+        if (lane == 0) next = (unsigned)atomicAdd(a.ctr, 1ull);
+        const int64_t i = i0 + lane;
+        if (i < a.n) {
+            if constexpr (P == 1) wide_particle<Gt, SERIES, UNI>(a, xd, qd, q0f, i);
+            else wide_particles<Gt, SERIES, UNI, P>(a, xd, qd, q0f, i);
         }
     }
     if (lane == 0) {
@@ -910,12 +996,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_push_wide_multi(const __grid_co
 template <typename Gt>
 void push_wide(cudaStream_t s, unsigned b, const PushArgs& a, const ParticleState& st)
 {
-    if (a.wide_series) {
-        if (a.uniform_species) launch_pass(k_push_wide<Gt, true, true>, b, s, a, st.xd, st.qd, st.q0f);
-        else launch_pass(k_push_wide<Gt, true, false>, b, s, a, st.xd, st.qd, st.q0f);
+    // two particles per thread with the fitted integrals (the node loops keep one)
+    if (a.pair && a.wide_series) {
+        if (a.uniform_species) launch_pass(k_push_wide<Gt, true, true, 2>, b, s, a, st.xd, st.qd, st.q0f);
+        else launch_pass(k_push_wide<Gt, true, false, 2>, b, s, a, st.xd, st.qd, st.q0f);
+    } else if (a.wide_series) {
+        if (a.uniform_species) launch_pass(k_push_wide<Gt, true, true, 1>, b, s, a, st.xd, st.qd, st.q0f);
+        else launch_pass(k_push_wide<Gt, true, false, 1>, b, s, a, st.xd, st.qd, st.q0f);
     } else {
-        if (a.uniform_species) launch_pass(k_push_wide<Gt, false, true>, b, s, a, st.xd, st.qd, st.q0f);
-        else launch_pass(k_push_wide<Gt, false, false>, b, s, a, st.xd, st.qd, st.q0f);
+        if (a.uniform_species) launch_pass(k_push_wide<Gt, false, true, 1>, b, s, a, st.xd, st.qd, st.q0f);
+        else launch_pass(k_push_wide<Gt, false, false, 1>, b, s, a, st.xd, st.qd, st.q0f);
     }
 }
 
@@ -1296,8 +1386,8 @@ cudaError_t launch_push(cudaStream_t s, int precision, const ParticleState& st, 
     if (f == kPlain) {
         launch_pass(k_push_f64, grid_for(a.n), s, a, st.xd, st.qd, st.q0d, st.sd);
     } else if (f == kWide) {
-        // a persistent grid of pass_blocks (<= 3 resident) blocks per SM, whose warps take
-        // chunks of particles from the work counters
+        // a persistent grid of pass_blocks resident blocks per SM, whose warps take chunks
+        // of particles from the work counters
         if (!a.ctr) return cudaErrorInvalidValue;
         int64_t nb = (a.n + kThreads - 1) / kThreads;
         if (nb > a.grid_blocks) nb = a.grid_blocks;

@@ -4,7 +4,7 @@
 // tolerances: how far particles may drift before they are re-bucketed
 // (sort_cells), the size of a bucket (sort_tile: cubes of 2^t cells per axis),
 // the number of leapfrog steps one particle pass covers (steps_per_pass) and, for
-// the FP64-state forms, the resident blocks per SM of the pass (pass_blocks), for the
+// the FP64-state forms, the launch shape of the pass (pass_blocks), for the
 // split-state forms, whether kicks read the grid from shared-memory tiles (gather_tile).
 // Their best values depend on the workload: on how fast the particles cross
 // cells (mass, momentum, box, step), on the grid size against L2 and on the
@@ -67,7 +67,7 @@ extern "C" int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, 
     best.sort_tile = 0;
     best.steps_per_pass = 4;
     const bool wide = form_of(p->precision) == kWide;
-    best.pass_blocks = wide ? 3 : 0;
+    best.pass_blocks = wide ? 2 : 0;
     best.gather_tile = wide ? 0 : -1;
     double best_ms = 0;
     int n = 0;
@@ -83,12 +83,12 @@ extern "C" int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, 
     };
     // a coarse pass over each knob, then the re-sort distance again between the coarse
     // values (its best value moves with the bucket size chosen after it)
-    const std::vector<Knob> knobs = {{&fdf_params::sort_cells, {2, 4, 8, 16, 32}},
+    const std::vector<Knob> knobs = {{&fdf_params::sort_cells, {2, 4, 8, 16, 32, 64}},
                                      {&fdf_params::sort_tile, {0, 1, 2}},
                                      {&fdf_params::steps_per_pass, {2, 3, 4}},
                                      {&fdf_params::pass_blocks, {2, 3}},
                                      {&fdf_params::gather_tile, {-1, 1}},
-                                     {&fdf_params::sort_cells, {3, 5, 6, 12}}};
+                                     {&fdf_params::sort_cells, {3, 5, 6, 12, 24, 48}}};
     for (const Knob& k : knobs) {
         if (k.field == &fdf_params::pass_blocks && !wide) continue;
         if (k.field == &fdf_params::gather_tile && wide) continue;

@@ -326,6 +326,26 @@ def test_full_size_workloads_few_steps(F, inputs, name):
             assert ex < TOL_X and eq < TOL_Q and ew < TOL_W, (ex, eq, ew)
 
 
+@pytest.mark.parametrize("n_steps", [200, 100])
+def test_pass_shapes_give_identical_results(F, inputs, c1_tables, n_steps):
+    """The FP64-state pass's launch shapes (pass_blocks 1, 2, 3: with two blocks per SM each
+    thread carries two particles in lockstep) run the same arithmetic per particle: the
+    results are bitwise equal.  Two ragged species, so that chunks end part-way and a
+    thread's second particle can fall past the end."""
+    p = inputs.config("c1_32", n_part=3001, n_species=2, m_ev=[0.05, 0.2], n_grid=16, n_steps=n_steps,
+                      precision=1, seed=91)
+    got = {}
+    for pb in (1, 2, 3):
+        with F.Run(dict(p, pass_blocks=pb), c1_tables) as r:
+            r.sample()
+            r.step(n_steps)
+            got[pb] = [r.get(s) for s in range(2)]
+    for pb in (1, 2):
+        for s in range(2):
+            for a, b in zip(got[pb][s], got[3][s]):
+                assert np.array_equal(a, b), (pb, s)
+
+
 # ---- inspection hooks --------------------------------------------------------------------------
 @pytest.mark.parametrize("prec,n_steps,series", [(1, 200, 1), (1, 100, 0), (3, 100, 1), (0, 40, 0)])
 def test_pass_info_reports_the_pass_kernel(F, inputs, c1_tables, prec, n_steps, series):
