@@ -54,7 +54,7 @@ WIDE_FP64_PER_PASS = 3
 # FP64-pipe instructions per particle-step of the plain FP64 pass (k_push_f64), from ncu
 # (sm__inst_executed_pipe_fp64.sum x 32 / particle-steps of the launch, 128^3 particles, one step
 # per pass; profiles/), for its FP64-pipe roofline.  Dropped if the sources changed.
-PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"}
+PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "a61bc5ef3323c092:d5abaea70b42f1be:55a2ba5a6a8ebd0f"}
 
 # DRAM bytes per particle-step of the pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the 50 passes of 4 steps of a one-species 256^3 run of the bench's schedule;
@@ -62,10 +62,10 @@ PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "
 # processes (the species are sorted one after the other, so each reads the grid on its own).
 # Valid only for the kernel sources they were measured on: their hash is checked and the figure
 # dropped if they changed.
-PUSH_TRAFFIC = {1: {"bytes_per_particle_step": (4.369e9 + 0.787e9) / (256 ** 3 * 4),
-                    "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"},
-                3: {"bytes_per_particle_step": (3.431e9 + 0.401e9) / (256 ** 3 * 4),
-                    "sources_sha256": "c67f6828a948ba3b:98326a2ea6af2403:55a2ba5a6a8ebd0f"}}
+PUSH_TRAFFIC = {1: {"bytes_per_particle_step": (4.877e9 + 0.788e9) / (256 ** 3 * 4),
+                    "sources_sha256": "a61bc5ef3323c092:d5abaea70b42f1be:55a2ba5a6a8ebd0f"},
+                3: {"bytes_per_particle_step": (3.432e9 + 0.401e9) / (256 ** 3 * 4),
+                    "sources_sha256": "a61bc5ef3323c092:d5abaea70b42f1be:55a2ba5a6a8ebd0f"}}
 PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
 
 
