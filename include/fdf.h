@@ -296,7 +296,9 @@ FDF_API int fdf_deposit_subset(fdf_ctx* c, int32_t species, int32_t quantity, in
  * in [0, L)), q[3][n_part] (eV), w[n_part] (delta-f weight, Sec. 2.2:
  * w = -expm1((p - |q|)/T) / (1 + exp(-|q|/T)); the FP32/BF16-grid forms take
  * p - |q| in FP64 and the rest in FP32, as their deposit does).  Any output pointer may be
- * NULL.  Device or host memory per out_on_device; synchronises the stream. */
+ * NULL.  Device or host memory per out_on_device; synchronises the stream.  Host buffers
+ * that are page-locked and mapped (cudaHostAlloc, cudaHostRegister) are written by the
+ * device directly; other host memory through a device staging buffer and copies. */
 FDF_API int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_t out_on_device);
 
 /* The pre-initial draw of one species before the momentum transform:

@@ -1526,9 +1526,28 @@ int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_
     const int64_t np = c->p.n_part;
     if (np == 0) return FDF_OK;
     const int64_t begin = species * np;
-    double* xs = out_on_device ? x : (x ? c->stage : nullptr);
-    double* qs = out_on_device ? q : (q ? c->stage + 3 * np : nullptr);
-    double* ws = out_on_device ? w : (w ? c->stage + 6 * np : nullptr);
+    // Host buffers that are page-locked and mapped into the device's address space are
+    // written by the export kernel itself (over the CPU-GPU link); others go through
+    // the staging buffer and a copy each.
+    bool direct = out_on_device != 0;
+    double *xm = x, *qm = q, *wm = w;
+    if (!direct) {
+        direct = true;
+        for (double** ptr : {&xm, &qm, &wm}) {
+            if (!*ptr) continue;
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, *ptr) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+                !at.devicePointer) {
+                cudaGetLastError();
+                direct = false;
+                break;
+            }
+            *ptr = (double*)at.devicePointer;
+        }
+    }
+    double* xs = direct ? xm : (x ? c->stage : nullptr);
+    double* qs = direct ? qm : (q ? c->stage + 3 * np : nullptr);
+    double* ws = direct ? wm : (w ? c->stage + 6 * np : nullptr);
     // a sorted state leaves id order: go through the sort's record buffer
     int rc = timed(c, FDF_K_OTHER, "export", [&] {
         if (c->sorts > 0 && c->recs)
@@ -1537,7 +1556,7 @@ int fdf_get(fdf_ctx* c, int32_t species, double* x, double* q, double* w, int32_
         return launch_export(c->stream, c->p.precision, c->st, c->n, begin, np, c->p.box_mpc, c->T_ev, xs, qs, ws);
     });
     if (rc) return rc;
-    if (!out_on_device) {
+    if (!direct) {
         if (x) FDF_CUDA(cudaMemcpyAsync(x, xs, 3 * np * 8, cudaMemcpyDeviceToHost, c->stream), "copy x");
         if (q) FDF_CUDA(cudaMemcpyAsync(q, qs, 3 * np * 8, cudaMemcpyDeviceToHost, c->stream), "copy q");
         if (w) FDF_CUDA(cudaMemcpyAsync(w, ws, np * 8, cudaMemcpyDeviceToHost, c->stream), "copy w");

@@ -346,6 +346,34 @@ def test_pass_shapes_give_identical_results(F, inputs, c1_tables, n_steps):
                 assert np.array_equal(a, b), (pb, s)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_get_into_page_locked_host_memory(F, inputs, c1_tables, prec):
+    """fdf_get into page-locked host buffers (written by the device directly), into
+    pageable host buffers (through the staging buffer) and into device memory: the
+    same values bit for bit, for a sorted state of two ragged species."""
+    import torch
+
+    p = inputs.config("c1_32", n_part=3001, n_species=2, m_ev=[0.05, 0.2], n_grid=16, n_steps=30, precision=prec,
+                      seed=93)
+    n = p["n_part"]
+    with F.Run(p, c1_tables) as r:
+        r.sample()
+        r.step(p["n_steps"])
+        for s in range(2):
+            pinned = [torch.empty(sh, dtype=torch.float64, pin_memory=True) for sh in ((3, n), (3, n), (n,))]
+            pageable = [np.empty(sh) for sh in ((3, n), (3, n), (n,))]
+            dev = [torch.empty(sh, dtype=torch.float64, device="cuda") for sh in ((3, n), (3, n), (n,))]
+            F.fdf_get(r.ctx, s, *pinned)
+            F.fdf_get(r.ctx, s, *pageable)
+            F.fdf_get(r.ctx, s, *dev)
+            for a, b, c in zip(pinned, pageable, dev):
+                assert np.array_equal(a.numpy(), b) and np.array_equal(c.cpu().numpy(), b)
+            # a NULL output next to page-locked ones
+            xq = [torch.empty((3, n), dtype=torch.float64, pin_memory=True) for _ in range(2)]
+            F.fdf_get(r.ctx, s, xq[0], xq[1], None)
+            assert np.array_equal(xq[0].numpy(), pageable[0]) and np.array_equal(xq[1].numpy(), pageable[1])
+
+
 # ---- inspection hooks --------------------------------------------------------------------------
 @pytest.mark.parametrize("prec,n_steps,series", [(1, 200, 1), (1, 100, 0), (3, 100, 1), (0, 40, 0)])
 def test_pass_info_reports_the_pass_kernel(F, inputs, c1_tables, prec, n_steps, series):
