@@ -139,9 +139,10 @@ typedef struct fdf_params {
                                   sampling and whenever the typical displacement since the last
                                   sort exceeds sort_cells cells; k > 0 = every k steps; -1 = never
                                   (always after sampling unless -1) */
-    int32_t  steps_per_pass;   /* leapfrog steps per particle pass, 1..4: the particle state is
-                                  read and written once per pass (0 = 4 for the FP32/BF16-grid
-                                  forms, 1 for the plain FP64 form) */
+    int32_t  steps_per_pass;   /* leapfrog steps per particle pass, 1..8: the particle state is
+                                  read and written once per pass, and 2 steps_per_pass + 1 grids
+                                  are held (0 = 4 for the FP32/BF16-grid forms, 1 for the plain
+                                  FP64 form) */
     int32_t  sort_tile;        /* sort buckets are cubes of 2^sort_tile cells per axis, 0..3
                                   (0 = single cells) */
     int32_t  sort_cells;       /* with sort_every = 0: re-bucket when the typical particle has
@@ -391,7 +392,7 @@ FDF_API void fdf_destroy(fdf_ctx* c);
  * stated tolerances): sort_cells, sort_tile, steps_per_pass and (FP64-state forms)
  * pass_blocks.  It times whole runs (fdf_sample + fdf_step(n_steps)) of p on the
  * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16, 32, 64},
- * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4}, pass_blocks in {2, 3} (FP64-state
+ * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4, 6, 8}, pass_blocks in {2, 3} (FP64-state
  * forms) or gather_tile in {-1, 1} (split-state forms), then sort_cells again in
  * {3, 5, 6, 12, 24, 48}), starting from the automatic choices, and writes
  * the fastest parameter set to *out (p with the knobs set).  The paper

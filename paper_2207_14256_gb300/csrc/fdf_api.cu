@@ -193,7 +193,7 @@ struct StateLayout {
 int steps_per_pass(const fdf_params& p)
 {
     if (p.steps_per_pass > 0) return p.steps_per_pass;
-    return form_of(p.precision) == kPlain ? 1 : kMaxSub - 1;
+    return form_of(p.precision) == kPlain ? 1 : 4;
 }
 
 // Grids held at once: the current pass's (its steps plus the opening kick's) and
@@ -307,7 +307,7 @@ int fdf::validate_params(const fdf_params* p)
     if (p->flags & ~(FDF_FLAG_FIXED_AMPLITUDE | FDF_FLAG_LEGENDRE_DIPOLE)) return fail(FDF_EINVAL, "unknown flags");
     if (p->sort_every < -1) return fail(FDF_EINVAL, "sort_every must be -1, 0 or a step count");
     if (p->steps_per_pass < 0 || p->steps_per_pass > kMaxSub - 1)
-        return fail(FDF_EINVAL, "steps_per_pass must be 0 (automatic) or 1..4");
+        return fail(FDF_EINVAL, "steps_per_pass must be 0 (automatic) or 1..8");
     if (p->sort_tile < 0 || p->sort_tile > 3 || (p->n_grid >> p->sort_tile) < 1)
         return fail(FDF_EINVAL, "sort_tile must be 0..3 and at most log2(n_grid)");
     if (p->sort_cells < 0) return fail(FDF_EINVAL, "sort_cells must be >= 0");

@@ -105,7 +105,7 @@ struct SubStep {
 
 constexpr double kSeriesMaxE = 0.25;
 
-constexpr int kMaxSub = 5;      // sub-steps per particle pass (an open kick and 4 steps)
+constexpr int kMaxSub = 9;      // sub-steps per particle pass (an open kick and 8 steps)
 
 struct PushArgs {
     int64_t n;                  // particles in all species

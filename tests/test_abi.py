@@ -113,7 +113,7 @@ def test_host_only_calls(fdf, inputs):
     bad = fdf.make_params(inputs.config("c1_32", n_species=5, m_ev=[0.1] * 4))
     with pytest.raises(fdf.FdfError):
         fdf.fdf_footprint(bad)
-    for knob in (dict(interp_order=3), dict(sort_tile=4), dict(sort_cells=-1), dict(steps_per_pass=5),
+    for knob in (dict(interp_order=3), dict(sort_tile=4), dict(sort_cells=-1), dict(steps_per_pass=9),
                  dict(superstep_tol=-0.1), dict(superstep_tol=float("nan")), dict(eom=6), dict(eom=-1),
                  dict(precision=0, eom=5, steps_per_pass=3), dict(precision=5), dict(precision=-1),
                  dict(flags=4), dict(pass_blocks=4), dict(pass_blocks=-1), dict(gather_tile=2), dict(deposit_presum=2)):

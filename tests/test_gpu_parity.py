@@ -163,6 +163,19 @@ def test_run_c1_shapes_fp32_grid_forms(F, inputs, c1_tables, prec, n_steps):
     assert np.linalg.norm(dep - dref) / np.linalg.norm(dref) < 1e-5
 
 
+@pytest.mark.parametrize("prec,spp", [(1, 6), (1, 8), (3, 8)])
+def test_long_passes_match_the_oracle(F, inputs, c1_tables, prec, spp):
+    """Passes of 6 and 8 leapfrog steps (the longest the launch carries) against the oracle,
+    200 steps (the fitted-polynomial path of the FP64-state form)."""
+    p = inputs.config("c1_32", n_part=4096, precision=prec, n_steps=200, steps_per_pass=spp)
+    (res,), dep = run_gpu(F, p, c1_tables)
+    o = O.Oracle(p, c1_tables)
+    ref = o.run(np.arange(p["n_part"]))
+    ex, eq, ew = errors(*res, ref, p["box"])
+    print("prec %d, %d steps per pass: max |dx|/L %.3e  max |dq|/q %.3e  max |dw| %.3e" % (prec, spp, ex, eq, ew))
+    assert ex < TOL_X and eq < TOL_Q and ew < TOL_W, (ex, eq, ew)
+
+
 @pytest.mark.parametrize("prec", [0, 1, 3])
 def test_ragged_two_species(F, inputs, c1_tables, prec):
     p = inputs.config("c1_32", n_part=3001, n_species=2, m_ev=[0.05, 0.25], n_grid=16, n_steps=40,
