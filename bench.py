@@ -54,18 +54,19 @@ WIDE_FP64_PER_PASS = 3
 # FP64-pipe instructions per particle-step of the plain FP64 pass (k_push_f64), from ncu
 # (sm__inst_executed_pipe_fp64.sum x 32 / particle-steps of the launch, 128^3 particles, one step
 # per pass; profiles/), for its FP64-pipe roofline.  Dropped if the sources changed.
-PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3, "sources_sha256": "a61bc5ef3323c092:d5abaea70b42f1be:55a2ba5a6a8ebd0f"}
+PLAIN_FP64 = {"per_particle_step": 19136512 * 32 / 128 ** 3,
+              "sources_sha256": "a61bc5ef3323c092:256bffcc5979e4f1:55a2ba5a6a8ebd0f"}
 
 # DRAM bytes per particle-step of the pass, from ncu (dram__bytes_read.sum + dram__bytes_write.sum,
-# mean over the 50 passes of 4 steps of a one-species 256^3 run of the bench's schedule;
+# mean over the 50 passes of a one-species 256^3 run of the bench's schedule;
 # profiles/), by precision setting.  A launch's traffic is this times the particle-steps it
 # processes (the species are sorted one after the other, so each reads the grid on its own).
 # Valid only for the kernel sources they were measured on: their hash is checked and the figure
 # dropped if they changed.
-PUSH_TRAFFIC = {1: {"bytes_per_particle_step": (4.877e9 + 0.788e9) / (256 ** 3 * 4),
-                    "sources_sha256": "a61bc5ef3323c092:d5abaea70b42f1be:55a2ba5a6a8ebd0f"},
-                3: {"bytes_per_particle_step": (3.432e9 + 0.401e9) / (256 ** 3 * 4),
-                    "sources_sha256": "a61bc5ef3323c092:d5abaea70b42f1be:55a2ba5a6a8ebd0f"}}
+PUSH_TRAFFIC = {1: {"bytes_per_particle_step": (10.827e9 + 0.795e9) / (256 ** 3 * 8),
+                    "sources_sha256": "a61bc5ef3323c092:256bffcc5979e4f1:55a2ba5a6a8ebd0f"},
+                3: {"bytes_per_particle_step": (3.433e9 + 0.402e9) / (256 ** 3 * 4),
+                    "sources_sha256": "a61bc5ef3323c092:256bffcc5979e4f1:55a2ba5a6a8ebd0f"}}
 PUSH_SOURCES = ("k_particles.cu", "fdf_internal.cuh", "device_math.cuh")
 
 
@@ -236,9 +237,9 @@ def hbm_roofline(p, ktimes, hbm):
             "frac": achieved / hbm if hbm else None,
             "traffic": (tr["bytes_per_particle_step"] * n_total * p["n_steps"] / max(push_n, 1)
                         if tr and push_sources_hash() == tr["sources_sha256"] else None),
-            "traffic_note": "ncu DRAM bytes per particle-step of the pass (one-species 256^3 run, passes of 4 steps; "
-                            "profiles/) times the launch's particle-steps; null when the kernel sources changed "
-                            "since the capture",
+            "traffic_note": "ncu DRAM bytes per particle-step of the pass (one-species 256^3 run, the headline's "
+                            "schedule; profiles/) times the launch's particle-steps; null when the kernel sources "
+                            "changed since the capture",
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800",
             "algorithmic_bytes_per_launch": alg, "avg_launch_ms": push_avg,
             "steps_per_launch": p["n_steps"] / max(push_n, 1),
@@ -433,17 +434,22 @@ def bench_ours(args, rank, world, dist):
                      "note": "the same workload with the paper's super-steps (not the headline: the headline builds "
                              "every step's fields by transform)"}
 
-    # the split-state form (fixed-point positions, FP32 q0 + dq) on the same workload and
-    # schedule knobs: not the configured precision, reported beside it
+    # the split-state form (fixed-point positions, FP32 q0 + dq) on the same workload with
+    # its own tuned schedule (the headline's with --schedule or --no-tune): not the
+    # configured precision, reported beside it
     split = None
     if not args.no_split:
         psp = dict(p, precision=I.PREC_F32_FIXED)
         Psp = fdf.make_params(psp)
-        for k, v in fdf.knobs(P).items():
-            if k != "n_gl":
-                setattr(Psp, k, v)
+        if args.schedule or args.no_tune:
+            for k, v in fdf.knobs(P).items():
+                if k not in ("n_gl", "pass_blocks", "gather_tile"):
+                    setattr(Psp, k, v)
+        else:
+            Psp, _, _ = fdf.fdf_tune(Psp, T, stream)
         sms, skt = time_form(fdf, torch, Psp, T, stream, psp, dep, 2, 1, barrier)
         split = {"value": units / (sms / 1e3), "ms_per_step": sms, "precision": FORM_NAMES[psp["precision"]],
+                 "schedule": fdf.knobs(Psp),
                  "kernels": {k: {"ms_per_step": v[0], "launches_per_step": v[1]} for k, v in skt.items()},
                  "roofline_hbm": hbm_roofline(psp, skt, peaks().get("hbm_gbs"))}
 
@@ -709,9 +715,9 @@ def main():
         out["speedup_vs_plain_f64"] = value / out["plain_f64"]["value"]
     if r["split"]:
         out["split_state"] = dict(r["split"], value=world * r["split"]["value"],
-                                  note="the split-state form (FDF_PREC_F32_FIXED) on the same workload and schedule: "
-                                       "positions as 32-bit fixed point, momenta as FP32 q0 + dq, float-float drift "
-                                       "and FP32 kick integrals; not the configured precision")
+                                  note="the split-state form (FDF_PREC_F32_FIXED) on the same workload, its own "
+                                       "tuned schedule: positions as 32-bit fixed point, momenta as FP32 q0 + dq, "
+                                       "float-float drift and FP32 kick integrals; not the configured precision")
     if r["c4"]:
         out["c4"] = dict(r["c4"], value=world * r["c4"]["value"],
                          note="the reduced-precision workload, timed as the headline (graph replays + deposit)")
