@@ -220,8 +220,9 @@ def time_form(fdf, torch, P, T, stream, p, dep, runs, warmup, barrier):
 
 
 def hbm_roofline(p, ktimes, hbm):
-    """The particle pass against HBM: the method's algorithmic bytes per launch (SURVEY's
-    108 B per particle-step + 28 B per cell per kick at FP32) over its mean launch time."""
+    """The particle pass against HBM: the method's algorithmic bytes per launch (108 B per
+    particle-step: x and q read and written in FP64, q0 read in FP32; + 28 B per cell per kick
+    for the seven FP32 gradient fields) over its mean launch time."""
     prec = p["precision"]
     push_ms, push_n = ktimes["push"]
     push_avg = push_ms / max(push_n, 1)
