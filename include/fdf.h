@@ -392,7 +392,7 @@ FDF_API void fdf_destroy(fdf_ctx* c);
  * stated tolerances): sort_cells, sort_tile, steps_per_pass and (FP64-state forms)
  * pass_blocks.  It times whole runs (fdf_sample + fdf_step(n_steps)) of p on the
  * device, one knob at a time (coordinate descent over sort_cells in {2, 4, 8, 16, 32, 64},
- * sort_tile in {0, 1, 2}, steps_per_pass in {2, 3, 4, 6, 8}, pass_blocks in {2, 3} (FP64-state
+ * sort_tile in {0, 1, 2, 3}, steps_per_pass in {2, 3, 4, 6, 8}, pass_blocks in {2, 3} (FP64-state
  * forms) or gather_tile in {-1, 1} (split-state forms), then sort_cells again in
  * {3, 5, 6, 12, 24, 48}), starting from the automatic choices, and writes
  * the fastest parameter set to *out (p with the knobs set).  The paper

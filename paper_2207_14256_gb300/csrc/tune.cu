@@ -84,7 +84,7 @@ extern "C" int fdf_tune(const fdf_params* p, const fdf_tables* t, void* stream, 
     // a coarse pass over each knob, then the re-sort distance again between the coarse
     // values (its best value moves with the bucket size chosen after it)
     const std::vector<Knob> knobs = {{&fdf_params::sort_cells, {2, 4, 8, 16, 32, 64}},
-                                     {&fdf_params::sort_tile, {0, 1, 2}},
+                                     {&fdf_params::sort_tile, {0, 1, 2, 3}},
                                      {&fdf_params::steps_per_pass, {2, 3, 4, 6, 8}},
                                      {&fdf_params::pass_blocks, {2, 3}},
                                      {&fdf_params::gather_tile, {-1, 1}},

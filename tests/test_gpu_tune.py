@@ -48,7 +48,7 @@ def test_tuned_knobs_are_valid_and_change_no_result(F, inputs):
     k = F.knobs(tuned)
     print("tuned knobs", k, "best run %.2f ms over %d timed runs" % (ms, trials))
     assert trials >= 6 and ms > 0
-    assert k["sort_cells"] in (2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 48, 64) and k["sort_tile"] in (0, 1, 2) and k["steps_per_pass"] in (2, 3, 4, 6, 8)
+    assert k["sort_cells"] in (2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 48, 64) and k["sort_tile"] in (0, 1, 2, 3) and k["steps_per_pass"] in (2, 3, 4, 6, 8)
     assert k["pass_blocks"] in (2, 3)
     # every other field is the caller's
     for f, _ in F.fdf_params._fields_:
