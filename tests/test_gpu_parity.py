@@ -387,6 +387,24 @@ def test_get_into_page_locked_host_memory(F, inputs, c1_tables, prec):
             assert np.array_equal(xq[0].numpy(), pageable[0]) and np.array_equal(xq[1].numpy(), pageable[1])
 
 
+@pytest.mark.parametrize("n_part", [1, 31, 33, 63, 65, 129])
+def test_pass_chunk_edges(F, inputs, c1_tables, n_part):
+    """Particle counts around the pass's work chunks (32 particles per warp, 64 in pairs):
+    both launch shapes against the oracle, and equal to each other bit for bit."""
+    p = inputs.config("c1_32", n_part=n_part, n_grid=8, n_steps=200, precision=1, seed=97)
+    got = {}
+    for pb in (2, 3):
+        with F.Run(dict(p, pass_blocks=pb), c1_tables) as r:
+            r.sample()
+            r.step(p["n_steps"])
+            got[pb] = r.get(0)
+    for a, b in zip(got[2], got[3]):
+        assert np.array_equal(a, b)
+    ref = O.Oracle(p, c1_tables).run(np.arange(n_part))
+    ex, eq, ew = errors(*got[2], ref, p["box"])
+    assert ex < TOL_X and eq < TOL_Q and ew < TOL_W, (ex, eq, ew)
+
+
 # ---- inspection hooks --------------------------------------------------------------------------
 @pytest.mark.parametrize("prec,n_steps,series", [(1, 200, 1), (1, 100, 0), (3, 100, 1), (0, 40, 0)])
 def test_pass_info_reports_the_pass_kernel(F, inputs, c1_tables, prec, n_steps, series):
